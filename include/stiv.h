@@ -1,0 +1,219 @@
+/*
+ * libstiv: contact detection and space-time interference volumes (STIV) of
+ * vesicle meshes on one GPU.
+ *
+ * Method: Lu, Rahimian & Zorin, "Parallel contact-aware simulations of
+ * deformable particles in 3D Stokes flow" (arXiv 1812.04719):
+ *   - each vesicle surface is a spherical-harmonic (SH) series of order p
+ *     (Sec. 3.1.1), upsampled to order P = 2p and triangulated (Sec. 3.1.2,
+ *     Fig. 3) at the start (X0, time t_n) and end (X1, time t_{n+1}) of a step;
+ *   - candidate vesicle pairs come from space-time bounding boxes sorted on a
+ *     Morton-ordered grid (Sec. 3.3.1, Alg. 1);
+ *   - each vertex-triangle (and edge-edge) pair gets its earliest contact time
+ *     from the coplanarity equation (Eq. 3.1, d_m = 0) under linear motion;
+ *   - each contact gets the volume of Eq. 3.2 (App. A) and its gradient with
+ *     respect to X1 (Sec. 3.1.2, Sec. 3.3.2), summed per vesicle pair (Alg. 2).
+ *
+ * Conventions for every entry point:
+ *   - Array pointers are DEVICE pointers owned by the caller; the library never
+ *     frees them and keeps none of them after the call returns.
+ *   - Every call is asynchronous on the given CUDA stream (a cudaStream_t
+ *     passed as void*, NULL = legacy default stream).  Counts are written to
+ *     device memory; stiv_sync_counts copies them to the host.
+ *   - The return value is a status: STIV_OK, or STIV_ERR_* for a bad argument
+ *     or a CUDA launch/allocation failure.  Nothing traps or aborts.  Errors
+ *     found by the kernels themselves (capacity overflow, invalid periodic
+ *     box, non-finite input) are flags in counts[STIV_C_STATUS].
+ *   - Scratch memory is owned by the handle (grown on demand with cudaMalloc).
+ *
+ * Layouts (N = number of vesicles, p_v = SH order of vesicle v, P_v = 2 p_v):
+ *   coef:  per vesicle [2 time][3 coord][(p_v+1)^2] doubles at coef_off[v];
+ *          real orthonormal SH without Condon-Shortley phase, entry n^2+n+m,
+ *          m > 0 ~ cos(m phi), m < 0 ~ sin(|m| phi).
+ *   verts: per vesicle [2 time][3 coord][n_v(P_v)] at vert_off[v] (elements),
+ *          n_v(P) = 2P(P+1) + 2; doubles (STIV_FP64) or floats (STIV_MIXED).
+ *          Vertex i*2P + j sits at polar angle arccos(x_i) (x_i the Gauss-
+ *          Legendre nodes of order P+1, descending) and longitude 2 pi j/(2P);
+ *          vertex 2P(P+1) is the north pole, 2P(P+1)+1 the south pole.
+ *   mesh:  triangles and edges of stiv_mesh_topology; triangle ids and edge
+ *          ids in the contact records refer to them.
+ */
+#ifndef STIV_H
+#define STIV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum stiv_status {
+  STIV_OK = 0,
+  STIV_ERR_ARG = 1,       /* bad argument (null pointer, size out of range) */
+  STIV_ERR_CAPACITY = 2,  /* an output buffer was too small (counts say how big) */
+  STIV_ERR_TIMEOUT = 3,   /* a bounded device wait gave up */
+  STIV_ERR_CUDA = 4,      /* a CUDA call failed (see stiv_last_cuda_error) */
+  STIV_ERR_INPUT = 5      /* kernels flagged the input (see counts[STIV_C_STATUS]) */
+};
+
+enum stiv_precision {
+  STIV_FP64 = 0,   /* FP64 synthesis and vertices; FP64 contact arithmetic */
+  STIV_MIXED = 1   /* FP32 synthesis and vertices; FP64 contact arithmetic */
+};
+
+/* Entries of the device counts array (int64, STIV_NCOUNTS entries). */
+enum stiv_count {
+  STIV_C_PAIRS = 0,    /* candidate vesicle pairs (i < j, image shift)        */
+  STIV_C_PRIM = 1,     /* primitive pairs whose exact swept boxes overlap     */
+  STIV_C_VF = 2,       /* vertex-triangle contacts                            */
+  STIV_C_EE = 3,       /* edge-edge contacts                                  */
+  STIV_C_CPAIRS = 4,   /* vesicle pairs with at least one contact             */
+  STIV_C_DEGEN = 5,    /* primitive pairs skipped as degenerate               */
+  STIV_C_STATUS = 6,   /* bit flags STIV_F_*                                  */
+  STIV_C_PATCH = 7,    /* patch pairs examined by the narrow phase            */
+  STIV_NCOUNTS = 8
+};
+
+enum stiv_flag {
+  STIV_F_PAIRS_OVERFLOW = 1,     /* candidate pairs exceeded stiv_pairs.capacity */
+  STIV_F_CONTACTS_OVERFLOW = 2,  /* contacts exceeded stiv_contacts.capacity    */
+  STIV_F_BOX_TOO_SMALL = 4,      /* a vesicle box spans >= L/2 on a periodic axis */
+  STIV_F_NONFINITE = 8,          /* a vertex coordinate is NaN or infinite      */
+  STIV_F_WORK_OVERFLOW = 16      /* internal work list overflow (re-run)         */
+};
+
+typedef struct stiv_params {
+  double d_m;          /* minimum separation; pads the vesicle boxes (Alg. 2 getBoundingBox) */
+  double eps;          /* epsilon of the space-time metric (App. A), units of velocity */
+  double dt;           /* time step Delta t; V depends on eps and dt only via eps*dt */
+  double box_L[3];     /* periodic box lengths; 0 = free space on that axis */
+  int32_t precision;   /* enum stiv_precision */
+  int32_t include_ee;  /* 1: edge-edge contacts as well as vertex-triangle ones */
+} stiv_params;
+
+/* Candidate vesicle pairs (Alg. 1 output, i < j), sorted by (i, j, shift).
+ * shift = 9 (sx+1) + 3 (sy+1) + (sz+1): vesicle j is taken at X + s * box_L. */
+typedef struct stiv_pairs {
+  int64_t capacity;
+  int32_t* i;
+  int32_t* j;
+  int32_t* shift;
+} stiv_pairs;
+
+/* Contacts (one record per primitive pair with a contact time in [0, 1]),
+ * sorted by (pair, type, a, b).
+ *   pair: index into the candidate pairs; type 0: vertex a of i vs triangle b
+ *   of j; type 1: vertex a of j vs triangle b of i; type 2: edge a of i vs
+ *   edge b of j.  tau: contact time in [0, 1] (fraction of the step).  w:
+ *   [capacity][2], barycentric weights (beta1, beta2) of the contact point in
+ *   the triangle (type 0/1), or the edge parameters (s on edge a, u on edge b). */
+typedef struct stiv_contacts {
+  int64_t capacity;
+  int32_t* pair;
+  int32_t* type;
+  int32_t* a;
+  int32_t* b;
+  double* tau;
+  double* w;
+} stiv_contacts;
+
+typedef struct stiv_handle stiv_handle;
+
+/* Create a handle.  Fails with STIV_ERR_ARG for a negative box length,
+ * non-positive eps or dt, or an unknown precision. */
+int stiv_create(stiv_handle** h, const stiv_params* prm);
+int stiv_destroy(stiv_handle* h);
+
+/* Human-readable name of a status code. */
+const char* stiv_status_string(int status);
+/* The last CUDA error code the handle saw (cudaError_t as int). */
+int stiv_last_cuda_error(const stiv_handle* h);
+
+/* Mesh topology of order P (2 <= P <= 64), Sec. 3.1.2 / Fig. 3: each grid quad
+ * (i,j),(i+1,j),(i+1,j+1),(i,j+1) split along (i,j)-(i+1,j+1) into
+ * [(i,j),(i+1,j),(i+1,j+1)] and [(i,j),(i+1,j+1),(i,j+1)] (ids 2(i*2P+j) and
+ * +1), north fan [N,(0,j),(0,j+1)] (id 4P^2+j), south fan [S,(P,j+1),(P,j)]
+ * (id 4P^2+2P+j), normals outward.  tri_dev: [4P^2+4P][3]; edge_dev:
+ * [6P^2+6P][2], the undirected edges as (min, max) sorted ascending. */
+int stiv_mesh_topology(int32_t P, int32_t* tri_dev, int32_t* edge_dev, void* stream);
+
+/* Sec. 3.1.2 upsampling: evaluate each vesicle's order-p series for X0 and X1
+ * on its order-2p mesh (grid and poles).  p_dev[v] in [1, p_max], p_max <= 32.
+ * Writes doubles (STIV_FP64) or floats (STIV_MIXED) into verts_dev. */
+int stiv_upsample(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                  const int64_t* coef_off_dev, const double* coef_dev,
+                  const int64_t* vert_off_dev, void* verts_dev);
+
+/* Alg. 2 lines 2-6 without the distribution steps: vesicle space-time boxes,
+ * candidate pairs (Alg. 1: Morton-grid sort and bbiCheck), then every
+ * vertex-triangle pair (both directions) and edge-edge pair of each candidate
+ * whose swept boxes overlap is tested with Eq. 3.1 (d_m = 0).  cand and out
+ * are filled; counts_dev gets STIV_NCOUNTS int64 entries.  A periodic axis
+ * requires every vesicle box to span less than half the box length. */
+int stiv_detect(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                const int64_t* vert_off_dev, const void* verts_dev,
+                const stiv_pairs* cand, const stiv_contacts* out, int64_t* counts_dev);
+
+/* Eq. 3.2: V_k of every contact and the per-pair sums V_pair[r] (0 for a
+ * candidate pair without contact).  V_contact_dev: [out->capacity];
+ * V_pair_dev: [cand->capacity].  Either may be NULL. */
+int stiv_stiv(stiv_handle* h, void* stream, int32_t n_ves, const int32_t* p_dev,
+              const int64_t* vert_off_dev, const void* verts_dev, const stiv_pairs* cand,
+              const stiv_contacts* contacts, const int64_t* counts_dev,
+              double* V_contact_dev, double* V_pair_dev);
+
+/* Eq. 3.2 and its gradient with respect to X1 (X0 fixed), through the contact
+ * time (implicit function of Eq. 3.1) and the inside-test weights.  Per
+ * contact k: grad_dev[k][4][3], and for each of the 4 points its vesicle
+ * (g_ves_dev[k][4]) and local vertex id (g_vid_dev[k][4]).  Row r of the
+ * Jacobian J = dV/dX1 (Sec. 3.2, Eq. 3.5-3.7) is the sum of the rows of the
+ * contacts with pair == r. */
+int stiv_stiv_grad(stiv_handle* h, void* stream, int32_t n_ves, const int32_t* p_dev,
+                   const int64_t* vert_off_dev, const void* verts_dev, const stiv_pairs* cand,
+                   const stiv_contacts* contacts, const int64_t* counts_dev,
+                   double* V_contact_dev, double* V_pair_dev,
+                   double* grad_dev, int32_t* g_ves_dev, int32_t* g_vid_dev);
+
+/* Scatter-add per-contact gradient rows, each scaled by weight_pair[pair] (or
+ * 1 if weight_pair is NULL), into a dense array in the vertex layout (only the
+ * X1 block of each vesicle is written; the caller zeroes gX_dev). */
+int stiv_grad_scatter(stiv_handle* h, void* stream, const int32_t* p_dev, const stiv_contacts* contacts,
+                      const int64_t* counts_dev, const double* weight_pair_dev,
+                      const double* grad_dev, const int32_t* g_ves_dev, const int32_t* g_vid_dev,
+                      const int64_t* vert_off_dev, double* gX_dev);
+
+/* Adjoint of the upsampling: gcoef = S^T gX for the X1 block of every vesicle
+ * (S the synthesis matrix of stiv_upsample, grid and poles).  gX_dev in the
+ * FP64 vertex layout; gcoef_dev in the coefficient layout (the X0 block is
+ * set to zero). */
+int stiv_grad_to_coef(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                      const int64_t* coef_off_dev, const int64_t* vert_off_dev,
+                      const double* gX_dev, double* gcoef_dev);
+
+/* The whole per-step path: upsample + detect + stiv_grad.  With use_graph = 1
+ * the launches are captured into a CUDA graph on the first call and replayed
+ * on later calls with the same arguments. */
+int stiv_step(stiv_handle* h, void* stream, int32_t use_graph, int32_t n_ves, int32_t p_max,
+              const int32_t* p_dev, const int64_t* coef_off_dev, const double* coef_dev,
+              const int64_t* vert_off_dev, void* verts_dev, const stiv_pairs* cand,
+              const stiv_contacts* out, int64_t* counts_dev, double* V_contact_dev,
+              double* V_pair_dev, double* grad_dev, int32_t* g_ves_dev, int32_t* g_vid_dev);
+
+/* Wait for the stream, copy the counts to the host and return STIV_ERR_CAPACITY
+ * if an overflow flag is set, STIV_ERR_INPUT for an input flag, else STIV_OK. */
+int stiv_sync_counts(void* stream, const int64_t* counts_dev, int64_t* counts_host);
+
+/* Stable LSD radix sort of (key, value) pairs on the low key_bits bits of the
+ * 64-bit keys (Alg. 1 line 4, the check-point sort, on one GPU).  scratch:
+ * at least stiv_sort_scratch_bytes(n) bytes of device memory. */
+size_t stiv_sort_scratch_bytes(int64_t n);
+int stiv_sort_pairs(void* stream, int64_t n, int32_t key_bits, const uint64_t* keys_in,
+                    const int32_t* vals_in, uint64_t* keys_out, int32_t* vals_out,
+                    void* scratch, size_t scratch_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STIV_H */

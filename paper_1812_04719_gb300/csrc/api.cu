@@ -1,0 +1,256 @@
+// C-ABI entry points of libstiv: handle, scratch, mesh topology, the detect
+// pipeline (Alg. 2) and the captured per-step graph.
+#include "stiv_internal.cuh"
+
+#include <stdlib.h>
+#include <string.h>
+
+int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, const int32_t* p_dev, const int64_t* voff,
+                     const void* X, const stiv_pairs* cand, detect_ws& w, int64_t* ctr);
+int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, const int64_t* voff, const void* X,
+                      const stiv_pairs* cand, detect_ws& w, int num_sms, int p_max);
+int stiv_contact_order(stiv_handle* h, cudaStream_t st, const stiv_pairs* cand, const stiv_contacts* out,
+                       detect_ws& w);
+
+namespace {
+
+__global__ void topology_kernel(int P, int32_t* tri, int32_t* edge) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < stiv_ntris(P)) {
+    int v[3];
+    stiv_tri_verts(P, k, v);
+    tri[3 * k] = v[0]; tri[3 * k + 1] = v[1]; tri[3 * k + 2] = v[2];
+  }
+  if (k < 2 * P * (P + 1)) {  // grid vertex k writes its forward edges
+    int nb[5];
+    int n = stiv_forward_nbrs(P, k, nb);
+    int e0 = stiv_first_edge(P, k);
+    for (int q = 0; q < n; ++q) { edge[2 * (e0 + q)] = k; edge[2 * (e0 + q) + 1] = nb[q]; }
+  }
+}
+
+__global__ void finalize_kernel(int64_t* ctr, int64_t C, int64_t* counts) {
+  if (threadIdx.x == 0) {
+    if (ctr[11] > C) ctr[STIV_C_STATUS] |= STIV_F_CONTACTS_OVERFLOW;
+    for (int k = 0; k < STIV_NCOUNTS; ++k) counts[k] = ctr[k];
+  }
+}
+
+inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" const char* stiv_status_string(int s) {
+  switch (s) {
+    case STIV_OK: return "ok";
+    case STIV_ERR_ARG: return "invalid argument";
+    case STIV_ERR_CAPACITY: return "output capacity exceeded";
+    case STIV_ERR_TIMEOUT: return "device wait timed out";
+    case STIV_ERR_CUDA: return "CUDA error";
+    case STIV_ERR_INPUT: return "invalid input flagged by the kernels";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int stiv_last_cuda_error(const stiv_handle* h) { return h ? h->last_cuda_error : 0; }
+
+extern "C" int stiv_create(stiv_handle** out, const stiv_params* prm) {
+  if (!out || !prm) return STIV_ERR_ARG;
+  *out = nullptr;
+  for (int c = 0; c < 3; ++c) if (!(prm->box_L[c] >= 0.0)) return STIV_ERR_ARG;
+  if (!(prm->eps > 0.0) || !(prm->dt > 0.0) || !(prm->d_m >= 0.0)) return STIV_ERR_ARG;
+  if (prm->precision != STIV_FP64 && prm->precision != STIV_MIXED) return STIV_ERR_ARG;
+  stiv_handle* h = (stiv_handle*)calloc(1, sizeof(stiv_handle));
+  if (!h) return STIV_ERR_ARG;
+  h->prm = *prm;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) { free(h); return STIV_ERR_CUDA; }
+  *out = h;
+  return STIV_OK;
+}
+
+extern "C" int stiv_destroy(stiv_handle* h) {
+  if (!h) return STIV_ERR_ARG;
+  for (int p = 0; p <= STIV_MAX_P; ++p)
+    if (h->tab_ready[p]) { cudaFree(h->tab[p].leg); cudaFree(h->tab[p].trig); cudaFree(h->tab[p].theta); }
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->ws) cudaFree(h->ws);
+  free(h);
+  return STIV_OK;
+}
+
+int stiv_ws_reserve(stiv_handle* h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return STIV_OK;
+  if (h->ws) { STIV_CUDA(h, cudaFree(h->ws)); h->ws = nullptr; h->ws_bytes = 0; }
+  size_t nb = bytes + bytes / 4;
+  STIV_CUDA(h, cudaMalloc(&h->ws, nb));
+  h->ws_bytes = nb;
+  return STIV_OK;
+}
+
+extern "C" int stiv_mesh_topology(int32_t P, int32_t* tri_dev, int32_t* edge_dev, void* stream) {
+  if (P < 2 || P > STIV_MAX_PP || !tri_dev || !edge_dev) return STIV_ERR_ARG;
+  int n = stiv_ntris(P);
+  topology_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(P, tri_dev, edge_dev);
+  if (cudaGetLastError() != cudaSuccess) return STIV_ERR_CUDA;
+  return STIV_OK;
+}
+
+// Scratch of stiv_detect, carved from the handle's buffer.
+static int detect_layout(stiv_handle* h, int n, const stiv_pairs* cand, const stiv_contacts* out, detect_ws& w,
+                         bool carve) {
+  w.R = (int64_t)n * 64 + 1024;
+  w.Q = cand->capacity * 8 + 1024;
+  w.W = cand->capacity * 64 + 1024;
+  if (w.W < out->capacity) w.W = out->capacity;
+  w.C = out->capacity > 0 ? out->capacity : 1;
+  int64_t smax = w.R > w.Q ? w.R : w.Q;
+  if (w.C > smax) smax = w.C;
+  w.sort_scratch_bytes = stiv_sort_scratch_impl(smax);
+  size_t off = 0;
+  size_t o_vbox = off; off = align_up(off + sizeof(double) * 6 * (size_t)n);
+  size_t o_pbox = off; off = align_up(off + sizeof(float) * 6 * (size_t)STIV_MAX_PATCH * n);
+  size_t o_grid = off; off = align_up(off + sizeof(double) * 16);
+  size_t o_cc = off; off = align_up(off + sizeof(int32_t) * (size_t)(n + 1));
+  size_t o_co = off; off = align_up(off + sizeof(int32_t) * (size_t)(n + 1));
+  size_t o_rk = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.R);
+  size_t o_rv = off; off = align_up(off + sizeof(int32_t) * (size_t)w.R);
+  size_t o_rk2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.R);
+  size_t o_rv2 = off; off = align_up(off + sizeof(int32_t) * (size_t)w.R);
+  size_t o_rb = off; off = align_up(off + sizeof(int32_t) * (size_t)w.R);
+  size_t o_rc = off; off = align_up(off + sizeof(int32_t) * (size_t)w.R);
+  size_t o_pk = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q);
+  size_t o_pv = off; off = align_up(off + sizeof(int32_t) * (size_t)w.Q);
+  size_t o_pk2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q);
+  size_t o_pv2 = off; off = align_up(off + sizeof(int32_t) * (size_t)w.Q);
+  size_t o_wk = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.W);
+  size_t o_ck = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.C);
+  size_t o_cv = off; off = align_up(off + sizeof(int32_t) * (size_t)w.C);
+  size_t o_ck2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.C);
+  size_t o_cv2 = off; off = align_up(off + sizeof(int32_t) * (size_t)w.C);
+  size_t o_ti = off; off = align_up(off + sizeof(int32_t) * 4 * (size_t)w.C);
+  size_t o_tf = off; off = align_up(off + sizeof(double) * 3 * (size_t)w.C);
+  size_t o_ctr = off; off = align_up(off + sizeof(int64_t) * 16);
+  size_t o_ss = off; off = align_up(off + w.sort_scratch_bytes);
+  if (!carve) return stiv_ws_reserve(h, off);
+  char* b = (char*)h->ws;
+  w.vbox = (double*)(b + o_vbox); w.pbox = (float*)(b + o_pbox); w.grid = (double*)(b + o_grid);
+  w.cell_count = (int32_t*)(b + o_cc); w.cell_off = (int32_t*)(b + o_co);
+  w.rec_key = (uint64_t*)(b + o_rk); w.rec_val = (int32_t*)(b + o_rv);
+  w.rec_key2 = (uint64_t*)(b + o_rk2); w.rec_val2 = (int32_t*)(b + o_rv2);
+  w.rec_box = (int32_t*)(b + o_rb); w.rec_cell = (int32_t*)(b + o_rc);
+  w.pkey = (uint64_t*)(b + o_pk); w.pval = (int32_t*)(b + o_pv);
+  w.pkey2 = (uint64_t*)(b + o_pk2); w.pval2 = (int32_t*)(b + o_pv2);
+  w.work = (uint64_t*)(b + o_wk);
+  w.ckey = (uint64_t*)(b + o_ck); w.cval = (int32_t*)(b + o_cv);
+  w.ckey2 = (uint64_t*)(b + o_ck2); w.cval2 = (int32_t*)(b + o_cv2);
+  w.tmp_i32 = (int32_t*)(b + o_ti); w.tmp_f64 = (double*)(b + o_tf);
+  w.ctr = (int64_t*)(b + o_ctr);
+  w.sort_scratch = b + o_ss;
+  return STIV_OK;
+}
+
+extern "C" int stiv_detect(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                           const int64_t* vert_off_dev, const void* verts_dev, const stiv_pairs* cand,
+                           const stiv_contacts* out, int64_t* counts_dev) {
+  if (!h || n_ves < 0 || p_max < 1 || p_max > STIV_MAX_P || !cand || !out || !counts_dev) return STIV_ERR_ARG;
+  if (cand->capacity < 1 || out->capacity < 1) return STIV_ERR_ARG;
+  if (!cand->i || !cand->j || !cand->shift || !out->pair || !out->type || !out->a || !out->b || !out->tau || !out->w)
+    return STIV_ERR_ARG;
+  if (cand->capacity >= ((int64_t)1 << 31) || out->capacity >= ((int64_t)1 << 31) || n_ves >= (1 << 24))
+    return STIV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n_ves < 2) {
+    STIV_CUDA(h, cudaMemsetAsync(counts_dev, 0, sizeof(int64_t) * STIV_NCOUNTS, st));
+    return STIV_OK;
+  }
+  if (!p_dev || !vert_off_dev || !verts_dev) return STIV_ERR_ARG;
+  detect_ws w;
+  int rc = detect_layout(h, n_ves, cand, out, w, false);
+  if (rc) return rc;
+  detect_layout(h, n_ves, cand, out, w, true);
+  STIV_CUDA(h, cudaMemsetAsync(w.ctr, 0, sizeof(int64_t) * 16, st));
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  rc = stiv_broad_phase(h, st, n_ves, p_dev, vert_off_dev, verts_dev, cand, w, w.ctr);
+  if (rc) return rc;
+  rc = stiv_narrow_phase(h, st, p_dev, vert_off_dev, verts_dev, cand, w, sms, p_max);
+  if (rc) return rc;
+  rc = stiv_contact_order(h, st, cand, out, w);
+  if (rc) return rc;
+  finalize_kernel<<<1, 32, 0, st>>>(w.ctr, w.C, counts_dev);
+  STIV_LAUNCH(h);
+  return STIV_OK;
+}
+
+extern "C" int stiv_sync_counts(void* stream, const int64_t* counts_dev, int64_t* counts_host) {
+  if (!counts_dev || !counts_host) return STIV_ERR_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return STIV_ERR_CUDA;
+  if (cudaMemcpy(counts_host, counts_dev, sizeof(int64_t) * STIV_NCOUNTS, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return STIV_ERR_CUDA;
+  int64_t f = counts_host[STIV_C_STATUS];
+  if (f & (STIV_F_PAIRS_OVERFLOW | STIV_F_CONTACTS_OVERFLOW | STIV_F_WORK_OVERFLOW)) return STIV_ERR_CAPACITY;
+  if (f & (STIV_F_BOX_TOO_SMALL | STIV_F_NONFINITE)) return STIV_ERR_INPUT;
+  return STIV_OK;
+}
+
+static int step_eager(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                      const int64_t* coef_off_dev, const double* coef_dev, const int64_t* vert_off_dev,
+                      void* verts_dev, const stiv_pairs* cand, const stiv_contacts* out, int64_t* counts_dev,
+                      double* Vc, double* Vp, double* grad, int32_t* gves, int32_t* gvid) {
+  int rc = stiv_upsample(h, stream, n_ves, p_max, p_dev, coef_off_dev, coef_dev, vert_off_dev, verts_dev);
+  if (rc) return rc;
+  rc = stiv_detect(h, stream, n_ves, p_max, p_dev, vert_off_dev, verts_dev, cand, out, counts_dev);
+  if (rc) return rc;
+  if (grad)
+    return stiv_stiv_grad(h, stream, n_ves, p_dev, vert_off_dev, verts_dev, cand, out, counts_dev, Vc, Vp, grad,
+                          gves, gvid);
+  return stiv_stiv(h, stream, n_ves, p_dev, vert_off_dev, verts_dev, cand, out, counts_dev, Vc, Vp);
+}
+
+extern "C" int stiv_step(stiv_handle* h, void* stream, int32_t use_graph, int32_t n_ves, int32_t p_max,
+                         const int32_t* p_dev, const int64_t* coef_off_dev, const double* coef_dev,
+                         const int64_t* vert_off_dev, void* verts_dev, const stiv_pairs* cand,
+                         const stiv_contacts* out, int64_t* counts_dev, double* V_contact_dev, double* V_pair_dev,
+                         double* grad_dev, int32_t* g_ves_dev, int32_t* g_vid_dev) {
+  if (!h || !cand || !out) return STIV_ERR_ARG;
+  if (!use_graph || !stream)
+    return step_eager(h, stream, n_ves, p_max, p_dev, coef_off_dev, coef_dev, vert_off_dev, verts_dev, cand, out,
+                      counts_dev, V_contact_dev, V_pair_dev, grad_dev, g_ves_dev, g_vid_dev);
+  // key of everything the captured launches depend on
+  unsigned long long key = 1469598103934665603ull;
+  auto mix = [&](unsigned long long x) { key = (key ^ x) * 1099511628211ull; };
+  const void* ptrs[] = {p_dev, coef_off_dev, coef_dev, vert_off_dev, verts_dev, cand->i, cand->j, cand->shift,
+                        out->pair, out->type, out->a, out->b, out->tau, out->w, counts_dev, V_contact_dev,
+                        V_pair_dev, grad_dev, g_ves_dev, g_vid_dev, stream};
+  for (const void* p : ptrs) mix((unsigned long long)(uintptr_t)p);
+  mix((unsigned long long)n_ves); mix((unsigned long long)p_max);
+  mix((unsigned long long)cand->capacity); mix((unsigned long long)out->capacity);
+  if (h->graph_exec && key == h->graph_key) {
+    STIV_CUDA(h, cudaGraphLaunch(h->graph_exec, (cudaStream_t)stream));
+    return STIV_OK;
+  }
+  // first call with these arguments: run eagerly (allocates tables and scratch), then capture
+  int rc = step_eager(h, stream, n_ves, p_max, p_dev, coef_off_dev, coef_dev, vert_off_dev, verts_dev, cand, out,
+                      counts_dev, V_contact_dev, V_pair_dev, grad_dev, g_ves_dev, g_vid_dev);
+  if (rc) return rc;
+  if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+  cudaStream_t st = (cudaStream_t)stream;
+  STIV_CUDA(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  void* ws_before = h->ws;
+  rc = step_eager(h, stream, n_ves, p_max, p_dev, coef_off_dev, coef_dev, vert_off_dev, verts_dev, cand, out,
+                  counts_dev, V_contact_dev, V_pair_dev, grad_dev, g_ves_dev, g_vid_dev);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+  if (e != cudaSuccess || h->ws != ws_before) {
+    if (graph) cudaGraphDestroy(graph);
+    h->last_cuda_error = (int)e;
+    return STIV_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) { h->graph_exec = nullptr; h->last_cuda_error = (int)e; return STIV_ERR_CUDA; }
+  h->graph_key = key;
+  return STIV_OK;
+}

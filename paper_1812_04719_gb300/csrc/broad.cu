@@ -1,0 +1,330 @@
+// Space-time bounding boxes (Alg. 2 getBoundingBox) and the bounding-box
+// intersection of Alg. 1 (Sec. 3.3.1) on one GPU.
+//
+//   1. vesicle boxes: exact FP64 min/max of X0 and X1 over all vertices, padded
+//      by d_m; patch boxes (4 x 8 grid quads and their vertices) in FP32,
+//      rounded outward, for the narrow phase;
+//   2. h_m = mean box diagonal (Alg. 1 line 1), cell size of a uniform grid
+//      (periodic axes: L / floor(L / h_m));
+//   3. each box lists the cells it overlaps (an exact cell-range enumeration
+//      standing in for the check points of Alg. 1 line 2), keyed by the
+//      Morton id of the (wrapped) cell;
+//   4. stable radix sort by Morton id (Alg. 1 line 4);
+//   5. all box pairs within a cell: the image shift follows from the unwrapped
+//      cell coordinates, then bbiCheck in FP64 (Alg. 1 lines 5-9);
+//   6. sort + unique (Alg. 1 line 11) -> pairs (i < j, shift), ascending.
+#include "stiv_internal.cuh"
+
+#include <math.h>
+
+namespace {
+
+__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
+
+template <typename T>
+__device__ __forceinline__ double ld(const void* p, size_t i) { return (double)((const T*)p)[i]; }
+
+__device__ __forceinline__ double vload(const void* X, int mixed, size_t i) {
+  return mixed ? (double)((const float*)X)[i] : ((const double*)X)[i];
+}
+
+// One CTA per vesicle.
+__global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, const int64_t* voff, const void* X,
+                                                    int mixed, double dm, double Lx, double Ly, double Lz,
+                                                    double* vbox, float* pbox, int64_t* ctr) {
+  int v = blockIdx.x;
+  int P = 2 * pv[v], nv = stiv_nverts(P);
+  const size_t base = voff[v];
+  __shared__ double red[6][256];
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  bool bad = false;
+  for (int k = threadIdx.x; k < nv; k += blockDim.x)
+    for (int t = 0; t < 2; ++t)
+      for (int c = 0; c < 3; ++c) {
+        double x = vload(X, mixed, base + (size_t)(t * 3 + c) * nv + k);
+        if (!finite_d(x)) bad = true;
+        lo[c] = fmin(lo[c], x);
+        hi[c] = fmax(hi[c], x);
+      }
+  for (int c = 0; c < 3; ++c) { red[c][threadIdx.x] = lo[c]; red[3 + c][threadIdx.x] = hi[c]; }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_NONFINITE);
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int c = 0; c < 3; ++c) {
+        red[c][threadIdx.x] = fmin(red[c][threadIdx.x], red[c][threadIdx.x + s]);
+        red[3 + c][threadIdx.x] = fmax(red[3 + c][threadIdx.x], red[3 + c][threadIdx.x + s]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) {
+    int c = threadIdx.x;
+    double l = red[c][0] - dm, u = red[3 + c][0] + dm;
+    vbox[6 * v + c] = l;
+    vbox[6 * v + 3 + c] = u;
+    double L = c == 0 ? Lx : c == 1 ? Ly : Lz;
+    if (L > 0.0 && !(u - l < 0.5 * L)) atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_BOX_TOO_SMALL);
+  }
+  // patch boxes: vertex rows [I*BR, min(I*BR+BR, P)], columns [J*BC, J*BC+ncol] (wrapping), poles
+  int nbr = stiv_nband_blocks(P), nbc = stiv_ncol_blocks(P), W = 2 * P;
+  for (int patch = threadIdx.x; patch < nbr * nbc; patch += blockDim.x) {
+    int I = patch / nbc, J = patch % nbc;
+    int r0 = I * STIV_BR, r1 = min(r0 + STIV_BR, P);
+    int c0 = J * STIV_BC, nc = min(STIV_BC, W - c0);
+    double plo[3] = {INFINITY, INFINITY, INFINITY}, phi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int r = r0; r <= r1; ++r)
+      for (int cc = 0; cc <= nc; ++cc) {
+        int col = c0 + cc; if (col >= W) col -= W;
+        int vid = r * W + col;
+        for (int t = 0; t < 2; ++t)
+          for (int c = 0; c < 3; ++c) {
+            double x = vload(X, mixed, base + (size_t)(t * 3 + c) * nv + vid);
+            plo[c] = fmin(plo[c], x); phi[c] = fmax(phi[c], x);
+          }
+      }
+    for (int pole = 0; pole < 2; ++pole) {
+      if ((pole == 0 && I != 0) || (pole == 1 && I != nbr - 1)) continue;
+      int vid = W * (P + 1) + pole;
+      for (int t = 0; t < 2; ++t)
+        for (int c = 0; c < 3; ++c) {
+          double x = vload(X, mixed, base + (size_t)(t * 3 + c) * nv + vid);
+          plo[c] = fmin(plo[c], x); phi[c] = fmax(phi[c], x);
+        }
+    }
+    float* B = pbox + ((size_t)v * STIV_MAX_PATCH + patch) * 6;
+    for (int c = 0; c < 3; ++c) { B[c] = __double2float_rd(plo[c]); B[3 + c] = __double2float_ru(phi[c]); }
+  }
+}
+
+// grid[0..2] origin, [3..5] cell size, [6..8] cells per axis, [9..11] periodic flag, [12] h_m
+__global__ void __launch_bounds__(1024) grid_kernel(int n, const double* vbox, double Lx, double Ly, double Lz,
+                                                    double* grid) {
+  __shared__ double sdiag[1024], slo[3][1024], shi[3][1024];
+  double d = 0.0, lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int v = threadIdx.x; v < n; v += 1024) {
+    double e0 = vbox[6 * v + 3] - vbox[6 * v], e1 = vbox[6 * v + 4] - vbox[6 * v + 1], e2 = vbox[6 * v + 5] - vbox[6 * v + 2];
+    d += sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+    for (int c = 0; c < 3; ++c) { lo[c] = fmin(lo[c], vbox[6 * v + c]); hi[c] = fmax(hi[c], vbox[6 * v + 3 + c]); }
+  }
+  sdiag[threadIdx.x] = d;
+  for (int c = 0; c < 3; ++c) { slo[c][threadIdx.x] = lo[c]; shi[c][threadIdx.x] = hi[c]; }
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sdiag[threadIdx.x] += sdiag[threadIdx.x + s];
+      for (int c = 0; c < 3; ++c) {
+        slo[c][threadIdx.x] = fmin(slo[c][threadIdx.x], slo[c][threadIdx.x + s]);
+        shi[c][threadIdx.x] = fmax(shi[c][threadIdx.x], shi[c][threadIdx.x + s]);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double hm = sdiag[0] / n;
+    if (!(hm > 0.0)) hm = 1.0;
+    double L[3] = {Lx, Ly, Lz};
+    for (int c = 0; c < 3; ++c) {
+      if (L[c] > 0.0) {
+        double G = floor(L[c] / hm);
+        if (G < 1.0) G = 1.0;
+        if (G > 256.0) G = 256.0;
+        grid[c] = 0.0; grid[3 + c] = L[c] / G; grid[6 + c] = G; grid[9 + c] = 1.0;
+      } else {
+        double ext = shi[c][0] - slo[c][0];
+        double h = hm;
+        if (ext / h > 255.0) h = ext / 255.0;
+        grid[c] = slo[c][0]; grid[3 + c] = h; grid[6 + c] = floor(ext / h) + 1.0; grid[9 + c] = 0.0;
+      }
+    }
+    grid[12] = hm;
+  }
+}
+
+__device__ __forceinline__ void cell_range(const double* grid, const double* box, int c, int& u0, int& u1) {
+  double o = grid[c], h = grid[3 + c];
+  const double slack = 1e-6;  // cells; covers rounding of the divisions
+  u0 = (int)floor((box[c] - o) / h - slack);
+  u1 = (int)floor((box[3 + c] - o) / h + slack);
+  if (grid[9 + c] == 0.0) {  // free axis: clamp to the grid
+    int G = (int)grid[6 + c];
+    u0 = max(0, min(u0, G - 1));
+    u1 = max(0, min(u1, G - 1));
+  }
+  u0 = max(u0, -500); u1 = min(u1, 500);
+}
+
+__global__ void cell_count_kernel(int n, const double* vbox, const double* grid, int32_t* cnt) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  int c = 1;
+  for (int a = 0; a < 3; ++a) { int u0, u1; cell_range(grid, vbox + 6 * v, a, u0, u1); c *= (u1 - u0 + 1); }
+  cnt[v] = c;
+}
+
+// Exclusive scan of n+1 ints (last = total), one CTA.
+__global__ void __launch_bounds__(1024) scan1_kernel(const int32_t* in, int n, int32_t* out) {
+  __shared__ int32_t part[1024];
+  int per = (n + 1023) / 1024;
+  int lo = threadIdx.x * per, hi = min(lo + per, n);
+  int32_t s = 0;
+  for (int i = lo; i < hi; ++i) s += in[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int i = lo; i < hi; ++i) { out[i] = run; run += in[i]; }
+  if (threadIdx.x == 1023) out[n] = part[1023];
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t x) {
+  x &= 0x3FF;
+  x = (x | (x << 16)) & 0x030000FF;
+  x = (x | (x << 8)) & 0x0300F00F;
+  x = (x | (x << 4)) & 0x030C30C3;
+  x = (x | (x << 2)) & 0x09249249;
+  return x;
+}
+
+__global__ void cell_emit_kernel(int n, const double* vbox, const double* grid, const int32_t* off, int64_t R,
+                                 uint64_t* key, int32_t* val, int32_t* rbox, int32_t* rcell, int64_t* ctr) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  int lo[3], hi[3], G[3];
+  for (int a = 0; a < 3; ++a) { cell_range(grid, vbox + 6 * v, a, lo[a], hi[a]); G[a] = (int)grid[6 + a]; }
+  int64_t r = off[v];
+  if (v == n - 1) ctr[8] = off[n];
+  for (int x = lo[0]; x <= hi[0]; ++x)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int z = lo[2]; z <= hi[2]; ++z, ++r) {
+        if (r >= R) { atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_WORK_OVERFLOW); return; }
+        int w[3] = {x, y, z};
+        for (int a = 0; a < 3; ++a) w[a] = ((w[a] % G[a]) + G[a]) % G[a];
+        key[r] = spread10(w[0]) | (spread10(w[1]) << 1) | (spread10(w[2]) << 2);
+        val[r] = (int32_t)r;
+        rbox[r] = v;
+        rcell[r] = (x + 512) | ((y + 512) << 10) | ((z + 512) << 20);
+      }
+}
+
+__device__ __forceinline__ bool bbi(const double* a, const double* b) {
+  return a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] && b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
+}
+
+// Alg. 1 lines 5-9: every record against the later records of its cell.
+__global__ void cell_pairs_kernel(const int64_t* nrec_dev, int64_t R, const uint64_t* key, const int32_t* val,
+                                  const int32_t* rbox, const int32_t* rcell, const double* vbox,
+                                  const double* grid, double Lx, double Ly, double Lz, int64_t Q,
+                                  uint64_t* pkey, int32_t* pval, int64_t* ctr) {
+  int64_t nrec = *nrec_dev; if (nrec > R) nrec = R;
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nrec) return;
+  double L[3] = {Lx, Ly, Lz};
+  int G[3] = {(int)grid[6], (int)grid[7], (int)grid[8]};
+  int ra = val[k];
+  int ba = rbox[ra], ca = rcell[ra];
+  for (int64_t q = k + 1; q < nrec && key[q] == key[k]; ++q) {
+    int rb = val[q];
+    int bb = rbox[rb], cb = rcell[rb];
+    if (bb == ba) continue;
+    int s[3];
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+      int du = ((ca >> (10 * a)) & 0x3FF) - ((cb >> (10 * a)) & 0x3FF);
+      if (L[a] > 0.0) {
+        s[a] = du / G[a];
+        if (s[a] * G[a] != du || s[a] < -1 || s[a] > 1) ok = false;
+      } else {
+        s[a] = 0;
+        if (du != 0) ok = false;
+      }
+    }
+    if (!ok) continue;
+    int i = ba, j = bb;
+    if (i > j) { i = bb; j = ba; s[0] = -s[0]; s[1] = -s[1]; s[2] = -s[2]; }
+    double bj[6];
+    for (int a = 0; a < 3; ++a) {
+      bj[a] = vbox[6 * j + a]; bj[3 + a] = vbox[6 * j + 3 + a];
+      if (s[a] != 0) { double sh = s[a] * L[a]; bj[a] = bj[a] + sh; bj[3 + a] = bj[3 + a] + sh; }
+    }
+    if (!bbi(vbox + 6 * i, bj)) continue;
+    int code = 9 * (s[0] + 1) + 3 * (s[1] + 1) + (s[2] + 1);
+    unsigned long long slot = atomicAdd((unsigned long long*)&ctr[9], 1ull);
+    if ((int64_t)slot < Q) {
+      pkey[slot] = ((uint64_t)i << 29) | ((uint64_t)j << 5) | (uint64_t)code;
+      pval[slot] = 0;
+    } else {
+      atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_WORK_OVERFLOW);
+    }
+  }
+}
+
+// Alg. 1 line 11: unique sorted keys -> output pair list; one CTA.
+__global__ void __launch_bounds__(1024) unique_pairs_kernel(const int64_t* nkey_dev, int64_t Q, const uint64_t* key,
+                                                            int64_t cap, int32_t* oi, int32_t* oj, int32_t* os,
+                                                            int64_t* ctr) {
+  __shared__ int32_t part[1024];
+  int64_t n = *nkey_dev; if (n > Q) n = Q;
+  int64_t per = (n + 1023) / 1024;
+  int64_t lo = threadIdx.x * per, hi = lo + per < n ? lo + per : n;
+  int32_t c = 0;
+  for (int64_t k = lo; k < hi; ++k) c += (k == 0 || key[k] != key[k - 1]);
+  part[threadIdx.x] = c;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int64_t k = lo; k < hi; ++k) {
+    if (k == 0 || key[k] != key[k - 1]) {
+      if (run < cap) {
+        uint64_t x = key[k];
+        oi[run] = (int32_t)(x >> 29);
+        oj[run] = (int32_t)((x >> 5) & 0xFFFFFF);
+        os[run] = (int32_t)(x & 31);
+      }
+      ++run;
+    }
+  }
+  if (threadIdx.x == 1023) {
+    int64_t total = part[1023];
+    ctr[STIV_C_PAIRS] = total;
+    if (total > cap) atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_PAIRS_OVERFLOW);
+  }
+}
+
+}  // namespace
+
+// Host side of steps 1-6.  ws: scratch views prepared by the caller.
+int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, const int32_t* p_dev, const int64_t* voff,
+                     const void* X, const stiv_pairs* cand, detect_ws& w, int64_t* ctr) {
+  int mixed = h->prm.precision == STIV_MIXED;
+  const double* L = h->prm.box_L;
+  boxes_kernel<<<n, 256, 0, st>>>(n, p_dev, voff, X, mixed, h->prm.d_m, L[0], L[1], L[2], w.vbox, w.pbox, ctr);
+  grid_kernel<<<1, 1024, 0, st>>>(n, w.vbox, L[0], L[1], L[2], w.grid);
+  cell_count_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, w.vbox, w.grid, w.cell_count);
+  scan1_kernel<<<1, 1024, 0, st>>>(w.cell_count, n, w.cell_off);
+  cell_emit_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, w.vbox, w.grid, w.cell_off, w.R, w.rec_key, w.rec_val,
+                                                    w.rec_box, w.rec_cell, ctr);
+  STIV_LAUNCH(h);
+  // records: ctr[8] = count; sort by Morton id (30 bits)
+  int rc = stiv_sort_pairs_impl(st, w.R, 30, w.rec_key, w.rec_val, w.rec_key2, w.rec_val2, w.sort_scratch,
+                                w.sort_scratch_bytes, &ctr[8]);
+  if (rc) return rc;
+  cell_pairs_kernel<<<(unsigned)((w.R + 127) / 128), 128, 0, st>>>(&ctr[8], w.R, w.rec_key2, w.rec_val2, w.rec_box,
+                                                                   w.rec_cell, w.vbox, w.grid, L[0], L[1], L[2],
+                                                                   w.Q, w.pkey, w.pval, ctr);
+  STIV_LAUNCH(h);
+  rc = stiv_sort_pairs_impl(st, w.Q, 53, w.pkey, w.pval, w.pkey2, w.pval2, w.sort_scratch, w.sort_scratch_bytes,
+                            &ctr[9]);
+  if (rc) return rc;
+  unique_pairs_kernel<<<1, 1024, 0, st>>>(&ctr[9], w.Q, w.pkey2, cand->capacity, cand->i, cand->j, cand->shift, ctr);
+  STIV_LAUNCH(h);
+  return STIV_OK;
+}

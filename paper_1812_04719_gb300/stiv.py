@@ -1,0 +1,346 @@
+"""Python binding of libstiv (the C-ABI in include/stiv.h).
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of
+libstiv.so.  PyTorch supplies device memory and streams.  If the library is
+missing this module raises at import time of ``lib()``; there is no CPU path.
+
+Low level: ``stiv_create``, ``stiv_upsample``, ``stiv_detect``, ``stiv_stiv``,
+``stiv_stiv_grad``, ``stiv_grad_scatter``, ``stiv_grad_to_coef``, ``stiv_step``,
+``stiv_sync_counts``, ``stiv_mesh_topology``, ``stiv_sort_pairs`` take raw
+device pointers (ints) like the C functions.  High level: ``Stiv`` runs the
+per-step path of Alg. 2 (upsample, detect, volumes and gradient) on a scene
+held in device tensors and grows its output buffers when the kernels report
+an overflow.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstiv.so")
+
+STIV_OK, STIV_ERR_ARG, STIV_ERR_CAPACITY, STIV_ERR_TIMEOUT, STIV_ERR_CUDA, STIV_ERR_INPUT = range(6)
+STIV_FP64, STIV_MIXED = 0, 1
+C_PAIRS, C_PRIM, C_VF, C_EE, C_CPAIRS, C_DEGEN, C_STATUS, C_PATCH = range(8)
+NCOUNTS = 8
+F_PAIRS_OVERFLOW, F_CONTACTS_OVERFLOW, F_BOX_TOO_SMALL, F_NONFINITE, F_WORK_OVERFLOW = 1, 2, 4, 8, 16
+
+EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_error", "stiv_mesh_topology",
+           "stiv_upsample", "stiv_detect", "stiv_stiv", "stiv_stiv_grad", "stiv_grad_scatter",
+           "stiv_grad_to_coef", "stiv_step", "stiv_sync_counts", "stiv_sort_scratch_bytes", "stiv_sort_pairs"]
+
+
+class StivError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})" if what else status_string(status))
+
+
+class StivParams(ctypes.Structure):
+    _fields_ = [("d_m", ctypes.c_double), ("eps", ctypes.c_double), ("dt", ctypes.c_double),
+                ("box_L", ctypes.c_double * 3), ("precision", ctypes.c_int32), ("include_ee", ctypes.c_int32)]
+
+
+class StivPairs(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("i", ctypes.c_void_p), ("j", ctypes.c_void_p),
+                ("shift", ctypes.c_void_p)]
+
+
+class StivContacts(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("pair", ctypes.c_void_p), ("type", ctypes.c_void_p),
+                ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("tau", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libstiv.so (built by ``paper_1812_04719_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libstiv.so not found at {LIB_PATH}: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER
+    L.stiv_create.argtypes = [P(vp), P(StivParams)]
+    L.stiv_destroy.argtypes = [vp]
+    L.stiv_status_string.argtypes = [ctypes.c_int]
+    L.stiv_status_string.restype = ctypes.c_char_p
+    L.stiv_last_cuda_error.argtypes = [vp]
+    L.stiv_mesh_topology.argtypes = [i32, vp, vp, vp]
+    L.stiv_upsample.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp]
+    L.stiv_detect.argtypes = [vp, vp, i32, i32, vp, vp, vp, P(StivPairs), P(StivContacts), vp]
+    L.stiv_stiv.argtypes = [vp, vp, i32, vp, vp, vp, P(StivPairs), P(StivContacts), vp, vp, vp]
+    L.stiv_stiv_grad.argtypes = [vp, vp, i32, vp, vp, vp, P(StivPairs), P(StivContacts), vp, vp, vp, vp, vp, vp]
+    L.stiv_grad_scatter.argtypes = [vp, vp, vp, P(StivContacts), vp, vp, vp, vp, vp, vp, vp]
+    L.stiv_grad_to_coef.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp]
+    L.stiv_step.argtypes = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, P(StivPairs), P(StivContacts), vp, vp, vp,
+                            vp, vp, vp]
+    L.stiv_sync_counts.argtypes = [vp, vp, vp]
+    L.stiv_sort_scratch_bytes.argtypes = [i64]
+    L.stiv_sort_scratch_bytes.restype = ctypes.c_size_t
+    L.stiv_sort_pairs.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, ctypes.c_size_t]
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().stiv_status_string(int(s)).decode()
+    except Exception:
+        return f"status {s}"
+
+
+def _check(rc: int, what: str):
+    if rc != STIV_OK:
+        raise StivError(rc, what)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# low-level: same names as the C entry points, raw pointers
+# ---------------------------------------------------------------------------
+
+def stiv_create(d_m=0.0, eps=1.0, dt=0.1, box_L=(0.0, 0.0, 0.0), precision=STIV_FP64, include_ee=True) -> int:
+    prm = StivParams(float(d_m), float(eps), float(dt), (ctypes.c_double * 3)(*[float(x) for x in box_L]),
+                     int(precision), int(bool(include_ee)))
+    h = ctypes.c_void_p()
+    _check(lib().stiv_create(ctypes.byref(h), ctypes.byref(prm)), "stiv_create")
+    return h.value
+
+
+def stiv_destroy(h: int):
+    _check(lib().stiv_destroy(h), "stiv_destroy")
+
+
+def stiv_mesh_topology(P: int, tri_ptr: int, edge_ptr: int, stream: int):
+    _check(lib().stiv_mesh_topology(P, tri_ptr, edge_ptr, stream), "stiv_mesh_topology")
+
+
+def stiv_upsample(h, stream, n_ves, p_max, p_ptr, coef_off_ptr, coef_ptr, vert_off_ptr, verts_ptr):
+    _check(lib().stiv_upsample(h, stream, n_ves, p_max, p_ptr, coef_off_ptr, coef_ptr, vert_off_ptr, verts_ptr),
+           "stiv_upsample")
+
+
+def stiv_detect(h, stream, n_ves, p_max, p_ptr, vert_off_ptr, verts_ptr, cand: StivPairs, out: StivContacts,
+                counts_ptr):
+    _check(lib().stiv_detect(h, stream, n_ves, p_max, p_ptr, vert_off_ptr, verts_ptr, ctypes.byref(cand),
+                             ctypes.byref(out), counts_ptr), "stiv_detect")
+
+
+def stiv_stiv(h, stream, n_ves, p_ptr, vert_off_ptr, verts_ptr, cand, contacts, counts_ptr, Vc_ptr, Vp_ptr):
+    _check(lib().stiv_stiv(h, stream, n_ves, p_ptr, vert_off_ptr, verts_ptr, ctypes.byref(cand),
+                           ctypes.byref(contacts), counts_ptr, Vc_ptr, Vp_ptr), "stiv_stiv")
+
+
+def stiv_stiv_grad(h, stream, n_ves, p_ptr, vert_off_ptr, verts_ptr, cand, contacts, counts_ptr, Vc_ptr, Vp_ptr,
+                   grad_ptr, gves_ptr, gvid_ptr):
+    _check(lib().stiv_stiv_grad(h, stream, n_ves, p_ptr, vert_off_ptr, verts_ptr, ctypes.byref(cand),
+                                ctypes.byref(contacts), counts_ptr, Vc_ptr, Vp_ptr, grad_ptr, gves_ptr, gvid_ptr),
+           "stiv_stiv_grad")
+
+
+def stiv_grad_scatter(h, stream, p_ptr, contacts, counts_ptr, wpair_ptr, grad_ptr, gves_ptr, gvid_ptr,
+                      vert_off_ptr, gX_ptr):
+    _check(lib().stiv_grad_scatter(h, stream, p_ptr, ctypes.byref(contacts), counts_ptr, wpair_ptr, grad_ptr,
+                                   gves_ptr, gvid_ptr, vert_off_ptr, gX_ptr), "stiv_grad_scatter")
+
+
+def stiv_grad_to_coef(h, stream, n_ves, p_max, p_ptr, coef_off_ptr, vert_off_ptr, gX_ptr, gcoef_ptr):
+    _check(lib().stiv_grad_to_coef(h, stream, n_ves, p_max, p_ptr, coef_off_ptr, vert_off_ptr, gX_ptr, gcoef_ptr),
+           "stiv_grad_to_coef")
+
+
+def stiv_step(h, stream, use_graph, n_ves, p_max, p_ptr, coef_off_ptr, coef_ptr, vert_off_ptr, verts_ptr, cand,
+              out, counts_ptr, Vc_ptr, Vp_ptr, grad_ptr, gves_ptr, gvid_ptr):
+    _check(lib().stiv_step(h, stream, int(use_graph), n_ves, p_max, p_ptr, coef_off_ptr, coef_ptr, vert_off_ptr,
+                           verts_ptr, ctypes.byref(cand), ctypes.byref(out), counts_ptr, Vc_ptr, Vp_ptr, grad_ptr,
+                           gves_ptr, gvid_ptr), "stiv_step")
+
+
+def stiv_sync_counts(stream, counts_ptr):
+    host = np.zeros(NCOUNTS, dtype=np.int64)
+    rc = lib().stiv_sync_counts(stream, counts_ptr, host.ctypes.data)
+    return rc, host
+
+
+def stiv_sort_pairs(stream, n, key_bits, keys_in_ptr, vals_in_ptr, keys_out_ptr, vals_out_ptr, scratch_ptr,
+                    scratch_bytes):
+    _check(lib().stiv_sort_pairs(stream, n, key_bits, keys_in_ptr, vals_in_ptr, keys_out_ptr, vals_out_ptr,
+                                 scratch_ptr, scratch_bytes), "stiv_sort_pairs")
+
+
+def stiv_sort_scratch_bytes(n: int) -> int:
+    return int(lib().stiv_sort_scratch_bytes(int(n)))
+
+
+# ---------------------------------------------------------------------------
+# high level
+# ---------------------------------------------------------------------------
+
+def nverts(P: int) -> int:
+    return 2 * P * (P + 1) + 2
+
+
+@dataclass
+class DeviceScene:
+    """Scene inputs resident on the device, in the library's layouts."""
+    n: int
+    p_max: int
+    p: torch.Tensor          # int32 [N]
+    coef_off: torch.Tensor   # int64 [N]
+    coef: torch.Tensor       # float64 flat
+    vert_off: torch.Tensor   # int64 [N]
+    verts: torch.Tensor      # float64 or float32 flat
+    box_L: tuple
+    eps: float
+    dt: float
+    d_m: float
+
+    @staticmethod
+    def from_scene(sc, precision=STIV_FP64, device="cuda") -> "DeviceScene":
+        dt = torch.float32 if precision == STIV_MIXED else torch.float64
+        vo = sc.vert_off()
+        return DeviceScene(
+            n=sc.n, p_max=int(sc.p.max()),
+            p=torch.as_tensor(sc.p, dtype=torch.int32, device=device),
+            coef_off=torch.as_tensor(sc.coef_off, dtype=torch.int64, device=device),
+            coef=torch.as_tensor(sc.coef, dtype=torch.float64, device=device),
+            vert_off=torch.as_tensor(vo, dtype=torch.int64, device=device),
+            verts=torch.zeros(sc.n_vert_values(), dtype=dt, device=device),
+            box_L=tuple(float(x) for x in sc.L), eps=float(sc.eps), dt=float(sc.dt), d_m=float(sc.d_m))
+
+
+class Buffers:
+    """Output buffers of one step, sized by capacities."""
+
+    def __init__(self, device, pair_cap: int, contact_cap: int, grad: bool):
+        self.pair_cap, self.contact_cap = int(pair_cap), int(contact_cap)
+        i32 = dict(dtype=torch.int32, device=device)
+        f64 = dict(dtype=torch.float64, device=device)
+        self.ci = torch.zeros(self.pair_cap, **i32)
+        self.cj = torch.zeros(self.pair_cap, **i32)
+        self.cs = torch.zeros(self.pair_cap, **i32)
+        self.pair = torch.zeros(self.contact_cap, **i32)
+        self.type = torch.zeros(self.contact_cap, **i32)
+        self.a = torch.zeros(self.contact_cap, **i32)
+        self.b = torch.zeros(self.contact_cap, **i32)
+        self.tau = torch.zeros(self.contact_cap, **f64)
+        self.w = torch.zeros(self.contact_cap, 2, **f64)
+        self.counts = torch.zeros(NCOUNTS, dtype=torch.int64, device=device)
+        self.Vc = torch.zeros(self.contact_cap, **f64)
+        self.Vp = torch.zeros(self.pair_cap, **f64)
+        self.grad = torch.zeros(self.contact_cap, 4, 3, **f64) if grad else None
+        self.gves = torch.zeros(self.contact_cap, 4, **i32) if grad else None
+        self.gvid = torch.zeros(self.contact_cap, 4, **i32) if grad else None
+
+    def pairs_struct(self) -> StivPairs:
+        return StivPairs(self.pair_cap, _ptr(self.ci), _ptr(self.cj), _ptr(self.cs))
+
+    def contacts_struct(self) -> StivContacts:
+        return StivContacts(self.contact_cap, _ptr(self.pair), _ptr(self.type), _ptr(self.a), _ptr(self.b),
+                            _ptr(self.tau), _ptr(self.w))
+
+
+class Stiv:
+    """One library handle plus the buffers of the per-step path."""
+
+    def __init__(self, box_L=(0.0, 0.0, 0.0), eps=1.0, dt=0.1, d_m=0.0, precision=STIV_FP64, include_ee=True,
+                 pair_cap=1024, contact_cap=1 << 16, device="cuda"):
+        self.precision = precision
+        self.device = torch.device(device)
+        self.h = stiv_create(d_m=d_m, eps=eps, dt=dt, box_L=box_L, precision=precision, include_ee=include_ee)
+        self.pair_cap, self.contact_cap = pair_cap, contact_cap
+        self.buf = None
+
+    @staticmethod
+    def for_scene(sc, precision=STIV_FP64, **kw) -> "Stiv":
+        return Stiv(box_L=tuple(sc.L), eps=sc.eps, dt=sc.dt, d_m=sc.d_m, precision=precision, **kw)
+
+    def close(self):
+        if self.h:
+            stiv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _buffers(self, grad: bool) -> Buffers:
+        b = self.buf
+        if b is None or b.pair_cap != self.pair_cap or b.contact_cap != self.contact_cap or (grad and b.grad is None):
+            self.buf = Buffers(self.device, self.pair_cap, self.contact_cap, grad)
+        return self.buf
+
+    def upsample(self, ds: DeviceScene, stream=None):
+        stiv_upsample(self.h, _stream(stream), ds.n, ds.p_max, _ptr(ds.p), _ptr(ds.coef_off), _ptr(ds.coef),
+                      _ptr(ds.vert_off), _ptr(ds.verts))
+
+    def step(self, ds: DeviceScene, grad: bool = True, upsample: bool = True, use_graph: bool = False,
+             stream=None, max_retries: int = 8) -> dict:
+        """upsample (optional) + detect + V (+ dV/dX1).  Returns host counts and
+        device views of the outputs trimmed to their counts."""
+        st = _stream(stream)
+        for _ in range(max_retries):
+            b = self._buffers(grad)
+            cand, out = b.pairs_struct(), b.contacts_struct()
+            if upsample:
+                stiv_step(self.h, st, use_graph, ds.n, ds.p_max, _ptr(ds.p), _ptr(ds.coef_off), _ptr(ds.coef),
+                          _ptr(ds.vert_off), _ptr(ds.verts), cand, out, _ptr(b.counts), _ptr(b.Vc), _ptr(b.Vp),
+                          _ptr(b.grad) if grad else 0, _ptr(b.gves) if grad else 0, _ptr(b.gvid) if grad else 0)
+            else:
+                stiv_detect(self.h, st, ds.n, ds.p_max, _ptr(ds.p), _ptr(ds.vert_off), _ptr(ds.verts), cand, out,
+                            _ptr(b.counts))
+                if grad:
+                    stiv_stiv_grad(self.h, st, ds.n, _ptr(ds.p), _ptr(ds.vert_off), _ptr(ds.verts), cand, out,
+                                   _ptr(b.counts), _ptr(b.Vc), _ptr(b.Vp), _ptr(b.grad), _ptr(b.gves), _ptr(b.gvid))
+                else:
+                    stiv_stiv(self.h, st, ds.n, _ptr(ds.p), _ptr(ds.vert_off), _ptr(ds.verts), cand, out,
+                              _ptr(b.counts), _ptr(b.Vc), _ptr(b.Vp))
+            rc, counts = stiv_sync_counts(st, _ptr(b.counts))
+            if rc == STIV_ERR_CAPACITY:
+                f = int(counts[C_STATUS])
+                if f & F_PAIRS_OVERFLOW or f & F_WORK_OVERFLOW:
+                    self.pair_cap = max(2 * self.pair_cap, int(counts[C_PAIRS]) + 16)
+                if f & F_CONTACTS_OVERFLOW:
+                    self.contact_cap = max(2 * self.contact_cap, int(counts[C_VF] + counts[C_EE]) + 16)
+                continue
+            _check(rc, "step")
+            return self.result(counts, grad)
+        raise StivError(STIV_ERR_CAPACITY, "step: capacities kept overflowing")
+
+    def result(self, counts, grad: bool) -> dict:
+        b = self.buf
+        npairs = int(counts[C_PAIRS])
+        nc = int(counts[C_VF] + counts[C_EE])
+        r = dict(counts=counts, i=b.ci[:npairs], j=b.cj[:npairs], shift=b.cs[:npairs], pair=b.pair[:nc],
+                 type=b.type[:nc], a=b.a[:nc], b=b.b[:nc], tau=b.tau[:nc], w=b.w[:nc], V=b.Vc[:nc],
+                 V_pair=b.Vp[:npairs])
+        if grad:
+            r.update(grad=b.grad[:nc], gves=b.gves[:nc], gvid=b.gvid[:nc])
+        return r
+
+
+def shift_vec(code):
+    """shift code 9(sx+1) + 3(sy+1) + (sz+1) -> (sx, sy, sz) (numpy, vectorised)."""
+    code = np.asarray(code)
+    return np.stack([code // 9 - 1, (code // 3) % 3 - 1, code % 3 - 1], axis=-1)

@@ -1,0 +1,32 @@
+"""Test helper: run the CUDA path through the C-ABI binding and bring results
+to the host as numpy arrays.  Test infrastructure only."""
+import numpy as np
+import torch
+
+from paper_1812_04719_gb300 import stiv as S
+
+
+def run_gpu(sc, precision=S.STIV_FP64, grad=True, use_graph=False, include_ee=True, pair_cap=256,
+            contact_cap=4096, eng=None):
+    eng = eng or S.Stiv.for_scene(sc, precision=precision, include_ee=include_ee, pair_cap=pair_cap,
+                                  contact_cap=contact_cap)
+    ds = S.DeviceScene.from_scene(sc, precision=precision)
+    r = eng.step(ds, grad=grad, use_graph=use_graph)
+    torch.cuda.synchronize()
+    out = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
+    out["verts"] = ds.verts.double().cpu().numpy()
+    out["eng"] = eng
+    out["ds"] = ds
+    return out
+
+
+def verts_list(sc, flat):
+    """Flat vertex array -> list of [2][3][n_v] arrays (FP64)."""
+    offs = sc.vert_off()
+    sizes = sc.vert_sizes()
+    return [flat[o:o + s].reshape(2, 3, -1).astype(np.float64) for o, s in zip(offs, sizes)]
+
+
+def gpu_pairs_rows(g):
+    sv = S.shift_vec(g["shift"])
+    return np.concatenate([g["i"][:, None], g["j"][:, None], sv], axis=1).astype(np.int32)
