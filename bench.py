@@ -1,0 +1,389 @@
+"""Benchmark of the per-step contact path on the 1440-vesicle workload.
+
+One step = the whole hot path on one synthetic scene resident in HBM:
+SH upsampling of X0 and X1 (p = 16 -> 32), space-time boxes, candidate
+vesicle pairs (Morton grid), vertex-triangle and edge-edge contact tests,
+contact volumes V and dV/dX1, and the adjoint of dV/dX1 back to the SH
+coefficients.  Workload: 1440 prolate vesicles (reduced volume 0.91,
+R0 = 1.34) at 58% volume fraction on a staggered lattice in a periodic cube,
+step tuned to ~2 interfering neighbours per vesicle.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+       python bench.py --impl reference ...   (the CPU oracle on a bounded sample)
+Under torchrun (N > 1) every rank runs its own scene (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_PEAK_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor), nominal
+METRIC = "vesicle-steps/s of detect+V+∇V at p=16→32, 58% vf; % of roofline vs FP64 form"
+UNIT = "vesicle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--cells", default=None,
+                    help="smaller piece of the 58%% lattice (e.g. 6,6,2) for profiling; default: the 1440 scene")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of the dominant kernels (roofline numerators)
+# ---------------------------------------------------------------------------
+def synth_flops(p: int) -> int:
+    """FP64 flops of one (vesicle, time) synthesis as the kernel's loops run
+    them (mul + add per term; symmetric combinations)."""
+    P = 2 * p
+    nh = P // 2 + 1
+    leg = 0
+    for s in range(2 * p + 1):
+        m = (s + 1) >> 1
+        leg += 2 * (p + 1 - m) + 2
+    leg *= 3 * nh
+    four = 3 * (P + 1) * (P // 2 + 1) * (4 * p + 8)
+    poles = 6 * 2 * (p + 1)
+    return leg + four + poles
+
+
+def load_peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# the oracle on a bounded sample (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+class OracleScene:
+    """The scene prepared for the oracle once (untimed): every vesicle
+    synthesized, boxes and all candidate pairs (all-pairs box test)."""
+
+    def __init__(self, sc):
+        from concurrent.futures import ThreadPoolExecutor
+        import oracle as O
+        O.build()
+        self.O, self.sc = O, sc
+        self.threads = os.cpu_count() or 1
+        with ThreadPoolExecutor(self.threads) as ex:
+            self.X = list(ex.map(lambda v: O.synth_vesicle(int(sc.p[v]), int(sc.P[v]), sc.coef_of(v)), range(sc.n)))
+        boxes = np.stack([O.vesicle_box(X, sc.d_m) for X in self.X])
+        self.pairs = O.candidate_pairs(boxes, sc.L)
+
+    def sample(self, n_s: int, seed: int):
+        """Time the oracle on n_s random vesicles: their SH synthesis plus every
+        candidate pair they own (pair (i, j), i < j, is owned by i), i.e. the
+        vertex-triangle and edge-edge tests, V and dV/dX1 of those pairs.
+        Summed over all vesicles this is exactly one step of the scene."""
+        from concurrent.futures import ThreadPoolExecutor
+        O, sc = self.O, self.sc
+        rng = np.random.default_rng(seed)
+        S = np.sort(rng.choice(sc.n, size=min(n_s, sc.n), replace=False))
+        own = self.pairs[np.isin(self.pairs[:, 0], S)]
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(self.threads) as ex:
+            list(ex.map(lambda v: O.synth_vesicle(int(sc.p[v]), int(sc.P[v]), sc.coef_of(v)), S.tolist()))
+        O.contacts(sc.P, self.X, own, sc.L, sc.eps * sc.dt, nthreads=self.threads)
+        secs = time.perf_counter() - t0
+        desc = (f"{len(S)} random vesicles of the {sc.n}-vesicle scene: oracle SH synthesis of X0/X1 plus "
+                f"the {len(own)} candidate pairs they own (vertex-triangle and edge-edge tests, V, dV/dX1)")
+        return len(S), secs, desc
+
+    def sized(self, target_s: float, seed: int = 0) -> int:
+        n, secs, _ = self.sample(16, seed)
+        return int(max(4, min(self.sc.n, 16 * target_s / max(secs, 1e-3))))
+
+
+def oracle_sample(sc, target_s: float, rng_seed: int = 0):
+    """(vesicles, seconds, threads, description) of one timed oracle sample of
+    about target_s seconds."""
+    osc = OracleScene(sc)
+    n_s = osc.sized(target_s, rng_seed)
+    nv, secs, desc = osc.sample(n_s, rng_seed + 1)
+    return nv, secs, osc.threads, desc
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle, timed on this host's cores."""
+    if rank != 0:
+        return
+    from paper_1812_04719_gb300 import scenegen as G
+    sc = G.scene_1440(seed=args.seed)
+    osc = OracleScene(sc)
+    threads = osc.threads
+    budget = max(2.0, 150.0 / max(args.steps + args.warmup, 1))
+    n_s = osc.sized(budget)
+    per_step = []
+    total_v = 0
+    desc = ""
+    for k in range(args.warmup + args.steps):
+        nv, t, desc = osc.sample(n_s, seed=100 + k)
+        if k >= args.warmup:
+            per_step.append((nv, t))
+            total_v += nv
+    secs = sum(t for _, t in per_step)
+    value = total_v / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / len(per_step),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": sc.name, "n_vesicles": sc.n, "sample": "per step: " + desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    from paper_1812_04719_gb300 import build as B
+    B.build()
+    from paper_1812_04719_gb300 import scenegen as G
+    from paper_1812_04719_gb300 import stiv as S
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    prec = S.STIV_MIXED if args.precision == "mixed" else S.STIV_FP64
+    if args.cells:
+        sc = G.scene_lattice58(tuple(int(x) for x in args.cells.split(",")), seed=args.seed + rank)
+    else:
+        sc = G.scene_1440(seed=args.seed + rank)
+    eng = S.Stiv.for_scene(sc, precision=prec, pair_cap=8192, contact_cap=1 << 20, device=dev)
+    ds = S.DeviceScene.from_scene(sc, precision=prec, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    st = int(stream.cuda_stream)
+    # size the buffers (grows on overflow), then profile inside the captured graph
+    eng.step(ds, grad=True)
+    S.stiv_profile(eng.h, True)
+    gX = torch.zeros(ds.verts.numel(), dtype=torch.float64, device=dev)
+    gcoef = torch.zeros_like(ds.coef)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    def step(r_holder):
+        r = eng.step(ds, grad=True, use_graph=True, stream=stream)
+        b = eng.buf
+        cst = b.contacts_struct()
+        gX.zero_()
+        S.stiv_grad_scatter(eng.h, st, ds.p.data_ptr(), cst, b.counts.data_ptr(), 0, b.grad.data_ptr(),
+                            b.gves.data_ptr(), b.gvid.data_ptr(), ds.vert_off.data_ptr(), gX.data_ptr())
+        S.stiv_grad_to_coef(eng.h, st, ds.n, ds.p_max, ds.p.data_ptr(), ds.coef_off.data_ptr(),
+                            ds.vert_off.data_ptr(), gX.data_ptr(), gcoef.data_ptr())
+        r_holder[0] = r
+
+    holder = [None]
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step(holder)
+        torch.cuda.synchronize(dev)
+        S.stiv_profile_read(eng.h)
+    prof_tot = {}
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step(holder)
+        ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        for name, (n, ms) in S.stiv_profile_read(eng.h).items():
+            a = prof_tot.setdefault(name, [0, 0.0])
+            a[0] += n; a[1] += ms
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    ms_mean = float(np.mean(step_ms))
+    counts = holder[0]["counts"]
+    # max over ranks of the per-step time
+    if world > 1:
+        t = torch.tensor([ms_mean], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    else:
+        ms_max = ms_mean
+    value = sc.n * world / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel
+    stage_ms = {k: v[1] / args.steps for k, v in prof_tot.items()}
+    dom = max(stage_ms, key=stage_ms.get)
+    peaks, peak_src = load_peaks()
+    if dom == "narrow":
+        work = float(counts[S.C_FLOPS])
+        roof = {"bound": "alu", "achieved": work / (stage_ms[dom] * 1e-3) / 1e9, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "kernel": "narrow (FP64 contact tests)", "work_per_launch": work,
+                "peak_source": "FP64 1.25 TFLOP/s (vector = tensor rate on GB300)"}
+    elif dom == "synth":
+        work = float(sum(2 * synth_flops(int(p)) for p in sc.p)) if prec == S.STIV_FP64 else 0.0
+        roof = {"bound": "alu", "achieved": work / (stage_ms[dom] * 1e-3) / 1e9, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "kernel": "synth (FP64 SH synthesis)", "work_per_launch": work,
+                "peak_source": "FP64 1.25 TFLOP/s"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "kernel": dom}
+    if roof.get("achieved") is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["avg_launch_ms"] = stage_ms[dom]
+    launches = int(sum(v[0] for v in prof_tot.values()))
+
+    # end to end through the public API: pinned host coefficients in, V / J rows out
+    e2e = None
+    if not args.no_e2e:
+        host_coef = torch.empty(ds.coef.numel(), dtype=torch.float64, pin_memory=True)
+        host_coef.copy_(torch.as_tensor(sc.coef))
+        e_ms = []
+        bi = bo = 0
+        for k in range(max(3, args.steps // 2)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ds.coef.copy_(host_coef, non_blocking=True)
+            r = eng.step(ds, grad=True, use_graph=True, stream=stream)
+            Vp = r["V_pair"].to("cpu", non_blocking=False)
+            J = r["grad"].to("cpu", non_blocking=False)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            S.stiv_profile_read(eng.h)
+            if k >= 1:
+                e_ms.append(e0.elapsed_time(e1))
+            bi = host_coef.numel() * 8
+            bo = Vp.numel() * 8 + J.numel() * 8 + S.NCOUNTS * 8 + r["gves"].numel() * 4 + r["gvid"].numel() * 4
+        e2e = {"value": sc.n * world / (float(np.mean(e_ms)) * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(bo)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        nv, secs, threads, desc = oracle_sample(sc, args.cpu_seconds)
+        cpu = {"value": nv / secs, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if prec == S.STIV_FP64 else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": sc.name, "n_vesicles": sc.n, "p": 16, "P": 32,
+                           "precision": args.precision, "l2": "flushed (256 MB write) before every timed step",
+                           "step": "upsample X0,X1 + boxes + Alg.1 pairs + VF/EE contact tests + V + dV/dX1 "
+                                   "+ adjoint to SH coefficients",
+                           "graph": "CUDA graph replay (upsample+detect+V+dV); adjoint launched after it",
+                           "candidate_pairs": int(counts[S.C_PAIRS]),
+                           "contact_pairs": int(counts[S.C_CPAIRS]),
+                           "contacts_vf": int(counts[S.C_VF]), "contacts_ee": int(counts[S.C_EE]),
+                           "prim_pairs_tested": int(counts[S.C_PRIM]), "patch_pairs": int(counts[S.C_PATCH])},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda x: -x[1])},
+                "wall_s": t_wall}
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

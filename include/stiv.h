@@ -72,7 +72,8 @@ enum stiv_count {
   STIV_C_DEGEN = 5,    /* primitive pairs skipped as degenerate               */
   STIV_C_STATUS = 6,   /* bit flags STIV_F_*                                  */
   STIV_C_PATCH = 7,    /* patch pairs examined by the narrow phase            */
-  STIV_NCOUNTS = 8
+  STIV_C_FLOPS = 8,    /* FP64 flops executed by the exact contact tests      */
+  STIV_NCOUNTS = 9
 };
 
 enum stiv_flag {
@@ -199,6 +200,20 @@ int stiv_step(stiv_handle* h, void* stream, int32_t use_graph, int32_t n_ves, in
               const int64_t* vert_off_dev, void* verts_dev, const stiv_pairs* cand,
               const stiv_contacts* out, int64_t* counts_dev, double* V_contact_dev,
               double* V_pair_dev, double* grad_dev, int32_t* g_ves_dev, int32_t* g_vid_dev);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * every kernel (or kernel group) the library launches.  Inside a captured
+ * stiv_step graph the events are event-record nodes, re-recorded by each
+ * replay.  stiv_profile_read waits for the recorded events and writes, per
+ * stage name (32-byte NUL-terminated entries of names), the number of kernel
+ * launches and the summed milliseconds, and sets *n_names; eager records are
+ * then cleared, graph records are kept for the next replay (read once per
+ * replay).  Stage names: synth, boxes, cells, sort_cells, cell_pairs,
+ * sort_pairs, unique_pairs, patch_pairs, narrow, contact_order, finalize,
+ * stiv, stiv_grad, vpair, grad_scatter, grad_to_coef. */
+int stiv_profile(stiv_handle* h, int32_t enable);
+int stiv_profile_read(stiv_handle* h, int32_t max_names, char* names, int64_t* launches, double* total_ms,
+                      int32_t* n_names);
 
 /* Wait for the stream, copy the counts to the host and return STIV_ERR_CAPACITY
  * if an overflow flag is set, STIV_ERR_INPUT for an input flag, else STIV_OK. */

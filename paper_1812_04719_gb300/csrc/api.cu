@@ -5,6 +5,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <string>
+#include <vector>
+
 int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, const int32_t* p_dev, const int64_t* voff,
                      const void* X, const stiv_pairs* cand, detect_ws& w, int64_t* ctr);
 int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, const int64_t* voff, const void* X,
@@ -32,13 +35,119 @@ __global__ void topology_kernel(int P, int32_t* tri, int32_t* edge) {
 __global__ void finalize_kernel(int64_t* ctr, int64_t C, int64_t* counts) {
   if (threadIdx.x == 0) {
     if (ctr[11] > C) ctr[STIV_C_STATUS] |= STIV_F_CONTACTS_OVERFLOW;
-    for (int k = 0; k < STIV_NCOUNTS; ++k) counts[k] = ctr[k];
+    for (int k = 0; k < 8; ++k) counts[k] = ctr[k];
+    counts[STIV_C_FLOPS] = ctr[12];
   }
 }
 
 inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// per-kernel CUDA-event profiler
+// ---------------------------------------------------------------------------
+struct stiv_profiler {
+  struct rec { std::string name; int nk; cudaEvent_t b, e; bool in_graph; bool valid; };
+  std::vector<rec> recs;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> open;   // indices of stages begun but not ended
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t ev = pool.back(); pool.pop_back(); return ev; }
+    cudaEvent_t ev = nullptr;
+    cudaEventCreate(&ev);
+    return ev;
+  }
+};
+
+static bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+  return cs == cudaStreamCaptureStatusActive;
+}
+
+// While a stream is being captured the events become event-record nodes of
+// the graph (re-recorded by every replay); otherwise plain records.
+static void prof_record(cudaEvent_t ev, cudaStream_t st, bool graph) {
+  if (graph) cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  else cudaEventRecord(ev, st);
+}
+
+void stiv_prof_begin(stiv_handle* h, cudaStream_t st, const char* name, int nk) {
+  if (!h || !h->prof) return;
+  stiv_profiler* P = (stiv_profiler*)h->prof;
+  bool g = capturing(st);
+  stiv_profiler::rec r{name, nk, P->get(), P->get(), g, !g};
+  prof_record(r.b, st, g);
+  P->recs.push_back(r);
+  P->open.push_back((int)P->recs.size() - 1);
+}
+
+void stiv_prof_end(stiv_handle* h, cudaStream_t st) {
+  if (!h || !h->prof) return;
+  stiv_profiler* P = (stiv_profiler*)h->prof;
+  if (P->open.empty()) return;
+  int k = P->open.back();
+  P->open.pop_back();
+  prof_record(P->recs[k].e, st, P->recs[k].in_graph);
+}
+
+// Forget the records owned by a graph that is being destroyed.
+void stiv_prof_drop_graph(stiv_handle* h) {
+  if (!h || !h->prof) return;
+  stiv_profiler* P = (stiv_profiler*)h->prof;
+  std::vector<stiv_profiler::rec> keep;
+  for (auto& r : P->recs) {
+    if (r.in_graph) { P->pool.push_back(r.b); P->pool.push_back(r.e); }
+    else keep.push_back(r);
+  }
+  P->recs.swap(keep);
+}
+
+extern "C" int stiv_profile(stiv_handle* h, int32_t enable) {
+  if (!h) return STIV_ERR_ARG;
+  if (enable && !h->prof) h->prof = new stiv_profiler();
+  if (!enable && h->prof) {
+    stiv_profiler* P = (stiv_profiler*)h->prof;
+    cudaDeviceSynchronize();
+    if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; h->graph_key = 0; }
+    for (auto& r : P->recs) { cudaEventDestroy(r.b); cudaEventDestroy(r.e); }
+    for (auto ev : P->pool) cudaEventDestroy(ev);
+    delete P;
+    h->prof = nullptr;
+  }
+  return STIV_OK;
+}
+
+extern "C" int stiv_profile_read(stiv_handle* h, int32_t max_names, char* names, int64_t* launches,
+                                 double* total_ms, int32_t* n_names) {
+  if (!h || !h->prof || !n_names || max_names < 0) return STIV_ERR_ARG;
+  stiv_profiler* P = (stiv_profiler*)h->prof;
+  std::vector<std::string> keys;
+  std::vector<int64_t> cnt;
+  std::vector<double> tot;
+  std::vector<stiv_profiler::rec> keep;
+  for (auto& r : P->recs) {
+    if (!r.valid) { keep.push_back(r); continue; }   // captured but not replayed yet
+    if (cudaEventSynchronize(r.e) != cudaSuccess) return STIV_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.b, r.e) != cudaSuccess) return STIV_ERR_CUDA;
+    size_t k = 0;
+    while (k < keys.size() && keys[k] != r.name) ++k;
+    if (k == keys.size()) { keys.push_back(r.name); cnt.push_back(0); tot.push_back(0.0); }
+    cnt[k] += r.nk; tot[k] += ms;
+    if (r.in_graph) keep.push_back(r);
+    else { P->pool.push_back(r.b); P->pool.push_back(r.e); }
+  }
+  P->recs.swap(keep);
+  *n_names = (int32_t)keys.size();
+  for (size_t k = 0; k < keys.size() && (int)k < max_names; ++k) {
+    if (names) { strncpy(names + 32 * k, keys[k].c_str(), 31); names[32 * k + 31] = 0; }
+    if (launches) launches[k] = cnt[k];
+    if (total_ms) total_ms[k] = tot[k];
+  }
+  return STIV_OK;
+}
 
 extern "C" const char* stiv_status_string(int s) {
   switch (s) {
@@ -75,6 +184,7 @@ extern "C" int stiv_destroy(stiv_handle* h) {
     if (h->tab_ready[p]) { cudaFree(h->tab[p].leg); cudaFree(h->tab[p].trig); cudaFree(h->tab[p].theta); }
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->ws) cudaFree(h->ws);
+  stiv_profile(h, 0);
   free(h);
   return STIV_OK;
 }
@@ -178,6 +288,7 @@ extern "C" int stiv_detect(stiv_handle* h, void* stream, int32_t n_ves, int32_t 
   if (rc) return rc;
   rc = stiv_contact_order(h, st, cand, out, w);
   if (rc) return rc;
+  STIV_PROF(h, st, "finalize");
   finalize_kernel<<<1, 32, 0, st>>>(w.ctr, w.C, counts_dev);
   STIV_LAUNCH(h);
   return STIV_OK;
@@ -228,6 +339,8 @@ extern "C" int stiv_step(stiv_handle* h, void* stream, int32_t use_graph, int32_
   mix((unsigned long long)cand->capacity); mix((unsigned long long)out->capacity);
   if (h->graph_exec && key == h->graph_key) {
     STIV_CUDA(h, cudaGraphLaunch(h->graph_exec, (cudaStream_t)stream));
+    if (h->prof)
+      for (auto& r : ((stiv_profiler*)h->prof)->recs) if (r.in_graph) r.valid = true;
     return STIV_OK;
   }
   // first call with these arguments: run eagerly (allocates tables and scratch), then capture
@@ -235,6 +348,7 @@ extern "C" int stiv_step(stiv_handle* h, void* stream, int32_t use_graph, int32_
                       counts_dev, V_contact_dev, V_pair_dev, grad_dev, g_ves_dev, g_vid_dev);
   if (rc) return rc;
   if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+  stiv_prof_drop_graph(h);
   cudaStream_t st = (cudaStream_t)stream;
   STIV_CUDA(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
   void* ws_before = h->ws;

@@ -306,25 +306,45 @@ int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, const int32_t* p_de
                      const void* X, const stiv_pairs* cand, detect_ws& w, int64_t* ctr) {
   int mixed = h->prm.precision == STIV_MIXED;
   const double* L = h->prm.box_L;
+  {
+  STIV_PROF(h, st, "boxes");
   boxes_kernel<<<n, 256, 0, st>>>(n, p_dev, voff, X, mixed, h->prm.d_m, L[0], L[1], L[2], w.vbox, w.pbox, ctr);
+  }
+  {
+  STIV_PROF_N(h, st, "cells", 4);
   grid_kernel<<<1, 1024, 0, st>>>(n, w.vbox, L[0], L[1], L[2], w.grid);
   cell_count_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, w.vbox, w.grid, w.cell_count);
   scan1_kernel<<<1, 1024, 0, st>>>(w.cell_count, n, w.cell_off);
   cell_emit_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, w.vbox, w.grid, w.cell_off, w.R, w.rec_key, w.rec_val,
                                                     w.rec_box, w.rec_cell, ctr);
+  }
   STIV_LAUNCH(h);
   // records: ctr[8] = count; sort by Morton id (30 bits)
-  int rc = stiv_sort_pairs_impl(st, w.R, 30, w.rec_key, w.rec_val, w.rec_key2, w.rec_val2, w.sort_scratch,
+  int rc;
+  {
+  STIV_PROF_N(h, st, "sort_cells", stiv_sort_kernels(30));
+  rc = stiv_sort_pairs_impl(st, w.R, 30, w.rec_key, w.rec_val, w.rec_key2, w.rec_val2, w.sort_scratch,
                                 w.sort_scratch_bytes, &ctr[8]);
+  }
   if (rc) return rc;
+  {
+  STIV_PROF(h, st, "cell_pairs");
   cell_pairs_kernel<<<(unsigned)((w.R + 127) / 128), 128, 0, st>>>(&ctr[8], w.R, w.rec_key2, w.rec_val2, w.rec_box,
                                                                    w.rec_cell, w.vbox, w.grid, L[0], L[1], L[2],
                                                                    w.Q, w.pkey, w.pval, ctr);
+  }
   STIV_LAUNCH(h);
-  rc = stiv_sort_pairs_impl(st, w.Q, 53, w.pkey, w.pval, w.pkey2, w.pval2, w.sort_scratch, w.sort_scratch_bytes,
-                            &ctr[9]);
+  {
+    STIV_PROF_N(h, st, "sort_pairs", stiv_sort_kernels(53));
+    rc = stiv_sort_pairs_impl(st, w.Q, 53, w.pkey, w.pval, w.pkey2, w.pval2, w.sort_scratch, w.sort_scratch_bytes,
+                              &ctr[9]);
+  }
   if (rc) return rc;
-  unique_pairs_kernel<<<1, 1024, 0, st>>>(&ctr[9], w.Q, w.pkey2, cand->capacity, cand->i, cand->j, cand->shift, ctr);
+  {
+    STIV_PROF(h, st, "unique_pairs");
+    unique_pairs_kernel<<<1, 1024, 0, st>>>(&ctr[9], w.Q, w.pkey2, cand->capacity, cand->i, cand->j, cand->shift,
+                                            ctr);
+  }
   STIV_LAUNCH(h);
   return STIV_OK;
 }

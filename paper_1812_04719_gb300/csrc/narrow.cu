@@ -238,10 +238,15 @@ __device__ void filter_patch(PatchSm& S, const float* ob, int lane) {
 // ---------------------------------------------------------------------------
 enum { KIND_VF = 0, KIND_EE = 1 };
 
-__device__ double bisect64(double k0, double k1, double k2, double k3, double lo, double hi, double flo) {
+// FP64 flops of the procedure, counted as executed (fma = 2): the
+// algorithmic work of the exact contact test, reported for the roofline.
+__device__ double bisect64(double k0, double k1, double k2, double k3, double lo, double hi, double flo,
+                           long long& flops) {
   for (int it = 0; it < 64; ++it) {
     double mid = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+    flops += 2;
     if (!(mid > lo && mid < hi)) break;
+    flops += 6;
     double fm = horner3(k0, k1, k2, k3, mid);
     if (fm == 0.0) return mid;
     if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; }
@@ -276,7 +281,8 @@ __device__ int inside64(int kind, const d3* Y, double& w1, double& w2) {
 }
 
 // 0 no contact, 1 contact, 2 degenerate.
-__device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w1, double& w2) {
+__device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w1, double& w2, long long& flops) {
+  flops += 18 + 9 + 21 + 9 + 32;  // differences, three cross products (+ sum), four dot products
   d3 a, b, c, da, db, dc;
   if (kind == KIND_VF) {
     a = d3_sub(X0[2], X0[1]); b = d3_sub(X0[3], X0[1]); c = d3_sub(X0[0], X0[1]);
@@ -296,9 +302,12 @@ __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w
   // critical points of the cubic inside (0, 1)
   double e0 = k1, e1 = __dmul_rn(2.0, k2), e2 = __dmul_rn(3.0, k3);
   double r[2]; int nr = 0;
+  flops += 2;
   if (e2 != 0.0) {
     double disc = __fma_rn(e1, e1, -__dmul_rn(__dmul_rn(4.0, e2), e0));
+    flops += 4;
     if (disc > 0.0) {
+      flops += 6;
       double sq = __dsqrt_rn(disc);
       double q = __dmul_rn(-0.5, __dadd_rn(e1, e1 >= 0.0 ? sq : -sq));
       r[0] = __ddiv_rn(q, e2); r[1] = __ddiv_rn(e0, q); nr = 2;
@@ -320,10 +329,12 @@ __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w
   for (int s = 0; s + 1 < ne; ++s) {
     double l = ends[s], rr = ends[s + 1];
     double fl = horner3(k0, k1, k2, k3, l), fr = horner3(k0, k1, k2, k3, rr), t;
+    flops += 12;
     if (fl == 0.0) t = l;
     else if (fr == 0.0) t = rr;
-    else if ((fl < 0.0) != (fr < 0.0)) t = bisect64(k0, k1, k2, k3, l, rr, fl);
+    else if ((fl < 0.0) != (fr < 0.0)) t = bisect64(k0, k1, k2, k3, l, rr, fl, flops);
     else continue;
+    flops += 24 + 9 + 25 + 3 + 6 + 2 + 2;  // positions, differences, dots, determinant, numerators, divisions
     d3 Y[4];
     for (int q = 0; q < 4; ++q) Y[q] = d3_at(X0[q], t, D[q]);
     double u1 = 0.0, u2 = 0.0;
@@ -340,7 +351,7 @@ __device__ __forceinline__ d3 slot_pos(const PatchSm& S, int t, int sl) {
 
 // Drain up to n queued pairs, one per lane.
 __device__ void process_queue(WarpSm& ws, int n, int lane, int r, const narrow_args& a, long long& nprim,
-                              long long& ndeg) {
+                              long long& ndeg, long long& flops) {
   int type = -1, ga = 0, gb = 0;
   double tau = 0.0, w1 = 0.0, w2 = 0.0;
   if (lane < n) {
@@ -387,7 +398,8 @@ __device__ void process_queue(WarpSm& ws, int n, int lane, int r, const narrow_a
     }
     if (hit) {
       ++nprim;
-      int st = ccd64(kind == 2 ? KIND_EE : KIND_VF, X0, D, tau, w1, w2);
+      flops += 12;  // displacements D = X1 - X0
+      int st = ccd64(kind == 2 ? KIND_EE : KIND_VF, X0, D, tau, w1, w2, flops);
       if (st == 1) {
         type = kind;
         if (kind == 0) { ga = SA.v_gid[x]; gb = SB.t_gid[y]; }
@@ -417,14 +429,14 @@ __device__ void process_queue(WarpSm& ws, int n, int lane, int r, const narrow_a
 
 // Push this lane's candidate (if any) into the warp queue; drain when >= 32.
 __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, int lane, int r, const narrow_args& a,
-                                        long long& nprim, long long& ndeg) {
+                                        long long& nprim, long long& ndeg, long long& flops) {
   unsigned m = __ballot_sync(0xffffffffu, hit);
   int qn = ws.qn;
   if (hit) ws.q[qn + __popc(m & ((1u << lane) - 1u))] = entry;
   qn += __popc(m);
   __syncwarp();
   if (qn >= 32) {
-    process_queue(ws, 32, lane, r, a, nprim, ndeg);
+    process_queue(ws, 32, lane, r, a, nprim, ndeg, flops);
     __syncwarp();
     unsigned rest = (lane + 32 < qn) ? ws.q[lane + 32] : 0;
     __syncwarp();
@@ -441,7 +453,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
   int lane = threadIdx.x & 31;
   int64_t nwork = a.ctr[STIV_C_PATCH];
   if (nwork > a.W) nwork = a.W;
-  long long nprim = 0, ndeg = 0;
+  long long nprim = 0, ndeg = 0, flops = 0;
   while (true) {
     long long item = 0;
     if (lane == 0) item = (long long)atomicAdd((unsigned long long*)&a.ctr[10], 1ull);
@@ -472,7 +484,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
           int x = V.vf[xk], sl = V.v_slot[x];
           float lo[3] = {V.flo[0][sl], V.flo[1][sl], V.flo[2][sl]}, hi[3] = {V.fhi[0][sl], V.fhi[1][sl], V.fhi[2][sl]};
           bool hit = valid && fbox_hit(lo, hi, tb);
-          enqueue(ws, hit, ((unsigned)dir << 16) | ((unsigned)x << 8) | (unsigned)y, lane, r, a, nprim, ndeg);
+          enqueue(ws, hit, ((unsigned)dir << 16) | ((unsigned)x << 8) | (unsigned)y, lane, r, a, nprim, ndeg, flops);
         }
       }
     }
@@ -487,22 +499,24 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
           int x = ws.A.ef[xk];
           float lo[3] = {ws.A.eb[0][x], ws.A.eb[1][x], ws.A.eb[2][x]}, hi[3] = {ws.A.eb[3][x], ws.A.eb[4][x], ws.A.eb[5][x]};
           bool hit = valid && fbox_hit(lo, hi, eb);
-          enqueue(ws, hit, (2u << 16) | ((unsigned)x << 8) | (unsigned)y, lane, r, a, nprim, ndeg);
+          enqueue(ws, hit, (2u << 16) | ((unsigned)x << 8) | (unsigned)y, lane, r, a, nprim, ndeg, flops);
         }
       }
     }
     int qn = ws.qn;
-    if (qn > 0) process_queue(ws, qn, lane, r, a, nprim, ndeg);
+    if (qn > 0) process_queue(ws, qn, lane, r, a, nprim, ndeg, flops);
     __syncwarp();
   }
   // totals
   for (int off = 16; off > 0; off >>= 1) {
     nprim += __shfl_down_sync(0xffffffffu, nprim, off);
     ndeg += __shfl_down_sync(0xffffffffu, ndeg, off);
+    flops += __shfl_down_sync(0xffffffffu, flops, off);
   }
   if (lane == 0) {
     if (nprim) atomicAdd((unsigned long long*)&a.ctr[STIV_C_PRIM], (unsigned long long)nprim);
     if (ndeg) atomicAdd((unsigned long long*)&a.ctr[STIV_C_DEGEN], (unsigned long long)ndeg);
+    if (flops) atomicAdd((unsigned long long*)&a.ctr[12], (unsigned long long)flops);
   }
 }
 
@@ -600,8 +614,11 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   int mp = stiv_npatches(2 * p_max);
   size_t psmem = (size_t)4 * 2 * mp * 6 * sizeof(float) + (size_t)4 * 2 * mp * sizeof(unsigned short);
   STIV_CUDA(h, cudaFuncSetAttribute(patch_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+  {
+  STIV_PROF(h, st, "patch_pairs");
   patch_pairs_kernel<<<blocks, 128, psmem, st>>>(p_dev, w.vbox, w.pbox, L[0], L[1], L[2], cand->i, cand->j,
                                                  cand->shift, cand->capacity, w.W, w.work, w.ctr, mp);
+  }
   STIV_LAUNCH(h);
   narrow_args a;
   a.pv = p_dev; a.voff = voff; a.X = X; a.mixed = h->prm.precision == STIV_MIXED;
@@ -617,6 +634,7 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   int per_sm = 0;
   STIV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, narrow_kernel, NW * 32, smem));
   if (per_sm < 1) per_sm = 1;
+  STIV_PROF(h, st, "narrow");
   narrow_kernel<<<per_sm * num_sms, NW * 32, smem, st>>>(a);
   STIV_LAUNCH(h);
   return STIV_OK;

@@ -301,20 +301,28 @@ __global__ void __launch_bounds__(256) adjoint_kernel(adj_args a) {
 
 }  // namespace
 
+static int cand_bits(int64_t cap) {
+  int pbits = 1;
+  while (pbits < 32 && ((int64_t)1 << pbits) <= cap) ++pbits;
+  return pbits;
+}
+
 int stiv_contact_order(stiv_handle* h, cudaStream_t st, const stiv_pairs* cand, const stiv_contacts* out,
                        detect_ws& w) {
   int64_t C = w.C;
   int32_t* rp = w.tmp_i32; int32_t* rt = rp + C; int32_t* ra = rp + 2 * C; int32_t* rb = rp + 3 * C;
   double* rtau = w.tmp_f64; double* rw = w.tmp_f64 + C;
   int blocks = (int)((C + 255) / 256); if (blocks > 4096) blocks = 4096; if (blocks < 1) blocks = 1;
+  {
+  STIV_PROF_N(h, st, "contact_order", 2 + stiv_sort_kernels(32 + cand_bits(cand->capacity)));
   contact_keys_kernel<<<blocks, 256, 0, st>>>(w.ctr, C, rp, rt, ra, rb, w.ckey, w.cval);
   STIV_LAUNCH(h);
-  int pbits = 1;
-  while (pbits < 32 && ((int64_t)1 << pbits) <= cand->capacity) ++pbits;
+  int pbits = cand_bits(cand->capacity);
   int rc = stiv_sort_pairs_impl(st, C, 32 + pbits, w.ckey, w.cval, w.ckey2, w.cval2, w.sort_scratch,
                                 w.sort_scratch_bytes, &w.ctr[11]);
   if (rc) return rc;
   contact_gather_kernel<<<blocks, 256, 0, st>>>(w.ctr, C, w.cval2, rp, rt, ra, rb, rtau, rw, *out, w.ctr);
+  }
   STIV_LAUNCH(h);
   return STIV_OK;
 }
@@ -343,10 +351,12 @@ static int run_stiv(stiv_handle* h, void* stream, const int32_t* p_dev, const in
   int dev_sms = 152;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (Vtmp || grad) {
+    STIV_PROF(h, st, A.grad ? "stiv_grad" : "stiv");
     stiv_kernel<<<dev_sms * 8, 128, 0, st>>>(A);
     STIV_LAUNCH(h);
   }
   if (Vp) {
+    STIV_PROF(h, st, "vpair");
     vpair_kernel<<<dev_sms * 4, 128, 0, st>>>(ct->pair, counts_dev, ct->capacity, Vtmp, cand->capacity, Vp);
     STIV_LAUNCH(h);
   }
@@ -380,6 +390,7 @@ extern "C" int stiv_grad_scatter(stiv_handle* h, void* stream, const int32_t* p_
     return STIV_ERR_ARG;
   int dev_sms = 152;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device);
+  STIV_PROF(h, (cudaStream_t)stream, "grad_scatter");
   scatter_grad_kernel<<<dev_sms * 4, 128, 0, (cudaStream_t)stream>>>(counts_dev, contacts->capacity, contacts->pair,
                                                                      weight_pair_dev, grad_dev, g_ves_dev, g_vid_dev,
                                                                      p_dev, vert_off_dev, gX_dev);
@@ -404,6 +415,7 @@ extern "C" int stiv_grad_to_coef(stiv_handle* h, void* stream, int32_t n_ves, in
   }
   size_t smem = sizeof(double) * (size_t)3 * (2 * p_max + 1) * (2 * p_max + 1);
   STIV_CUDA(h, cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  STIV_PROF(h, st, "grad_to_coef");
   adjoint_kernel<<<n_ves, 256, smem, st>>>(a);
   STIV_LAUNCH(h);
   return STIV_OK;

@@ -38,7 +38,29 @@ struct stiv_handle {
   // CUDA graph of stiv_step
   cudaGraphExec_t graph_exec;
   unsigned long long graph_key;
+  // per-kernel CUDA-event profiler (stiv_profile); null when off
+  void* prof;
 };
+
+// Brackets the launches of one named stage with CUDA events on its stream
+// while the profiler is on (no-op otherwise).
+// nk = number of kernels the stage launches.
+void stiv_prof_begin(stiv_handle* h, cudaStream_t st, const char* name, int nk);
+void stiv_prof_end(stiv_handle* h, cudaStream_t st);
+void stiv_prof_drop_graph(stiv_handle* h);
+struct stiv_prof_scope {
+  stiv_handle* h; cudaStream_t st;
+  stiv_prof_scope(stiv_handle* h_, cudaStream_t st_, const char* name, int nk) : h(h_), st(st_) {
+    stiv_prof_begin(h, st, name, nk);
+  }
+  ~stiv_prof_scope() { stiv_prof_end(h, st); }
+};
+#define STIV_PROF_CAT2(a, b) a##b
+#define STIV_PROF_CAT(a, b) STIV_PROF_CAT2(a, b)
+#define STIV_PROF_N(h, st, name, nk) stiv_prof_scope STIV_PROF_CAT(prof_scope_, __LINE__)(h, st, name, nk)
+#define STIV_PROF(h, st, name) STIV_PROF_N(h, st, name, 1)
+// kernels launched by one radix sort of key_bits bits (histogram, scan, scatter per 8-bit digit)
+inline int stiv_sort_kernels(int key_bits) { return 3 * ((key_bits + 7) / 8); }
 
 // Scratch layout used by stiv_detect (byte offsets into handle->ws).
 struct detect_ws {

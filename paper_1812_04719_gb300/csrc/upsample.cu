@@ -205,6 +205,7 @@ extern "C" int stiv_upsample(stiv_handle* h, void* stream, int32_t n_ves, int32_
   }
   size_t smem = synth_smem(p_max);
   STIV_CUDA(h, cudaFuncSetAttribute(synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  STIV_PROF(h, st, "synth");
   synth_kernel<<<dim3(n_ves, 2), 256, smem, st>>>(a);
   STIV_LAUNCH(h);
   return STIV_OK;

@@ -249,7 +249,7 @@ def bcc_lattice(nx, ny, nz, a, c):
 
 
 def lattice_scene(name, cells, phi, ps, seed, tilt_deg, trans_amp, rot_deg, pert, shape_amp=0.01,
-                  flow_amp=0.0, cubic=True, periodic=True) -> Scene:
+                  flow_amp=0.0, cubic=True, periodic=True, cell_shape=None) -> Scene:
     """Staggered (body-centred) lattice of prolate vesicles, long axes near z,
     each tilted by a random angle <= tilt_deg (re-drawn until no two
     ellipsoids overlap), in a periodic box at volume fraction phi.  The step is
@@ -263,7 +263,9 @@ def lattice_scene(name, cells, phi, ps, seed, tilt_deg, trans_amp, rot_deg, pert
     nx, ny, nz = cells
     n = 2 * nx * ny * nz
     vol = 4.0 / 3.0 * math.pi * a_ax * b_ax * b_ax
-    if cubic:   # cube: nx a = nz c
+    if cell_shape is not None:
+        a, c = cell_shape
+    elif cubic:   # cube: nx a = nz c
         a = (n * vol / phi) ** (1.0 / 3.0) / nx
         c = nx * a / nz
     else:       # cells stretched like the vesicles, box need not be a cube
@@ -366,6 +368,16 @@ def scene_1440(seed: int = 3, p: int = 16) -> Scene:
     n = 1440
     return lattice_scene(f"1440 vesicles, 58% volume fraction, p={p}->{2*p}", (12, 12, 5), 0.58,
                          [p] * n, seed, tilt_deg=3.0, trans_amp=C1440_TRANS, rot_deg=1.0, pert=0.02)
+
+
+def scene_lattice58(cells=(6, 6, 2), seed: int = 3, p: int = 16) -> Scene:
+    """A smaller piece of the 58% lattice workload (same cell shape, density,
+    step and order); 2 * prod(cells) vesicles, periodic box."""
+    n = 2 * cells[0] * cells[1] * cells[2]
+    a = (1440 * 4.0 / 3.0 * math.pi * np.prod(prolate_axes()[0:1]) * prolate_axes()[1] ** 2 / 0.58) ** (1 / 3) / 12
+    name = f"{n} vesicles, 58% volume fraction, p={p}->{2*p} (lattice {cells[0]}x{cells[1]}x{cells[2]}x2)"
+    return lattice_scene(name, cells, 0.58, [p] * n, seed, tilt_deg=3.0, trans_amp=C1440_TRANS, rot_deg=1.0,
+                         pert=0.02, cubic=False, cell_shape=(a, 12 * a / 5))
 
 
 def scene_4096(seed: int = 4) -> Scene:

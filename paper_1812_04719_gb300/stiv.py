@@ -26,13 +26,14 @@ LIB_PATH = os.path.join(HERE, "libstiv.so")
 
 STIV_OK, STIV_ERR_ARG, STIV_ERR_CAPACITY, STIV_ERR_TIMEOUT, STIV_ERR_CUDA, STIV_ERR_INPUT = range(6)
 STIV_FP64, STIV_MIXED = 0, 1
-C_PAIRS, C_PRIM, C_VF, C_EE, C_CPAIRS, C_DEGEN, C_STATUS, C_PATCH = range(8)
-NCOUNTS = 8
+C_PAIRS, C_PRIM, C_VF, C_EE, C_CPAIRS, C_DEGEN, C_STATUS, C_PATCH, C_FLOPS = range(9)
+NCOUNTS = 9
 F_PAIRS_OVERFLOW, F_CONTACTS_OVERFLOW, F_BOX_TOO_SMALL, F_NONFINITE, F_WORK_OVERFLOW = 1, 2, 4, 8, 16
 
 EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_error", "stiv_mesh_topology",
            "stiv_upsample", "stiv_detect", "stiv_stiv", "stiv_stiv_grad", "stiv_grad_scatter",
-           "stiv_grad_to_coef", "stiv_step", "stiv_sync_counts", "stiv_sort_scratch_bytes", "stiv_sort_pairs"]
+           "stiv_grad_to_coef", "stiv_step", "stiv_sync_counts", "stiv_sort_scratch_bytes", "stiv_sort_pairs",
+           "stiv_profile", "stiv_profile_read"]
 
 
 class StivError(RuntimeError):
@@ -88,6 +89,8 @@ def lib() -> ctypes.CDLL:
     L.stiv_sort_scratch_bytes.argtypes = [i64]
     L.stiv_sort_scratch_bytes.restype = ctypes.c_size_t
     L.stiv_sort_pairs.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, ctypes.c_size_t]
+    L.stiv_profile.argtypes = [vp, i32]
+    L.stiv_profile_read.argtypes = [vp, i32, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -185,6 +188,26 @@ def stiv_sort_pairs(stream, n, key_bits, keys_in_ptr, vals_in_ptr, keys_out_ptr,
                     scratch_bytes):
     _check(lib().stiv_sort_pairs(stream, n, key_bits, keys_in_ptr, vals_in_ptr, keys_out_ptr, vals_out_ptr,
                                  scratch_ptr, scratch_bytes), "stiv_sort_pairs")
+
+
+def stiv_profile(h: int, enable: bool):
+    _check(lib().stiv_profile(h, int(bool(enable))), "stiv_profile")
+
+
+def stiv_profile_read(h: int) -> dict:
+    """{stage: (launches, total_ms)} since the last read."""
+    maxn = 64
+    names = ctypes.create_string_buffer(32 * maxn)
+    cnt = np.zeros(maxn, dtype=np.int64)
+    tot = np.zeros(maxn, dtype=np.float64)
+    n = ctypes.c_int32(0)
+    _check(lib().stiv_profile_read(h, maxn, ctypes.addressof(names), cnt.ctypes.data, tot.ctypes.data,
+                                   ctypes.addressof(n)), "stiv_profile_read")
+    out = {}
+    for k in range(min(n.value, maxn)):
+        nm = names.raw[32 * k:32 * k + 32].split(b"\0", 1)[0].decode()
+        out[nm] = (int(cnt[k]), float(tot[k]))
+    return out
 
 
 def stiv_sort_scratch_bytes(n: int) -> int:
