@@ -366,7 +366,8 @@ def run_ours(args, rank, world, local):
                            "candidate_pairs": int(counts[S.C_PAIRS]),
                            "contact_pairs": int(counts[S.C_CPAIRS]),
                            "contacts_vf": int(counts[S.C_VF]), "contacts_ee": int(counts[S.C_EE]),
-                           "prim_pairs_tested": int(counts[S.C_PRIM]), "patch_pairs": int(counts[S.C_PATCH])},
+                           "prim_pairs_tested": int(counts[S.C_PRIM]), "patch_pairs": int(counts[S.C_PATCH]),
+                           "prim_pairs_fp64": int(counts[S.C_EXACT])},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda x: -x[1])},
                 "wall_s": t_wall}

@@ -73,7 +73,8 @@ enum stiv_count {
   STIV_C_STATUS = 6,   /* bit flags STIV_F_*                                  */
   STIV_C_PATCH = 7,    /* patch pairs examined by the narrow phase            */
   STIV_C_FLOPS = 8,    /* FP64 flops executed by the exact contact tests      */
-  STIV_NCOUNTS = 9
+  STIV_C_EXACT = 9,    /* primitive pairs that ran the FP64 contact test      */
+  STIV_NCOUNTS = 10
 };
 
 enum stiv_flag {
@@ -91,6 +92,9 @@ typedef struct stiv_params {
   double box_L[3];     /* periodic box lengths; 0 = free space on that axis */
   int32_t precision;   /* enum stiv_precision */
   int32_t include_ee;  /* 1: edge-edge contacts as well as vertex-triangle ones */
+  int32_t exact_only;  /* 1: skip the certified FP32 rejection and run the FP64 contact
+                          test on every primitive pair whose boxes overlap (same results,
+                          slower; for cross-checks) */
 } stiv_params;
 
 /* Candidate vesicle pairs (Alg. 1 output, i < j), sorted by (i, j, shift).

@@ -37,6 +37,7 @@ __global__ void finalize_kernel(int64_t* ctr, int64_t C, int64_t* counts) {
     if (ctr[11] > C) ctr[STIV_C_STATUS] |= STIV_F_CONTACTS_OVERFLOW;
     for (int k = 0; k < 8; ++k) counts[k] = ctr[k];
     counts[STIV_C_FLOPS] = ctr[12];
+    counts[STIV_C_EXACT] = ctr[13];
   }
 }
 
@@ -207,19 +208,25 @@ extern "C" int stiv_mesh_topology(int32_t P, int32_t* tri_dev, int32_t* edge_dev
 }
 
 // Scratch of stiv_detect, carved from the handle's buffer.
-static int detect_layout(stiv_handle* h, int n, const stiv_pairs* cand, const stiv_contacts* out, detect_ws& w,
-                         bool carve) {
+static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* cand, const stiv_contacts* out,
+                         detect_ws& w, bool carve) {
   w.R = (int64_t)n * 64 + 1024;
   w.Q = cand->capacity * 8 + 1024;
   w.W = cand->capacity * 64 + 1024;
   if (w.W < out->capacity) w.W = out->capacity;
   w.C = out->capacity > 0 ? out->capacity : 1;
+  w.Q3 = 16 * w.C + 4096;
+  w.Q2 = (h->prm.exact_only ? 32 : 4) * w.C + 4096;
   int64_t smax = w.R > w.Q ? w.R : w.Q;
   if (w.C > smax) smax = w.C;
   w.sort_scratch_bytes = stiv_sort_scratch_impl(smax);
   size_t off = 0;
   size_t o_vbox = off; off = align_up(off + sizeof(double) * 6 * (size_t)n);
-  size_t o_pbox = off; off = align_up(off + sizeof(float) * 6 * (size_t)STIV_MAX_PATCH * n);
+  w.pstride = stiv_npatches(2 * p_max);
+  size_t o_pbox = off; off = align_up(off + sizeof(float) * 6 * (size_t)w.pstride * n);
+  w.fstride = 6 * (int64_t)stiv_nverts(2 * p_max);
+  size_t o_vorg = off; off = align_up(off + sizeof(float) * 4 * (size_t)n);
+  size_t o_fprep = off; off = align_up(off + sizeof(float) * (size_t)w.fstride * n);
   size_t o_grid = off; off = align_up(off + sizeof(double) * 16);
   size_t o_cc = off; off = align_up(off + sizeof(int32_t) * (size_t)(n + 1));
   size_t o_co = off; off = align_up(off + sizeof(int32_t) * (size_t)(n + 1));
@@ -234,6 +241,8 @@ static int detect_layout(stiv_handle* h, int n, const stiv_pairs* cand, const st
   size_t o_pk2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q);
   size_t o_pv2 = off; off = align_up(off + sizeof(int32_t) * (size_t)w.Q);
   size_t o_wk = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.W);
+  size_t o_q3 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q3);
+  size_t o_q2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q2);
   size_t o_ck = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.C);
   size_t o_cv = off; off = align_up(off + sizeof(int32_t) * (size_t)w.C);
   size_t o_ck2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.C);
@@ -245,6 +254,8 @@ static int detect_layout(stiv_handle* h, int n, const stiv_pairs* cand, const st
   if (!carve) return stiv_ws_reserve(h, off);
   char* b = (char*)h->ws;
   w.vbox = (double*)(b + o_vbox); w.pbox = (float*)(b + o_pbox); w.grid = (double*)(b + o_grid);
+  w.vorg = (float*)(b + o_vorg); w.fprep = (float*)(b + o_fprep);
+  w.exact_only = h->prm.exact_only;
   w.cell_count = (int32_t*)(b + o_cc); w.cell_off = (int32_t*)(b + o_co);
   w.rec_key = (uint64_t*)(b + o_rk); w.rec_val = (int32_t*)(b + o_rv);
   w.rec_key2 = (uint64_t*)(b + o_rk2); w.rec_val2 = (int32_t*)(b + o_rv2);
@@ -252,6 +263,7 @@ static int detect_layout(stiv_handle* h, int n, const stiv_pairs* cand, const st
   w.pkey = (uint64_t*)(b + o_pk); w.pval = (int32_t*)(b + o_pv);
   w.pkey2 = (uint64_t*)(b + o_pk2); w.pval2 = (int32_t*)(b + o_pv2);
   w.work = (uint64_t*)(b + o_wk);
+  w.q3 = (unsigned long long*)(b + o_q3); w.q2 = (unsigned long long*)(b + o_q2);
   w.ckey = (uint64_t*)(b + o_ck); w.cval = (int32_t*)(b + o_cv);
   w.ckey2 = (uint64_t*)(b + o_ck2); w.cval2 = (int32_t*)(b + o_cv2);
   w.tmp_i32 = (int32_t*)(b + o_ti); w.tmp_f64 = (double*)(b + o_tf);
@@ -276,9 +288,9 @@ extern "C" int stiv_detect(stiv_handle* h, void* stream, int32_t n_ves, int32_t 
   }
   if (!p_dev || !vert_off_dev || !verts_dev) return STIV_ERR_ARG;
   detect_ws w;
-  int rc = detect_layout(h, n_ves, cand, out, w, false);
+  int rc = detect_layout(h, n_ves, p_max, cand, out, w, false);
   if (rc) return rc;
-  detect_layout(h, n_ves, cand, out, w, true);
+  detect_layout(h, n_ves, p_max, cand, out, w, true);
   STIV_CUDA(h, cudaMemsetAsync(w.ctr, 0, sizeof(int64_t) * 16, st));
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);

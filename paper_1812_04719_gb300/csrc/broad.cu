@@ -31,7 +31,8 @@ __device__ __forceinline__ double vload(const void* X, int mixed, size_t i) {
 // One CTA per vesicle.
 __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, const int64_t* voff, const void* X,
                                                     int mixed, double dm, double Lx, double Ly, double Lz,
-                                                    double* vbox, float* pbox, int64_t* ctr) {
+                                                    double* vbox, float* pbox, int pstride, float* vorg,
+                                                    float* fprep, int64_t fstride, int64_t* ctr) {
   int v = blockIdx.x;
   int P = 2 * pv[v], nv = stiv_nverts(P);
   const size_t base = voff[v];
@@ -56,6 +57,7 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
       }
     __syncthreads();
   }
+  __shared__ float sorg[4];
   if (threadIdx.x < 3) {
     int c = threadIdx.x;
     double l = red[c][0] - dm, u = red[3 + c][0] + dm;
@@ -63,7 +65,26 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
     vbox[6 * v + 3 + c] = u;
     double L = c == 0 ? Lx : c == 1 ? Ly : Lz;
     if (L > 0.0 && !(u - l < 0.5 * L)) atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_BOX_TOO_SMALL);
+    // FP32 frame of this vesicle: origin at the (float-rounded) box centre
+    float o = (float)(0.5 * (red[c][0] + red[3 + c][0]));
+    sorg[c] = o;
+    vorg[4 * v + c] = o;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // R bounds |X - o| over the vesicle (both times), rounded up
+    double R = 0.0;
+    for (int c = 0; c < 3; ++c) R = fmax(R, fmax(red[3 + c][0] - (double)sorg[c], (double)sorg[c] - red[c][0]));
+    vorg[4 * v + 3] = __double2float_ru(R);
+  }
+  // per-vertex FP32 data: position at t_n relative to the origin, displacement X1 - X0
+  for (int k = threadIdx.x; k < nv; k += blockDim.x)
+    for (int c = 0; c < 3; ++c) {
+      double x0 = vload(X, mixed, base + (size_t)c * nv + k);
+      double x1 = vload(X, mixed, base + (size_t)(3 + c) * nv + k);
+      fprep[(size_t)v * fstride + (size_t)c * nv + k] = (float)(x0 - (double)sorg[c]);
+      fprep[(size_t)v * fstride + (size_t)(3 + c) * nv + k] = (float)(x1 - x0);
+    }
   // patch boxes: vertex rows [I*BR, min(I*BR+BR, P)], columns [J*BC, J*BC+ncol] (wrapping), poles
   int nbr = stiv_nband_blocks(P), nbc = stiv_ncol_blocks(P), W = 2 * P;
   for (int patch = threadIdx.x; patch < nbr * nbc; patch += blockDim.x) {
@@ -90,7 +111,7 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
           plo[c] = fmin(plo[c], x); phi[c] = fmax(phi[c], x);
         }
     }
-    float* B = pbox + ((size_t)v * STIV_MAX_PATCH + patch) * 6;
+    float* B = pbox + ((size_t)v * pstride + patch) * 6;
     for (int c = 0; c < 3; ++c) { B[c] = __double2float_rd(plo[c]); B[3 + c] = __double2float_ru(phi[c]); }
   }
 }
@@ -308,7 +329,8 @@ int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, const int32_t* p_de
   const double* L = h->prm.box_L;
   {
   STIV_PROF(h, st, "boxes");
-  boxes_kernel<<<n, 256, 0, st>>>(n, p_dev, voff, X, mixed, h->prm.d_m, L[0], L[1], L[2], w.vbox, w.pbox, ctr);
+  boxes_kernel<<<n, 256, 0, st>>>(n, p_dev, voff, X, mixed, h->prm.d_m, L[0], L[1], L[2], w.vbox, w.pbox,
+                                  w.pstride, w.vorg, w.fprep, w.fstride, ctr);
   }
   {
   STIV_PROF_N(h, st, "cells", 4);

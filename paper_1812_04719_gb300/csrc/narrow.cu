@@ -2,18 +2,28 @@
 // directions) and edge-edge pair of a candidate vesicle pair whose swept boxes
 // overlap is tested with the coplanarity cubic of Eq. 3.1 (d_m = 0).
 //
-// The triangulated grid (Sec. 3.1.2, Fig. 3) is cut into patches of 4 x 8 grid
-// quads.  Each primitive belongs to exactly one patch, so a primitive pair is
-// examined by exactly one patch pair:
-//   level 1 (patch_pairs_kernel): per candidate vesicle pair, one warp tests
-//     the FP32 outward-rounded patch boxes and lists overlapping patch pairs;
-//   level 2 (narrow_kernel): per patch pair, one warp stages both patches'
-//     vertices (FP64, the second one shifted by its periodic image) in shared
-//     memory, builds FP32 outward-rounded primitive boxes, keeps the primitive
-//     pairs whose FP32 boxes overlap, and queues them; a full queue is drained
-//     by the whole warp: exact FP64 box test, then the FP64 contact test.
-// FP32 boxes contain the exact FP64 boxes, so the FP32 culling never drops a
-// pair that the exact test keeps.
+// The triangulated grid (Sec. 3.1.2, Fig. 3) is cut into patches of 2 x 4 grid
+// quads; each primitive belongs to exactly one patch, so each primitive pair
+// is examined by exactly one patch pair.
+//   patch_pairs_kernel: per candidate vesicle pair, one warp lists the patch
+//     pairs whose FP32 (outward) boxes overlap;
+//   narrow_kernel (stages 1-3a): per patch pair, one warp stages both patches
+//     in shared memory and filters the primitive pairs; the survivors leave
+//     as global pair descriptors;
+//   pieces_kernel (stage 3b) and fp64_kernel (stage 4) work on those lists,
+//     so that every stage runs on full warps.  The stages:
+//     1. FP32 swept-box test (conservative: never drops an overlapping pair);
+//     2. the exact FP64 swept-box test, on integer order keys of the FP64 bit
+//        patterns (no FP64 instruction; counts the pairs tested);
+//     3. certified FP32 rejection: a pair is dropped only when error-bounded
+//        FP32 arithmetic proves that the FP64 test below cannot report a
+//        contact (Bernstein bound: no root of the cubic in [0,1]; or, on every
+//        sub-interval that may hold a root, the point is certainly outside the
+//        triangle / the edges certainly miss);
+//     4. the FP64 contact test (cubic, root isolation, bisection, inside test)
+//        in the fixed arithmetic order, on the survivors only.
+// Stage 3 never changes a result: the contact list equals the one obtained by
+// running stage 4 on every pair of stage 2 (stiv_params.exact_only = 1).
 #include "stiv_internal.cuh"
 
 #include <math.h>
@@ -22,28 +32,29 @@ namespace {
 
 constexpr int NS = (STIV_BR + 1) * (STIV_BC + 1) + 2;  // vertex slots per patch (+2 poles)
 constexpr int SN = NS - 2, SS = NS - 1;               // pole slots
-constexpr int MAXV = 48, MAXT = 80, MAXE = 128;
-constexpr int NW = 4;                                  // warps per CTA
-constexpr int QCAP = 64;                               // queue entries per warp
+constexpr int MAXV = 16, MAXT = 32, MAXE = 48;
+constexpr int NW = 8;                                  // warps per CTA
+constexpr int QCAP = 64;                               // queue entries
 
 struct PatchSm {
-  double x[6][NS];                 // X0 xyz, X1 xyz per slot (periodic image applied)
-  float flo[3][NS], fhi[3][NS];    // FP32 outward box of each slot over both times
-  int nv, nt, ne;
-  int v_slot[MAXV], v_gid[MAXV];
-  int t_slots[MAXT], t_gid[MAXT];  // 3 slots, 6 bits each
-  int e_slots[MAXE], e_gid[MAXE];  // 2 slots (min vertex id first)
-  float tb[6][MAXT];
-  float eb[6][MAXE];
+  long long key[6][NS];            // exact swept box of each slot: order keys of lo xyz, hi xyz
+  float x[3][NS], d[3][NS];        // FP32: X0 - origin of vesicle i, X1 - X0
+  float lo[3][NS], hi[3][NS];      // FP32 conservative swept box of each slot (frame of vesicle i)
+  int vid[NS];                     // global vertex id of each slot (-1: unused)
+  unsigned char v_slot[MAXV];
+  int t_slots[MAXT];               // 3 slots, 6 bits each
+  int e_slots[MAXE];               // 2 slots (min vertex id first)
   unsigned char vf[MAXV], tf[MAXT], ef[MAXE];
-  int nvf, ntf, nef;
-  float box[6];                    // whole patch
+  int nv, nt, ne, nvf, ntf, nef;
+  int P, I, J, ves;
+  float box[6];
 };
 
 struct WarpSm {
   PatchSm A, B;
-  unsigned q[QCAP];
-  int qn;
+  unsigned q1[QCAP];
+  int n1;
+  float dx;                        // bound on the FP32 position error in this frame
 };
 
 struct narrow_args {
@@ -58,6 +69,13 @@ struct narrow_args {
   const uint64_t* work;
   int64_t W;
   int include_ee;
+  int exact_only;
+  const float* vorg;
+  const float* fprep;
+  int64_t fstride;
+  unsigned long long* q3;   // stage 3b input: (pair << 32) | (type << 30) | (a << 15) | b
+  unsigned long long* q2;   // stage 4 input
+  int64_t Q3, Q2;
   int64_t C;  // raw contact capacity
   int32_t* rc_pair; int32_t* rc_type; int32_t* rc_a; int32_t* rc_b;
   double* rc_tau; double* rc_w;
@@ -66,16 +84,30 @@ struct narrow_args {
 
 __device__ __forceinline__ int slot_of(int rr, int cc) { return rr * (STIV_BC + 1) + cc; }
 
-// Stage patch (I, J) of vesicle v into shared memory; shift s applied to both times.
-__device__ void load_patch(PatchSm& S, const narrow_args& a, int v, int patch, const int* s, int lane) {
+// Order-preserving integer key of a double (-0.0 folded onto +0.0): for finite
+// a, b:  a <= b  <=>  key(a) <= key(b).
+__device__ __forceinline__ long long dkey(double v) {
+  long long b = __double_as_longlong(v);
+  if (b == (long long)0x8000000000000000ull) b = 0;
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+
+// ---------------------------------------------------------------------------
+// staging
+// ---------------------------------------------------------------------------
+// Stage patch `patch` of vesicle v; s: periodic image of the vesicle (applied
+// to both time levels in FP64, as the contact test sees it); off: FP32 offset
+// of this vesicle's frame origin from the frame of the pair.
+__device__ __noinline__ void load_patch(PatchSm& S, const narrow_args& a, int v, int patch, const int* s, const float* off,
+                           float dx, int lane) {
   int P = 2 * a.pv[v], W = 2 * P, nv = stiv_nverts(P);
   int nbr = stiv_nband_blocks(P), nbc = stiv_ncol_blocks(P);
   int I = patch / nbc, J = patch % nbc;
   int r0 = I * STIV_BR, rq = min(STIV_BR, P - r0), c0 = J * STIV_BC, ncol = min(STIV_BC, W - c0);
   bool first = I == 0, last = I == nbr - 1;
   size_t base = a.voff[v];
+  const float* fp = a.fprep + (size_t)v * a.fstride;
   double sh[3] = {s[0] * a.L[0], s[1] * a.L[1], s[2] * a.L[2]};
-  // vertex slots
   for (int k = lane; k < NS; k += 32) {
     int vid = -1;
     if (k < SN) {
@@ -83,173 +115,317 @@ __device__ void load_patch(PatchSm& S, const narrow_args& a, int v, int patch, c
       if (rr <= rq && cc <= ncol) { int col = c0 + cc; if (col >= W) col -= W; vid = (r0 + rr) * W + col; }
     } else if (k == SN && first) vid = W * (P + 1);
     else if (k == SS && last) vid = W * (P + 1) + 1;
+    S.vid[k] = vid;
     if (vid >= 0) {
-      for (int f = 0; f < 6; ++f) {
-        size_t idx = base + (size_t)f * nv + vid;
-        double x = a.mixed ? (double)((const float*)a.X)[idx] : ((const double*)a.X)[idx];
-        int c = f % 3;
-        if (s[c] != 0) x = x + sh[c];
-        S.x[f][k] = x;
-      }
       for (int c = 0; c < 3; ++c) {
-        double lo = fmin(S.x[c][k], S.x[3 + c][k]), hi = fmax(S.x[c][k], S.x[3 + c][k]);
-        S.flo[c][k] = __double2float_rd(lo);
-        S.fhi[c][k] = __double2float_ru(hi);
+        size_t i0 = base + (size_t)c * nv + vid, i1 = base + (size_t)(3 + c) * nv + vid;
+        double x0 = a.mixed ? (double)((const float*)a.X)[i0] : ((const double*)a.X)[i0];
+        double x1 = a.mixed ? (double)((const float*)a.X)[i1] : ((const double*)a.X)[i1];
+        if (s[c] != 0) { x0 = x0 + sh[c]; x1 = x1 + sh[c]; }
+        long long k0 = dkey(x0), k1 = dkey(x1);
+        S.key[c][k] = k0 < k1 ? k0 : k1;
+        S.key[3 + c][k] = k0 < k1 ? k1 : k0;
+        float xf = fp[(size_t)c * nv + vid] + off[c];
+        float df = fp[(size_t)(3 + c) * nv + vid];
+        S.x[c][k] = xf;
+        S.d[c][k] = df;
+        float m = dx + 4.7683716e-7f * (fabsf(xf) + fabsf(df));  // 2^-21 (|x| + |d|)
+        S.lo[c][k] = fminf(xf, xf + df) - m;
+        S.hi[c][k] = fmaxf(xf, xf + df) + m;
       }
     } else {
-      for (int c = 0; c < 3; ++c) { S.flo[c][k] = INFINITY; S.fhi[c][k] = -INFINITY; }
+      for (int c = 0; c < 3; ++c) { S.lo[c][k] = INFINITY; S.hi[c][k] = -INFINITY; }
     }
   }
   __syncwarp();
-  // primitive counts
   int rown = rq + (last ? 1 : 0);
   int nvg = rown * ncol;
   int npole = (first && J == 0 ? 1 : 0) + (last && J == 0 ? 1 : 0);
   int ntq = 2 * rq * ncol;
   int nfan = (first ? ncol : 0) + (last ? ncol : 0);
-  S.nv = nvg + npole;
-  S.nt = ntq + nfan;
-  S.ne = rown * ncol + 2 * rq * ncol + nfan;
-  // vertices
-  for (int k = lane; k < S.nv; k += 32) {
-    int slot, gid;
-    if (k < nvg) {
-      int rr = k / ncol, cc = k % ncol;
-      slot = slot_of(rr, cc); gid = (r0 + rr) * W + c0 + cc;
-    } else if (first && J == 0 && k == nvg) { slot = SN; gid = W * (P + 1); }
-    else { slot = SS; gid = W * (P + 1) + 1; }
-    S.v_slot[k] = slot; S.v_gid[k] = gid;
+  if (lane == 0) {
+    S.nv = nvg + npole; S.nt = ntq + nfan; S.ne = rown * ncol + 2 * rq * ncol + nfan;
+    S.P = P; S.I = I; S.J = J; S.ves = v;
   }
-  // triangles (vertex order of the mesh definition)
-  for (int k = lane; k < S.nt; k += 32) {
-    int s0, s1, s2, gid;
+  for (int k = lane; k < nvg + npole; k += 32) {
+    int slot;
+    if (k < nvg) slot = slot_of(k / ncol, k % ncol);
+    else if (first && J == 0 && k == nvg) slot = SN;
+    else slot = SS;
+    S.v_slot[k] = (unsigned char)slot;
+  }
+  for (int k = lane; k < ntq + nfan; k += 32) {
+    int s0, s1, s2;
     if (k < ntq) {
-      int q = k >> 1, rr = q / ncol, cc = q % ncol, i = r0 + rr, j = c0 + cc;
-      gid = 2 * (i * W + j) + (k & 1);
+      int q = k >> 1, rr = q / ncol, cc = q % ncol;
       if ((k & 1) == 0) { s0 = slot_of(rr, cc); s1 = slot_of(rr + 1, cc); s2 = slot_of(rr + 1, cc + 1); }
       else { s0 = slot_of(rr, cc); s1 = slot_of(rr + 1, cc + 1); s2 = slot_of(rr, cc + 1); }
     } else {
       int k2 = k - ntq;
-      if (first && k2 < ncol) {
-        int cc = k2; gid = 4 * P * P + c0 + cc;
-        s0 = SN; s1 = slot_of(0, cc); s2 = slot_of(0, cc + 1);
-      } else {
-        int cc = first ? k2 - ncol : k2; gid = 4 * P * P + W + c0 + cc;
-        s0 = SS; s1 = slot_of(rq, cc + 1); s2 = slot_of(rq, cc);
-      }
+      if (first && k2 < ncol) { s0 = SN; s1 = slot_of(0, k2); s2 = slot_of(0, k2 + 1); }
+      else { int cc = first ? k2 - ncol : k2; s0 = SS; s1 = slot_of(rq, cc + 1); s2 = slot_of(rq, cc); }
     }
-    S.t_slots[k] = s0 | (s1 << 6) | (s2 << 12); S.t_gid[k] = gid;
-    for (int c = 0; c < 3; ++c) {
-      S.tb[c][k] = fminf(S.flo[c][s0], fminf(S.flo[c][s1], S.flo[c][s2]));
-      S.tb[3 + c][k] = fmaxf(S.fhi[c][s0], fmaxf(S.fhi[c][s1], S.fhi[c][s2]));
-    }
+    S.t_slots[k] = s0 | (s1 << 6) | (s2 << 12);
   }
-  // edges: ring edges of owned vertices, then meridian / diagonal edges of owned quads, then pole edges
-  for (int k = lane; k < S.ne; k += 32) {
-    int sa, sb, va, vb;
+  for (int k = lane; k < rown * ncol + 2 * rq * ncol + nfan; k += 32) {
+    int sa, sb;
     int nh = rown * ncol;
     if (k < nh) {
-      int rr = k / ncol, cc = k % ncol, i = r0 + rr, j = c0 + cc, jn = j + 1 == W ? 0 : j + 1;
-      sa = slot_of(rr, cc); sb = slot_of(rr, cc + 1); va = i * W + j; vb = i * W + jn;
+      int rr = k / ncol, cc = k % ncol;
+      sa = slot_of(rr, cc); sb = slot_of(rr, cc + 1);
     } else if (k < nh + 2 * rq * ncol) {
-      int k2 = k - nh, q = k2 >> 1, rr = q / ncol, cc = q % ncol, i = r0 + rr, j = c0 + cc;
-      int jn = j + 1 == W ? 0 : j + 1;
-      sa = slot_of(rr, cc); va = i * W + j;
-      if ((k2 & 1) == 0) { sb = slot_of(rr + 1, cc); vb = (i + 1) * W + j; }
-      else { sb = slot_of(rr + 1, cc + 1); vb = (i + 1) * W + jn; }
+      int k2 = k - nh, q = k2 >> 1, rr = q / ncol, cc = q % ncol;
+      sa = slot_of(rr, cc);
+      sb = ((k2 & 1) == 0) ? slot_of(rr + 1, cc) : slot_of(rr + 1, cc + 1);
     } else {
       int k2 = k - nh - 2 * rq * ncol;
-      if (first && k2 < ncol) { int cc = k2; sa = slot_of(0, cc); va = c0 + cc; sb = SN; vb = W * (P + 1); }
-      else {
-        int cc = first ? k2 - ncol : k2;
-        sa = slot_of(rq, cc); va = P * W + c0 + cc; sb = SS; vb = W * (P + 1) + 1;
-      }
+      if (first && k2 < ncol) { sa = slot_of(0, k2); sb = SN; }
+      else { int cc = first ? k2 - ncol : k2; sa = slot_of(rq, cc); sb = SS; }
     }
-    if (vb < va) { int t = va; va = vb; vb = t; t = sa; sa = sb; sb = t; }
-    S.e_slots[k] = sa | (sb << 6); S.e_gid[k] = stiv_edge_index(P, va, vb);
-    for (int c = 0; c < 3; ++c) {
-      S.eb[c][k] = fminf(S.flo[c][sa], S.flo[c][sb]);
-      S.eb[3 + c][k] = fmaxf(S.fhi[c][sa], S.fhi[c][sb]);
-    }
+    if (S.vid[sb] < S.vid[sa]) { int t = sa; sa = sb; sb = t; }
+    S.e_slots[k] = sa | (sb << 6);
   }
   __syncwarp();
-  // whole-patch box
   if (lane < 6) {
     float acc = lane < 3 ? INFINITY : -INFINITY;
     int c = lane % 3;
-    for (int k = 0; k < NS; ++k) acc = lane < 3 ? fminf(acc, S.flo[c][k]) : fmaxf(acc, S.fhi[c][k]);
+    for (int k = 0; k < NS; ++k) acc = lane < 3 ? fminf(acc, S.lo[c][k]) : fmaxf(acc, S.hi[c][k]);
     S.box[lane] = acc;
   }
   __syncwarp();
 }
 
-__device__ __forceinline__ bool fbox_hit(const float* lo_a, const float* hi_a, const float* b) {
-  return lo_a[0] <= b[3] && b[0] <= hi_a[0] && lo_a[1] <= b[4] && b[1] <= hi_a[1] && lo_a[2] <= b[5] && b[2] <= hi_a[2];
+// Global id of primitive k of a staged patch (vertex id, triangle id, or edge index).
+__device__ int prim_gid(const PatchSm& S, int kind, int k) {
+  int P = S.P, W = 2 * P;
+  int r0 = S.I * STIV_BR, rq = min(STIV_BR, P - r0), c0 = S.J * STIV_BC, ncol = min(STIV_BC, W - c0);
+  bool first = S.I == 0;
+  if (kind == 0) return S.vid[S.v_slot[k]];
+  if (kind == 1) {
+    int ntq = 2 * rq * ncol;
+    if (k < ntq) { int q = k >> 1, rr = q / ncol, cc = q % ncol; return 2 * ((r0 + rr) * W + c0 + cc) + (k & 1); }
+    int k2 = k - ntq;
+    if (first && k2 < ncol) return 4 * P * P + c0 + k2;
+    return 4 * P * P + W + c0 + (first ? k2 - ncol : k2);
+  }
+  int e = S.e_slots[k];
+  return stiv_edge_index(P, S.vid[e & 63], S.vid[(e >> 6) & 63]);
 }
 
-// Compact the primitives of S that overlap box ob (FP32) into S.*f lists.
+__device__ __forceinline__ void slot_box(const PatchSm& S, int sl, float* b) {
+  b[0] = S.lo[0][sl]; b[1] = S.lo[1][sl]; b[2] = S.lo[2][sl];
+  b[3] = S.hi[0][sl]; b[4] = S.hi[1][sl]; b[5] = S.hi[2][sl];
+}
+__device__ __forceinline__ void merge_box(const PatchSm& S, int sl, float* b) {
+  b[0] = fminf(b[0], S.lo[0][sl]); b[1] = fminf(b[1], S.lo[1][sl]); b[2] = fminf(b[2], S.lo[2][sl]);
+  b[3] = fmaxf(b[3], S.hi[0][sl]); b[4] = fmaxf(b[4], S.hi[1][sl]); b[5] = fmaxf(b[5], S.hi[2][sl]);
+}
+__device__ __forceinline__ void tri_box(const PatchSm& S, int k, float* b) {
+  int t = S.t_slots[k];
+  slot_box(S, t & 63, b); merge_box(S, (t >> 6) & 63, b); merge_box(S, (t >> 12) & 63, b);
+}
+__device__ __forceinline__ void edge_box(const PatchSm& S, int k, float* b) {
+  int e = S.e_slots[k];
+  slot_box(S, e & 63, b); merge_box(S, (e >> 6) & 63, b);
+}
+__device__ __forceinline__ bool fbox_hit(const float* a, const float* b) {
+  return a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] && b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
+}
+
+// Compact the primitives of S whose FP32 boxes overlap box ob.
 __device__ void filter_patch(PatchSm& S, const float* ob, int lane) {
-  int base;
-  base = 0;
-  for (int k0 = 0; k0 < S.nv; k0 += 32) {
-    int k = k0 + lane;
-    bool hit = false;
-    if (k < S.nv) {
-      int sl = S.v_slot[k];
-      float lo[3] = {S.flo[0][sl], S.flo[1][sl], S.flo[2][sl]}, hi[3] = {S.fhi[0][sl], S.fhi[1][sl], S.fhi[2][sl]};
-      hit = fbox_hit(lo, hi, ob);
+  for (int kind = 0; kind < 3; ++kind) {
+    int n = kind == 0 ? S.nv : kind == 1 ? S.nt : S.ne;
+    unsigned char* out = kind == 0 ? S.vf : kind == 1 ? S.tf : S.ef;
+    int base = 0;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+      int k = k0 + lane;
+      bool hit = false;
+      if (k < n) {
+        float b[6];
+        if (kind == 0) slot_box(S, S.v_slot[k], b);
+        else if (kind == 1) tri_box(S, k, b);
+        else edge_box(S, k, b);
+        hit = fbox_hit(b, ob);
+      }
+      unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (hit) out[base + __popc(m & ((1u << lane) - 1u))] = (unsigned char)k;
+      base += __popc(m);
     }
-    unsigned m = __ballot_sync(0xffffffffu, hit);
-    if (hit) S.vf[base + __popc(m & ((1u << lane) - 1u))] = (unsigned char)k;
-    base += __popc(m);
+    if (lane == 0) { if (kind == 0) S.nvf = base; else if (kind == 1) S.ntf = base; else S.nef = base; }
   }
-  if (lane == 0) S.nvf = base;
-  base = 0;
-  for (int k0 = 0; k0 < S.nt; k0 += 32) {
-    int k = k0 + lane;
-    bool hit = false;
-    if (k < S.nt) {
-      float lo[3] = {S.tb[0][k], S.tb[1][k], S.tb[2][k]}, hi[3] = {S.tb[3][k], S.tb[4][k], S.tb[5][k]};
-      hit = fbox_hit(lo, hi, ob);
-    }
-    unsigned m = __ballot_sync(0xffffffffu, hit);
-    if (hit) S.tf[base + __popc(m & ((1u << lane) - 1u))] = (unsigned char)k;
-    base += __popc(m);
-  }
-  if (lane == 0) S.ntf = base;
-  base = 0;
-  for (int k0 = 0; k0 < S.ne; k0 += 32) {
-    int k = k0 + lane;
-    bool hit = false;
-    if (k < S.ne) {
-      float lo[3] = {S.eb[0][k], S.eb[1][k], S.eb[2][k]}, hi[3] = {S.eb[3][k], S.eb[4][k], S.eb[5][k]};
-      hit = fbox_hit(lo, hi, ob);
-    }
-    unsigned m = __ballot_sync(0xffffffffu, hit);
-    if (hit) S.ef[base + __popc(m & ((1u << lane) - 1u))] = (unsigned char)k;
-    base += __popc(m);
-  }
-  if (lane == 0) S.nef = base;
   __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
-// Eq. 3.1 (d_m = 0): earliest contact time of one primitive pair in FP64
+// certified FP32 rejection
+// ---------------------------------------------------------------------------
+struct f3 { float x, y, z; };
+__device__ __forceinline__ f3 fsub(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 fadd(f3 a, f3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ f3 fcross(f3 u, f3 v) {
+  return {fmaf(u.y, v.z, -(u.z * v.y)), fmaf(u.z, v.x, -(u.x * v.z)), fmaf(u.x, v.y, -(u.y * v.x))};
+}
+__device__ __forceinline__ float fdot(f3 u, f3 v) { return fmaf(u.z, v.z, fmaf(u.y, v.y, u.x * v.x)); }
+__device__ __forceinline__ float fnorm(f3 u) { return sqrtf(fdot(u, u)); }
+__device__ __forceinline__ f3 fat(f3 x, float t, f3 d) { return {fmaf(t, d.x, x.x), fmaf(t, d.y, x.y), fmaf(t, d.z, x.z)}; }
+__device__ __forceinline__ float amax3(f3 u) { return fmaxf(fabsf(u.x), fmaxf(fabsf(u.y), fabsf(u.z))); }
+
+constexpr float U32 = 5.9604645e-8f;   // 2^-24, unit roundoff of float
+
+// Sign of (g1 x g2) . (g3 x g4) over t in [tm - h, tm + h], each g linear in t
+// (value gv at tm, rate gd).  eg bounds the error of each component of each
+// gv.  |(g1 x g2) . (g3 x g4)| <= |g1||g2||g3||g4|, so the change over the
+// interval is at most sum_i h|gd_i| prod_{j != i} max|g_j|.  Returns +1
+// (certainly > 0), -1 (certainly < 0) or 0.
+__device__ int form_sign(const f3* gv, const f3* gd, float h, float eg) {
+  float val = fdot(fcross(gv[0], gv[1]), fcross(gv[2], gv[3]));
+  float M[4], R[4];
+  for (int i = 0; i < 4; ++i) {
+    R[i] = h * fnorm(gd[i]);
+    M[i] = fnorm(gv[i]) + R[i] + 2.0f * eg;
+  }
+  float p01 = M[0] * M[1], p23 = M[2] * M[3];
+  float prod = p01 * p23;
+  float var = R[0] * M[1] * p23 + M[0] * R[1] * p23 + p01 * R[2] * M[3] + p01 * M[2] * R[3];
+  float inp = 2.0f * eg * (M[1] * p23 + M[0] * p23 + p01 * M[3] + p01 * M[2]);
+  float rad = (var + inp + 64.0f * U32 * prod) * 1.001f;
+  if (val > rad) return 1;
+  if (val < -rad) return -1;
+  return 0;
+}
+
+// For every contact time in [t0, t0 + w], is the point certainly outside the
+// triangle / are the edges certainly apart (1), certainly inside (2), or
+// undecided (0)?  Points: VF xp, x0, x1, x2; EE p0, p1, q0, q1.
+// ep, ed: error bounds of the FP32 positions / displacements per component.
+__device__ int inside_cert(int kind, const f3* x, const f3* d, float t0, float w, float ep, float ed) {
+  float h = 0.5f * w + 1e-6f;           // half width, widened past the FP64 root's last ulp
+  float tm = t0 + 0.5f * w;
+  f3 P[4];
+  for (int q = 0; q < 4; ++q) P[q] = fat(x[q], tm, d[q]);
+  float pm = fmaxf(fmaxf(amax3(P[0]), amax3(P[1])), fmaxf(amax3(P[2]), amax3(P[3])));
+  float eg = 2.0f * (ep + ed) + 4.0f * U32 * pm;  // per component, differences of positions at tm
+  f3 gv[4], gd[4];
+  if (kind == 0) {
+    // barycentric weight of T_k ~ ((T_{k+2} - T_{k+1}) x (p - T_{k+1})) . n,  n = (T1 - T0) x (T2 - T0)
+    gv[2] = fsub(P[2], P[1]); gd[2] = fsub(d[2], d[1]);
+    gv[3] = fsub(P[3], P[1]); gd[3] = fsub(d[3], d[1]);
+    bool all_in = true;
+    for (int k = 0; k < 3; ++k) {
+      int a1 = 1 + (k + 1) % 3, a2 = 1 + (k + 2) % 3;
+      gv[0] = fsub(P[a2], P[a1]); gd[0] = fsub(d[a2], d[a1]);
+      gv[1] = fsub(P[0], P[a1]); gd[1] = fsub(d[0], d[a1]);
+      int sg = form_sign(gv, gd, h, eg);
+      if (sg < 0) return 1;
+      if (sg <= 0) all_in = false;
+    }
+    return all_in ? 2 : 0;
+  }
+  // EE with m = (p1 - p0) x (q1 - q0):  s ~ ((q0 - p0) x (q1 - q0)) . m,
+  // s - 1 ~ ((q0 - p1) x (q1 - q0)) . m,  u ~ ((q0 - p0) x (p1 - p0)) . m,
+  // u - 1 ~ ((q1 - p0) x (p1 - p0)) . m   (each divided by |m|^2)
+  f3 e1v = fsub(P[1], P[0]), e1d = fsub(d[1], d[0]);
+  f3 e2v = fsub(P[3], P[2]), e2d = fsub(d[3], d[2]);
+  const int va[4] = {2, 2, 2, 3}, vb[4] = {0, 1, 0, 0};
+  int sgn[4];
+  for (int k = 0; k < 4; ++k) {
+    gv[0] = fsub(P[va[k]], P[vb[k]]); gd[0] = fsub(d[va[k]], d[vb[k]]);
+    gv[1] = k < 2 ? e2v : e1v; gd[1] = k < 2 ? e2d : e1d;
+    gv[2] = e1v; gd[2] = e1d;
+    gv[3] = e2v; gd[3] = e2d;
+    sgn[k] = form_sign(gv, gd, h, eg);
+  }
+  if (sgn[0] < 0 || sgn[1] > 0 || sgn[2] < 0 || sgn[3] > 0) return 1;
+  if (sgn[0] > 0 && sgn[1] < 0 && sgn[2] > 0 && sgn[3] < 0) return 2;
+  return 0;
+}
+
+// Coefficients of the coplanarity cubic in FP32 and a bound E on the error of
+// any value of the cubic (or of its Bernstein coefficients on any sub-interval
+// of [0, 1]) against the exact cubic of the FP64 inputs.  Every coefficient is
+// a sum of <= 18 products of three difference components; A / Ad bound the
+// position / displacement differences, ep / ed the input errors.
+struct cubic32 { float k0, k1, k2, k3, E, ed; };
+
+__device__ __forceinline__ cubic32 cubic_fp32(int kind, const f3* x, const f3* d, float ep) {
+  f3 a, b, c, da, db, dc;
+  if (kind == 0) {
+    a = fsub(x[2], x[1]); b = fsub(x[3], x[1]); c = fsub(x[0], x[1]);
+    da = fsub(d[2], d[1]); db = fsub(d[3], d[1]); dc = fsub(d[0], d[1]);
+  } else {
+    a = fsub(x[1], x[0]); b = fsub(x[3], x[2]); c = fsub(x[2], x[0]);
+    da = fsub(d[1], d[0]); db = fsub(d[3], d[2]); dc = fsub(d[2], d[0]);
+  }
+  f3 n0 = fcross(a, b);
+  f3 n1 = fadd(fcross(da, b), fcross(a, db));
+  f3 n2 = fcross(da, db);
+  cubic32 r;
+  r.k0 = fdot(c, n0);
+  r.k1 = fdot(dc, n0) + fdot(c, n1);
+  r.k2 = fdot(c, n2) + fdot(dc, n1);
+  r.k3 = fdot(dc, n2);
+  float A = fmaxf(amax3(a), fmaxf(amax3(b), amax3(c)));
+  float Ad = fmaxf(amax3(da), fmaxf(amax3(db), amax3(dc)));
+  float Dm = 0.f;
+  for (int q = 0; q < 4; ++q) Dm = fmaxf(Dm, amax3(d[q]));
+  float ed = 2.0f * U32 * Dm + 1e-12f;           // |d - D| per component (float rounding of X1 - X0)
+  float epd = 2.0f * ep + 2.0f * U32 * A;        // per position-difference component
+  float edd = 2.0f * ed + 2.0f * U32 * Ad;       // per displacement-difference component
+  float rr = 8.0f * U32;                         // rounding per term
+  float E0 = 6.f * (3.f * epd * A * A + rr * A * A * A);
+  float E1 = 18.f * (edd * A * A + 2.f * epd * Ad * A + rr * Ad * A * A);
+  float E2 = 18.f * (epd * Ad * Ad + 2.f * edd * A * Ad + rr * A * Ad * Ad);
+  float E3 = 6.f * (3.f * edd * Ad * Ad + rr * Ad * Ad * Ad);
+  float S = fabsf(r.k0) + fabsf(r.k1) + fabsf(r.k2) + fabsf(r.k3);
+  float M = (A + Ad) * (A + Ad) * (A + Ad);
+  r.E = 1.25f * (E0 + E1 + E2 + E3) + 64.f * U32 * S + 1e-12f * 48.f * M;
+  r.ed = ed;
+  return r;
+}
+
+__device__ __forceinline__ bool certain_sign4(float c0, float c1, float c2, float c3, float E) {
+  return (c0 > E && c1 > E && c2 > E && c3 > E) || (c0 < -E && c1 < -E && c2 < -E && c3 < -E);
+}
+
+// Stage 3a: 1 if the cubic certainly has no root in [0, 1] (Bernstein
+// coefficients of one sign), 0 otherwise (also when it may vanish
+// identically, which the FP64 test reports as degenerate).
+__device__ int bernstein_reject(const cubic32& q) {
+  if (fabsf(q.k0) <= q.E && fabsf(q.k1) <= q.E && fabsf(q.k2) <= q.E && fabsf(q.k3) <= q.E) return 0;
+  float b1 = q.k0 + q.k1 * (1.f / 3.f), b2 = q.k0 + (2.f * q.k1 + q.k2) * (1.f / 3.f), b3 = q.k0 + q.k1 + q.k2 + q.k3;
+  return certain_sign4(q.k0, b1, b2, b3, q.E) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 3.1 (d_m = 0): earliest contact time of one primitive pair in FP64.
+// Comparisons are done on the bit patterns (integer pipe); the arithmetic is
+// the fixed FP64 sequence of the method definition.
 // ---------------------------------------------------------------------------
 enum { KIND_VF = 0, KIND_EE = 1 };
+
+__device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
+__device__ __forceinline__ bool is_neg(double v) {  // v < 0.0
+  long long b = __double_as_longlong(v);
+  return b < 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ bool is_pos(double v) { return __double_as_longlong(v) > 0; }  // v > 0.0, v not NaN
 
 // FP64 flops of the procedure, counted as executed (fma = 2): the
 // algorithmic work of the exact contact test, reported for the roofline.
 __device__ double bisect64(double k0, double k1, double k2, double k3, double lo, double hi, double flo,
                            long long& flops) {
+  bool neg_lo = is_neg(flo);
   for (int it = 0; it < 64; ++it) {
     double mid = __dmul_rn(__dadd_rn(lo, hi), 0.5);
     flops += 2;
-    if (!(mid > lo && mid < hi)) break;
+    // lo, mid, hi are non-negative: compare bit patterns
+    long long bm = __double_as_longlong(mid);
+    if (!(bm > __double_as_longlong(lo) && bm < __double_as_longlong(hi))) break;
     flops += 6;
     double fm = horner3(k0, k1, k2, k3, mid);
-    if (fm == 0.0) return mid;
-    if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; }
+    if (is_zero(fm)) return mid;
+    if (is_neg(fm) == neg_lo) lo = mid;
     else hi = mid;
   }
   return lo;
@@ -262,21 +438,24 @@ __device__ int inside64(int kind, const d3* Y, double& w1, double& w2) {
     d3 a = d3_sub(Y[2], Y[1]), b = d3_sub(Y[3], Y[1]), c = d3_sub(Y[0], Y[1]);
     double d00 = d3_dot(a, a), d01 = d3_dot(a, b), d11 = d3_dot(b, b), d20 = d3_dot(c, a), d21 = d3_dot(c, b);
     double den = __fma_rn(d00, d11, -__dmul_rn(d01, d01));
-    if (!(den > 0.0)) return -1;
+    if (!is_pos(den)) return -1;
     double b1 = __ddiv_rn(__fma_rn(d11, d20, -__dmul_rn(d01, d21)), den);
     double b2 = __ddiv_rn(__fma_rn(d00, d21, -__dmul_rn(d01, d20)), den);
     double b0 = __dsub_rn(__dsub_rn(1.0, b1), b2);
     w1 = b1; w2 = b2;
-    return (b0 >= 0.0 && b1 >= 0.0 && b2 >= 0.0) ? 1 : 0;
+    return (!is_neg(b0) && !is_neg(b1) && !is_neg(b2)) ? 1 : 0;
   } else {
     d3 d1 = d3_sub(Y[1], Y[0]), d2 = d3_sub(Y[3], Y[2]), r = d3_sub(Y[0], Y[2]);
     double A = d3_dot(d1, d1), B = d3_dot(d1, d2), E = d3_dot(d2, d2), C = d3_dot(d1, r), F = d3_dot(d2, r);
     double den = __fma_rn(A, E, -__dmul_rn(B, B));
-    if (!(den > 0.0)) return -1;
+    if (!is_pos(den)) return -1;
     double s = __ddiv_rn(__fma_rn(B, F, -__dmul_rn(C, E)), den);
     double u = __ddiv_rn(__fma_rn(A, F, -__dmul_rn(B, C)), den);
     w1 = s; w2 = u;
-    return (s >= 0.0 && s <= 1.0 && u >= 0.0 && u <= 1.0) ? 1 : 0;
+    const long long one = 0x3FF0000000000000ll;
+    bool s_le1 = is_neg(s) || __double_as_longlong(s) <= one;
+    bool u_le1 = is_neg(u) || __double_as_longlong(u) <= one;
+    return (!is_neg(s) && s_le1 && !is_neg(u) && u_le1) ? 1 : 0;
   }
 }
 
@@ -298,21 +477,20 @@ __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w
   double k1 = __dadd_rn(d3_dot(dc, n0), d3_dot(c, n1));
   double k2 = __dadd_rn(d3_dot(c, n2), d3_dot(dc, n1));
   double k3 = d3_dot(dc, n2);
-  if (k0 == 0.0 && k1 == 0.0 && k2 == 0.0 && k3 == 0.0) return 2;
-  // critical points of the cubic inside (0, 1)
+  if (is_zero(k0) && is_zero(k1) && is_zero(k2) && is_zero(k3)) return 2;
   double e0 = k1, e1 = __dmul_rn(2.0, k2), e2 = __dmul_rn(3.0, k3);
   double r[2]; int nr = 0;
   flops += 2;
-  if (e2 != 0.0) {
+  if (!is_zero(e2)) {
     double disc = __fma_rn(e1, e1, -__dmul_rn(__dmul_rn(4.0, e2), e0));
     flops += 4;
-    if (disc > 0.0) {
+    if (is_pos(disc)) {
       flops += 6;
       double sq = __dsqrt_rn(disc);
-      double q = __dmul_rn(-0.5, __dadd_rn(e1, e1 >= 0.0 ? sq : -sq));
+      double q = __dmul_rn(-0.5, __dadd_rn(e1, !is_neg(e1) ? sq : -sq));
       r[0] = __ddiv_rn(q, e2); r[1] = __ddiv_rn(e0, q); nr = 2;
     }
-  } else if (e1 != 0.0) {
+  } else if (!is_zero(e1)) {
     r[0] = __ddiv_rn(-e0, e1); nr = 1;
   }
   double cp[2]; int ncp = 0;
@@ -330,9 +508,9 @@ __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w
     double l = ends[s], rr = ends[s + 1];
     double fl = horner3(k0, k1, k2, k3, l), fr = horner3(k0, k1, k2, k3, rr), t;
     flops += 12;
-    if (fl == 0.0) t = l;
-    else if (fr == 0.0) t = rr;
-    else if ((fl < 0.0) != (fr < 0.0)) t = bisect64(k0, k1, k2, k3, l, rr, fl, flops);
+    if (is_zero(fl)) t = l;
+    else if (is_zero(fr)) t = rr;
+    else if (is_neg(fl) != is_neg(fr)) t = bisect64(k0, k1, k2, k3, l, rr, fl, flops);
     else continue;
     flops += 24 + 9 + 25 + 3 + 6 + 2 + 2;  // positions, differences, dots, determinant, numerators, divisions
     d3 Y[4];
@@ -345,115 +523,182 @@ __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w
   return degen ? 2 : 0;
 }
 
-__device__ __forceinline__ d3 slot_pos(const PatchSm& S, int t, int sl) {
-  return {S.x[3 * t + 0][sl], S.x[3 * t + 1][sl], S.x[3 * t + 2][sl]};
+// ---------------------------------------------------------------------------
+// stages 2-4 on queued pairs
+// ---------------------------------------------------------------------------
+// queue entry: kind (0 = VF A->B, 1 = VF B->A, 2 = EE) << 16 | x << 8 | y
+__device__ __forceinline__ void entry_slots(const WarpSm& ws, unsigned e, int& kind, int& x, int& y, int* sl,
+                                            const PatchSm*& SA, const PatchSm*& SB) {
+  kind = e >> 16; x = (e >> 8) & 0xFF; y = e & 0xFF;
+  SA = (kind == 1) ? &ws.B : &ws.A;   // side holding the first primitive (vertex / edge)
+  SB = (kind == 1) ? &ws.A : &ws.B;
+  if (kind < 2) {
+    sl[0] = SA->v_slot[x];
+    int t = SB->t_slots[y];
+    sl[1] = t & 63; sl[2] = (t >> 6) & 63; sl[3] = (t >> 12) & 63;
+  } else {
+    int ea = SA->e_slots[x], eb = SB->e_slots[y];
+    sl[0] = ea & 63; sl[1] = (ea >> 6) & 63; sl[2] = eb & 63; sl[3] = (eb >> 6) & 63;
+  }
 }
 
-// Drain up to n queued pairs, one per lane.
-__device__ void process_queue(WarpSm& ws, int n, int lane, int r, const narrow_args& a, long long& nprim,
-                              long long& ndeg, long long& flops) {
-  int type = -1, ga = 0, gb = 0;
-  double tau = 0.0, w1 = 0.0, w2 = 0.0;
+__device__ __forceinline__ const PatchSm& point_side(int kind, int q, const PatchSm* SA, const PatchSm* SB) {
+  return (q == 0 || (kind == 2 && q == 1)) ? *SA : *SB;
+}
+
+// ---------------------------------------------------------------------------
+// global pair descriptors (stages 3b and 4)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long make_desc(int r, int type, int ga, int gb) {
+  return ((unsigned long long)(unsigned)r << 32) | ((unsigned long long)type << 30) | ((unsigned long long)ga << 15) |
+         (unsigned long long)gb;
+}
+
+// The 4 points of a descriptor: vesicle, vertex id, and whether the point
+// belongs to vesicle j (periodic image applied).
+__device__ __forceinline__ void desc_points(const narrow_args& a, unsigned long long e, int& r, int& type, int& ga,
+                                            int& gb, int* ves, int* vid, bool* onj) {
+  r = (int)(e >> 32); type = (int)((e >> 30) & 3); ga = (int)((e >> 15) & 0x7FFF); gb = (int)(e & 0x7FFF);
+  int vi = a.ci[r], vj = a.cj[r];
+  if (type < 2) {
+    int vv = type == 0 ? vi : vj, vt = type == 0 ? vj : vi;
+    ves[0] = vv; vid[0] = ga; onj[0] = type == 1;
+    int tv[3];
+    stiv_tri_verts(2 * a.pv[vt], gb, tv);
+    for (int q = 0; q < 3; ++q) { ves[1 + q] = vt; vid[1 + q] = tv[q]; onj[1 + q] = type == 0; }
+  } else {
+    int u, v;
+    stiv_edge_verts(2 * a.pv[vi], ga, &u, &v);
+    ves[0] = vi; vid[0] = u; ves[1] = vi; vid[1] = v; onj[0] = onj[1] = false;
+    stiv_edge_verts(2 * a.pv[vj], gb, &u, &v);
+    ves[2] = vj; vid[2] = u; ves[3] = vj; vid[3] = v; onj[2] = onj[3] = true;
+  }
+}
+
+// FP32 frame of pair r: origin of vesicle i; offset of vesicle j's origin
+// (with its periodic image) and the bound on the FP32 position error.
+__device__ __forceinline__ float pair_frame(const narrow_args& a, int r, float* offB) {
+  int vi = a.ci[r], vj = a.cj[r], code = a.cs[r];
+  int s1[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
+  float dmax = 0.f;
+  for (int c = 0; c < 3; ++c) {
+    double o = ((double)a.vorg[4 * vj + c] + s1[c] * a.L[c]) - (double)a.vorg[4 * vi + c];
+    offB[c] = (float)o;
+    dmax = fmaxf(dmax, fabsf(offB[c]));
+  }
+  // |FP32 position - exact position| per component: rounding of X0 - origin,
+  // of the frame offset and of the frame change (generous)
+  return 2.3841858e-7f * (a.vorg[4 * vi + 3] + a.vorg[4 * vj + 3] + 2.0f * dmax);  // 2^-22 (...)
+}
+
+// FP32 points of a descriptor in the frame of its pair (for stage 3b).
+__device__ __forceinline__ void desc_points_f32(const narrow_args& a, unsigned long long e, int& kind, f3* xq, f3* dq,
+                                                float& ep) {
+  int r, ty, ga, gb, ves[4], vid[4];
+  bool onj[4];
+  desc_points(a, e, r, ty, ga, gb, ves, vid, onj);
+  float offB[3];
+  ep = pair_frame(a, r, offB);
+  kind = ty == 2 ? 1 : 0;
+  for (int q = 0; q < 4; ++q) {
+    int nv = stiv_nverts(2 * a.pv[ves[q]]);
+    const float* fp = a.fprep + (size_t)ves[q] * a.fstride + vid[q];
+    float o0 = onj[q] ? offB[0] : 0.f, o1 = onj[q] ? offB[1] : 0.f, o2 = onj[q] ? offB[2] : 0.f;
+    xq[q] = {fp[0] + o0, fp[(size_t)nv] + o1, fp[(size_t)2 * nv] + o2};
+    dq[q] = {fp[(size_t)3 * nv], fp[(size_t)4 * nv], fp[(size_t)5 * nv]};
+  }
+}
+
+// Append a descriptor to a global list (warp-aggregated; lanes with keep).
+__device__ __forceinline__ void push_global(unsigned long long* list, int64_t cap, int64_t* count, int64_t* status,
+                                            bool keep, unsigned long long e, int lane) {
+  unsigned m = __ballot_sync(0xffffffffu, keep);
+  if (!m) return;
+  unsigned long long base = 0;
+  int leader = __ffs(m) - 1;
+  if (lane == leader) base = atomicAdd((unsigned long long*)count, (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (keep) {
+    int64_t k = (int64_t)base + __popc(m & ((1u << lane) - 1u));
+    if (k < cap) list[k] = e;
+    else atomicOr((unsigned long long*)status, STIV_F_WORK_OVERFLOW);
+  }
+}
+
+__device__ __forceinline__ void load_f32(const int* sl, int kind, const PatchSm* SA, const PatchSm* SB, f3* xq,
+                                         f3* dq) {
+  for (int q = 0; q < 4; ++q) {
+    const PatchSm& S = point_side(kind, q, SA, SB);
+    xq[q] = {S.x[0][sl[q]], S.x[1][sl[q]], S.x[2][sl[q]]};
+    dq[q] = {S.d[0][sl[q]], S.d[1][sl[q]], S.d[2][sl[q]]};
+  }
+}
+
+// Stage 2 (exact box) and 3a (Bernstein) on up to n entries of q1; survivors
+// go to the global list of stage 3b (of stage 4 when the FP32 rejection is
+// off) as descriptors.
+__device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, const narrow_args& a,
+                                          long long& nprim) {
+  bool keep = false;
+  unsigned long long desc = 0;
   if (lane < n) {
-    unsigned e = ws.q[lane];
-    int kind = e >> 16, x = (e >> 8) & 0xFF, y = e & 0xFF;
-    const PatchSm& SA = (kind == 1) ? ws.B : ws.A;   // side holding the first primitive
-    const PatchSm& SB = (kind == 1) ? ws.A : ws.B;
-    int sl[4];
-    if (kind < 2) {
-      sl[0] = SA.v_slot[x];
-      int t = SB.t_slots[y];
-      sl[1] = t & 63; sl[2] = (t >> 6) & 63; sl[3] = (t >> 12) & 63;
-    } else {
-      int ea = SA.e_slots[x], eb = SB.e_slots[y];
-      sl[0] = ea & 63; sl[1] = (ea >> 6) & 63; sl[2] = eb & 63; sl[3] = (eb >> 6) & 63;
-    }
-    d3 X0[4], X1[4], D[4];
-    // points 0 (and 1 for EE) come from SA, the rest from SB
-    for (int q = 0; q < 4; ++q) {
-      const PatchSm& S = (q == 0 || (kind == 2 && q == 1)) ? SA : SB;
-      X0[q] = slot_pos(S, 0, sl[q]); X1[q] = slot_pos(S, 1, sl[q]);
-      D[q] = d3_sub(X1[q], X0[q]);
-    }
-    // exact FP64 swept-box overlap of the two primitives
+    unsigned e = ws.q1[lane];
+    int kind, x, y, sl[4];
+    const PatchSm *SA, *SB;
+    entry_slots(ws, e, kind, x, y, sl, SA, SB);
+    // exact FP64 swept-box overlap (order keys)
     int na = kind == 2 ? 2 : 1;
     bool hit = true;
-    {
-      double alo[3], ahi[3], blo[3], bhi[3];
-      const double* X0c = &X0[0].x; const double* X1c = &X1[0].x;
-      for (int c = 0; c < 3; ++c) {
-        alo[c] = ahi[c] = X0c[c];
-        for (int q = 0; q < 4; ++q) {
-          double u = X0c[3 * q + c], v = X1c[3 * q + c];
-          if (q < na) {
-            alo[c] = fmin(alo[c], fmin(u, v)); ahi[c] = fmax(ahi[c], fmax(u, v));
-          } else if (q == na) {
-            blo[c] = fmin(u, v); bhi[c] = fmax(u, v);
-          } else {
-            blo[c] = fmin(blo[c], fmin(u, v)); bhi[c] = fmax(bhi[c], fmax(u, v));
-          }
-        }
-        hit = hit && alo[c] <= bhi[c] && blo[c] <= ahi[c];
-      }
+    for (int c = 0; c < 3; ++c) {
+      long long alo = SA->key[c][sl[0]], ahi = SA->key[3 + c][sl[0]];
+      if (na == 2) { alo = min(alo, SA->key[c][sl[1]]); ahi = max(ahi, SA->key[3 + c][sl[1]]); }
+      long long blo = SB->key[c][sl[na]], bhi = SB->key[3 + c][sl[na]];
+      for (int q = na + 1; q < 4; ++q) { blo = min(blo, SB->key[c][sl[q]]); bhi = max(bhi, SB->key[3 + c][sl[q]]); }
+      hit = hit && alo <= bhi && blo <= ahi;
     }
     if (hit) {
       ++nprim;
-      flops += 12;  // displacements D = X1 - X0
-      int st = ccd64(kind == 2 ? KIND_EE : KIND_VF, X0, D, tau, w1, w2, flops);
-      if (st == 1) {
-        type = kind;
-        if (kind == 0) { ga = SA.v_gid[x]; gb = SB.t_gid[y]; }
-        else if (kind == 1) { ga = SA.v_gid[x]; gb = SB.t_gid[y]; }
-        else { ga = SA.e_gid[x]; gb = SB.e_gid[y]; }
-      } else if (st == 2) {
-        ++ndeg;
+      keep = true;
+      if (!a.exact_only) {
+        f3 xq[4], dq[4];
+        load_f32(sl, kind, SA, SB, xq, dq);
+        cubic32 q = cubic_fp32(kind == 2 ? 1 : 0, xq, dq, ws.dx);
+        keep = !bernstein_reject(q);
       }
+      if (keep) desc = make_desc(r, kind, prim_gid(*SA, kind == 2 ? 2 : 0, x), prim_gid(*SB, kind == 2 ? 2 : 1, y));
     }
   }
-  unsigned m = __ballot_sync(0xffffffffu, type >= 0);
-  if (m) {
-    unsigned long long base = 0;
-    int leader = __ffs(m) - 1;
-    if (lane == leader) base = atomicAdd((unsigned long long*)&a.ctr[11], (unsigned long long)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (type >= 0) {
-      int64_t k = (int64_t)base + __popc(m & ((1u << lane) - 1u));
-      if (k < a.C) {
-        a.rc_pair[k] = r; a.rc_type[k] = type; a.rc_a[k] = ga; a.rc_b[k] = gb;
-        a.rc_tau[k] = tau; a.rc_w[2 * k] = w1; a.rc_w[2 * k + 1] = w2;
-      }
-      atomicAdd((unsigned long long*)&a.ctr[type == 2 ? STIV_C_EE : STIV_C_VF], 1ull);
-    }
-  }
+  if (a.exact_only) push_global(a.q2, a.Q2, &a.ctr[15], &a.ctr[STIV_C_STATUS], keep, desc, lane);
+  else push_global(a.q3, a.Q3, &a.ctr[14], &a.ctr[STIV_C_STATUS], keep, desc, lane);
 }
 
-// Push this lane's candidate (if any) into the warp queue; drain when >= 32.
 __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, int lane, int r, const narrow_args& a,
-                                        long long& nprim, long long& ndeg, long long& flops) {
+                                        long long& nprim) {
   unsigned m = __ballot_sync(0xffffffffu, hit);
-  int qn = ws.qn;
-  if (hit) ws.q[qn + __popc(m & ((1u << lane) - 1u))] = entry;
-  qn += __popc(m);
+  if (!m) return;
+  int n1 = ws.n1;
+  if (hit) ws.q1[n1 + __popc(m & ((1u << lane) - 1u))] = entry;
+  n1 += __popc(m);
   __syncwarp();
-  if (qn >= 32) {
-    process_queue(ws, 32, lane, r, a, nprim, ndeg, flops);
+  if (n1 >= 32) {
+    stage_filter(ws, 32, lane, r, a, nprim);
+    unsigned rest = (lane + 32 < n1) ? ws.q1[lane + 32] : 0;
     __syncwarp();
-    unsigned rest = (lane + 32 < qn) ? ws.q[lane + 32] : 0;
-    __syncwarp();
-    if (lane + 32 < qn) ws.q[lane] = rest;
-    qn -= 32;
+    if (lane + 32 < n1) ws.q1[lane] = rest;
+    n1 -= 32;
   }
-  if (lane == 0) ws.qn = qn;
+  if (lane == 0) ws.n1 = n1;
   __syncwarp();
 }
 
+// Stages 1-3a: one warp per patch pair.
 __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
   extern __shared__ unsigned char smraw[];
   WarpSm& ws = ((WarpSm*)smraw)[threadIdx.x >> 5];
   int lane = threadIdx.x & 31;
   int64_t nwork = a.ctr[STIV_C_PATCH];
   if (nwork > a.W) nwork = a.W;
-  long long nprim = 0, ndeg = 0, flops = 0;
+  long long nprim = 0;
   while (true) {
     long long item = 0;
     if (lane == 0) item = (long long)atomicAdd((unsigned long long*)&a.ctr[10], 1ull);
@@ -464,27 +709,31 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
     int vi = a.ci[r], vj = a.cj[r], code = a.cs[r];
     int s0[3] = {0, 0, 0};
     int s1[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
-    load_patch(ws.A, a, vi, pa, s0, lane);
-    load_patch(ws.B, a, vj, pb, s1, lane);
+    float offA[3] = {0.f, 0.f, 0.f}, offB[3];
+    float dx = pair_frame(a, r, offB);
+    if (lane == 0) ws.dx = dx;
+    load_patch(ws.A, a, vi, pa, s0, offA, dx, lane);
+    load_patch(ws.B, a, vj, pb, s1, offB, dx, lane);
     filter_patch(ws.A, ws.B.box, lane);
     filter_patch(ws.B, ws.A.box, lane);
-    if (lane == 0) ws.qn = 0;
+    if (lane == 0) ws.n1 = 0;
     __syncwarp();
-    // VF: vertices of A vs triangles of B (type 0) and vertices of B vs triangles of A (type 1)
+    // stage 1: FP32 boxes.  VF: vertices of A vs triangles of B (0), vertices of B vs triangles of A (1)
     for (int dir = 0; dir < 2; ++dir) {
-      PatchSm& V = dir == 0 ? ws.A : ws.B;
-      PatchSm& T = dir == 0 ? ws.B : ws.A;
+      const PatchSm& V = dir == 0 ? ws.A : ws.B;
+      const PatchSm& T = dir == 0 ? ws.B : ws.A;
       for (int y0 = 0; y0 < T.ntf; y0 += 32) {
         int yk = y0 + lane;
         bool valid = yk < T.ntf;
         int y = valid ? T.tf[yk] : 0;
         float tb[6];
-        for (int c = 0; c < 6; ++c) tb[c] = valid ? T.tb[c][y] : 0.f;
+        tri_box(T, y, tb);
         for (int xk = 0; xk < V.nvf; ++xk) {
-          int x = V.vf[xk], sl = V.v_slot[x];
-          float lo[3] = {V.flo[0][sl], V.flo[1][sl], V.flo[2][sl]}, hi[3] = {V.fhi[0][sl], V.fhi[1][sl], V.fhi[2][sl]};
-          bool hit = valid && fbox_hit(lo, hi, tb);
-          enqueue(ws, hit, ((unsigned)dir << 16) | ((unsigned)x << 8) | (unsigned)y, lane, r, a, nprim, ndeg, flops);
+          int x = V.vf[xk];
+          float vb[6];
+          slot_box(V, V.v_slot[x], vb);
+          bool hit = valid && fbox_hit(vb, tb);
+          enqueue(ws, hit, ((unsigned)dir << 16) | ((unsigned)x << 8) | (unsigned)y, lane, r, a, nprim);
         }
       }
     }
@@ -494,29 +743,206 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
         bool valid = yk < ws.B.nef;
         int y = valid ? ws.B.ef[yk] : 0;
         float eb[6];
-        for (int c = 0; c < 6; ++c) eb[c] = valid ? ws.B.eb[c][y] : 0.f;
+        edge_box(ws.B, y, eb);
         for (int xk = 0; xk < ws.A.nef; ++xk) {
           int x = ws.A.ef[xk];
-          float lo[3] = {ws.A.eb[0][x], ws.A.eb[1][x], ws.A.eb[2][x]}, hi[3] = {ws.A.eb[3][x], ws.A.eb[4][x], ws.A.eb[5][x]};
-          bool hit = valid && fbox_hit(lo, hi, eb);
-          enqueue(ws, hit, (2u << 16) | ((unsigned)x << 8) | (unsigned)y, lane, r, a, nprim, ndeg, flops);
+          float ab[6];
+          edge_box(ws.A, x, ab);
+          bool hit = valid && fbox_hit(ab, eb);
+          enqueue(ws, hit, (2u << 16) | ((unsigned)x << 8) | (unsigned)y, lane, r, a, nprim);
         }
       }
     }
-    int qn = ws.qn;
-    if (qn > 0) process_queue(ws, qn, lane, r, a, nprim, ndeg, flops);
+    int n1 = ws.n1;
+    if (n1 > 0) stage_filter(ws, n1, lane, r, a, nprim);
+  }
+  for (int off = 16; off > 0; off >>= 1) nprim += __shfl_down_sync(0xffffffffu, nprim, off);
+  if (lane == 0 && nprim) atomicAdd((unsigned long long*)&a.ctr[STIV_C_PRIM], (unsigned long long)nprim);
+}
+
+// ---------------------------------------------------------------------------
+// stage 3b: the pieces of [0,1] that may hold a root, certified non-contact.
+// A warp takes 32 descriptors; the pieces that need the inside test become
+// (descriptor, piece) tasks spread over the lanes, so that every lane runs the
+// same test; an undecided piece is split once.
+// ---------------------------------------------------------------------------
+constexpr int PW = 8;          // warps per CTA
+constexpr int NPIECE = 16;     // level-1 pieces of [0, 1]
+constexpr int MAXTASK = 512;
+
+struct PieceWarp {
+  float x[32][4][3], d[32][4][3];
+  float k[32][4], E[32], ep[32], ed[32];
+  int kind[32], fail[32];
+  unsigned short task[MAXTASK], task2[MAXTASK];
+  int ntask2;
+};
+
+__global__ void __launch_bounds__(PW * 32) pieces_kernel(narrow_args a) {
+  extern __shared__ unsigned char psraw[];
+  PieceWarp& W = ((PieceWarp*)psraw)[threadIdx.x >> 5];
+  int lane = threadIdx.x & 31;
+  int64_t n3 = a.ctr[14];
+  if (n3 > a.Q3) n3 = a.Q3;
+  int64_t nb = (n3 + 31) / 32;
+  int64_t gw = (int64_t)blockIdx.x * PW + (threadIdx.x >> 5), nw = (int64_t)gridDim.x * PW;
+  for (int64_t b = gw; b < nb; b += nw) {
+    int64_t idx = b * 32 + lane;
+    bool valid = idx < n3;
+    unsigned long long e = valid ? a.q3[idx] : 0ull;
+    unsigned mask = 0;
+    W.fail[lane] = 0;
+    if (valid) {
+      int kind;
+      f3 xq[4], dq[4];
+      float ep;
+      desc_points_f32(a, e, kind, xq, dq, ep);
+      cubic32 q = cubic_fp32(kind, xq, dq, ep);
+      for (int p = 0; p < 4; ++p) {
+        W.x[lane][p][0] = xq[p].x; W.x[lane][p][1] = xq[p].y; W.x[lane][p][2] = xq[p].z;
+        W.d[lane][p][0] = dq[p].x; W.d[lane][p][1] = dq[p].y; W.d[lane][p][2] = dq[p].z;
+      }
+      W.k[lane][0] = q.k0; W.k[lane][1] = q.k1; W.k[lane][2] = q.k2; W.k[lane][3] = q.k3;
+      W.E[lane] = q.E; W.ep[lane] = ep; W.ed[lane] = q.ed; W.kind[lane] = kind;
+      if (fabsf(q.k0) <= q.E && fabsf(q.k1) <= q.E && fabsf(q.k2) <= q.E && fabsf(q.k3) <= q.E) {
+        W.fail[lane] = 1;   // may vanish identically: FP64 decides (degenerate)
+      } else {
+        const float w = 1.0f / NPIECE;
+        for (int p = 0; p < NPIECE; ++p) {
+          float t0 = p * w;
+          float f0 = fmaf(fmaf(fmaf(q.k3, t0, q.k2), t0, q.k1), t0, q.k0);
+          float fp1 = fmaf(fmaf(3.f * q.k3, t0, 2.f * q.k2), t0, q.k1);
+          float g1 = w * fp1, g2 = w * w * fmaf(3.f * q.k3, t0, q.k2), g3 = w * w * w * q.k3;
+          if (!certain_sign4(f0, f0 + g1 * (1.f / 3.f), f0 + (2.f * g1 + g2) * (1.f / 3.f), f0 + g1 + g2 + g3, q.E))
+            mask |= 1u << p;
+        }
+      }
+    }
+    // task list of this batch
+    int cnt = __popc(mask), off = cnt;
+    for (int o = 1; o < 32; o <<= 1) { int v = __shfl_up_sync(0xffffffffu, off, o); if (lane >= o) off += v; }
+    int total = __shfl_sync(0xffffffffu, off, 31);
+    off -= cnt;
+    for (unsigned m = mask; m; m &= m - 1) {
+      int p = __ffs(m) - 1;
+      if (off < MAXTASK) W.task[off] = (unsigned short)((lane << 5) | p);
+      else W.fail[lane] = 1;
+      ++off;
+    }
+    if (lane == 0) W.ntask2 = 0;
+    __syncwarp();
+    if (total > MAXTASK) total = MAXTASK;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      int t = t0 + lane;
+      if (t < total) {
+        int owner = W.task[t] >> 5, p = W.task[t] & 31;
+        f3 xq[4], dq[4];
+        for (int q = 0; q < 4; ++q) {
+          xq[q] = {W.x[owner][q][0], W.x[owner][q][1], W.x[owner][q][2]};
+          dq[q] = {W.d[owner][q][0], W.d[owner][q][1], W.d[owner][q][2]};
+        }
+        int res = inside_cert(W.kind[owner], xq, dq, p * (1.0f / NPIECE), 1.0f / NPIECE, W.ep[owner], W.ed[owner]);
+        if (res == 2) W.fail[owner] = 1;
+        else if (res == 0) {
+          int k = atomicAdd(&W.ntask2, 2);
+          if (k + 1 < MAXTASK) { W.task2[k] = (unsigned short)((owner << 6) | (2 * p)); W.task2[k + 1] = (unsigned short)((owner << 6) | (2 * p + 1)); }
+          else W.fail[owner] = 1;
+        }
+      }
+    }
+    __syncwarp();
+    int total2 = min(W.ntask2, MAXTASK);
+    for (int t0 = 0; t0 < total2; t0 += 32) {
+      int t = t0 + lane;
+      if (t < total2) {
+        int owner = W.task2[t] >> 6, p = W.task2[t] & 63;
+        const float w = 0.5f / NPIECE;
+        float t0p = p * w;
+        float k0 = W.k[owner][0], k1 = W.k[owner][1], k2 = W.k[owner][2], k3 = W.k[owner][3], E = W.E[owner];
+        float f0 = fmaf(fmaf(fmaf(k3, t0p, k2), t0p, k1), t0p, k0);
+        float fp1 = fmaf(fmaf(3.f * k3, t0p, 2.f * k2), t0p, k1);
+        float g1 = w * fp1, g2 = w * w * fmaf(3.f * k3, t0p, k2), g3 = w * w * w * k3;
+        if (!certain_sign4(f0, f0 + g1 * (1.f / 3.f), f0 + (2.f * g1 + g2) * (1.f / 3.f), f0 + g1 + g2 + g3, E)) {
+          f3 xq[4], dq[4];
+          for (int q = 0; q < 4; ++q) {
+            xq[q] = {W.x[owner][q][0], W.x[owner][q][1], W.x[owner][q][2]};
+            dq[q] = {W.d[owner][q][0], W.d[owner][q][1], W.d[owner][q][2]};
+          }
+          if (inside_cert(W.kind[owner], xq, dq, t0p, w, W.ep[owner], W.ed[owner]) != 1) W.fail[owner] = 1;
+        }
+      }
+    }
+    __syncwarp();
+    push_global(a.q2, a.Q2, &a.ctr[15], &a.ctr[STIV_C_STATUS], valid && W.fail[lane], e, lane);
     __syncwarp();
   }
-  // totals
+}
+
+// ---------------------------------------------------------------------------
+// stage 4: the FP64 contact test, one descriptor per thread.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) fp64_kernel(narrow_args a) {
+  int lane = threadIdx.x & 31;
+  int64_t n2 = a.ctr[15];
+  if (n2 > a.Q2) n2 = a.Q2;
+  long long ndeg = 0, flops = 0, nexact = 0;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n2; base += stride) {
+    int64_t idx = base + threadIdx.x;
+    int type = -1, ga = 0, gb = 0, r = 0;
+    double tau = 0.0, w1 = 0.0, w2 = 0.0;
+    if (idx < n2) {
+      ++nexact;
+      int ves[4], vid[4];
+      bool onj[4];
+      int ty;
+      desc_points(a, a.q2[idx], r, ty, ga, gb, ves, vid, onj);
+      int code = a.cs[r];
+      int sB[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
+      d3 X0[4], D[4];
+      for (int q = 0; q < 4; ++q) {
+        int nv = stiv_nverts(2 * a.pv[ves[q]]);
+        size_t vb = a.voff[ves[q]] + vid[q];
+        double p0[3], p1[3];
+        for (int c = 0; c < 3; ++c) {
+          size_t i0 = vb + (size_t)c * nv, i1 = vb + (size_t)(3 + c) * nv;
+          p0[c] = a.mixed ? (double)((const float*)a.X)[i0] : ((const double*)a.X)[i0];
+          p1[c] = a.mixed ? (double)((const float*)a.X)[i1] : ((const double*)a.X)[i1];
+          if (onj[q] && sB[c] != 0) { double sh = sB[c] * a.L[c]; p0[c] = p0[c] + sh; p1[c] = p1[c] + sh; }
+        }
+        X0[q] = {p0[0], p0[1], p0[2]};
+        D[q] = {__dsub_rn(p1[0], p0[0]), __dsub_rn(p1[1], p0[1]), __dsub_rn(p1[2], p0[2])};
+      }
+      flops += 12;  // displacements
+      int st = ccd64(ty == 2 ? KIND_EE : KIND_VF, X0, D, tau, w1, w2, flops);
+      if (st == 1) type = ty;
+      else if (st == 2) ++ndeg;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, type >= 0);
+    if (m) {
+      unsigned long long cb = 0;
+      int leader = __ffs(m) - 1;
+      if (lane == leader) cb = atomicAdd((unsigned long long*)&a.ctr[11], (unsigned long long)__popc(m));
+      cb = __shfl_sync(0xffffffffu, cb, leader);
+      if (type >= 0) {
+        int64_t k = (int64_t)cb + __popc(m & ((1u << lane) - 1u));
+        if (k < a.C) {
+          a.rc_pair[k] = r; a.rc_type[k] = type; a.rc_a[k] = ga; a.rc_b[k] = gb;
+          a.rc_tau[k] = tau; a.rc_w[2 * k] = w1; a.rc_w[2 * k + 1] = w2;
+        }
+        atomicAdd((unsigned long long*)&a.ctr[type == 2 ? STIV_C_EE : STIV_C_VF], 1ull);
+      }
+    }
+  }
   for (int off = 16; off > 0; off >>= 1) {
-    nprim += __shfl_down_sync(0xffffffffu, nprim, off);
     ndeg += __shfl_down_sync(0xffffffffu, ndeg, off);
     flops += __shfl_down_sync(0xffffffffu, flops, off);
+    nexact += __shfl_down_sync(0xffffffffu, nexact, off);
   }
   if (lane == 0) {
-    if (nprim) atomicAdd((unsigned long long*)&a.ctr[STIV_C_PRIM], (unsigned long long)nprim);
     if (ndeg) atomicAdd((unsigned long long*)&a.ctr[STIV_C_DEGEN], (unsigned long long)ndeg);
     if (flops) atomicAdd((unsigned long long*)&a.ctr[12], (unsigned long long)flops);
+    if (nexact) atomicAdd((unsigned long long*)&a.ctr[13], (unsigned long long)nexact);
   }
 }
 
@@ -527,11 +953,10 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
                                                           const int32_t* cj, const int32_t* cs, int64_t cap,
                                                           int64_t W, uint64_t* work, int64_t* ctr, int mp) {
   extern __shared__ float psm[];
-  int wid0 = threadIdx.x >> 5;
-  float* sbw = psm + (size_t)wid0 * 2 * mp * 6;                       // [2][mp][6]
-  unsigned short* law = (unsigned short*)(psm + (size_t)4 * 2 * mp * 6) + (size_t)wid0 * 2 * mp;
-  unsigned short* lbw = law + mp;
   int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* sbw = psm + (size_t)wid * 2 * mp * 6;                       // [2][mp][6]
+  unsigned short* law = (unsigned short*)(psm + (size_t)4 * 2 * mp * 6) + (size_t)wid * 2 * mp;
+  unsigned short* lbw = law + mp;
   int64_t npairs = ctr[STIV_C_PAIRS];
   if (npairs > cap) npairs = cap;
   double L[3] = {Lx, Ly, Lz};
@@ -540,7 +965,6 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
     int s[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
     int Pi = 2 * pv[i], Pj = 2 * pv[j];
     int ni = stiv_npatches(Pi), nj = stiv_npatches(Pj);
-    // FP32 boxes: vesicle j shifted (outward), patches of j shifted (outward)
     float shlo[3], shhi[3];
     for (int c = 0; c < 3; ++c) {
       double sh = s[c] * L[c];
@@ -553,25 +977,24 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
       bj[3 + c] = __fadd_ru(__double2float_ru(vbox[6 * j + 3 + c]), shhi[c]);
     }
     for (int k = lane; k < ni; k += 32)
-      for (int c = 0; c < 6; ++c) sbw[(0 * mp + (k)) * 6 + (c)] = pbox[((size_t)i * STIV_MAX_PATCH + k) * 6 + c];
+      for (int c = 0; c < 6; ++c) sbw[(0 * mp + k) * 6 + c] = pbox[((size_t)i * mp + k) * 6 + c];
     for (int k = lane; k < nj; k += 32)
       for (int c = 0; c < 3; ++c) {
-        sbw[(1 * mp + (k)) * 6 + (c)] = __fadd_rd(pbox[((size_t)j * STIV_MAX_PATCH + k) * 6 + c], shlo[c]);
-        sbw[(1 * mp + (k)) * 6 + (3 + c)] = __fadd_ru(pbox[((size_t)j * STIV_MAX_PATCH + k) * 6 + 3 + c], shhi[c]);
+        sbw[(1 * mp + k) * 6 + c] = __fadd_rd(pbox[((size_t)j * mp + k) * 6 + c], shlo[c]);
+        sbw[(1 * mp + k) * 6 + 3 + c] = __fadd_ru(pbox[((size_t)j * mp + k) * 6 + 3 + c], shhi[c]);
       }
     __syncwarp();
-    // patches of i overlapping box j, patches of j overlapping box i
     int na = 0, nb = 0;
     for (int k0 = 0; k0 < ni; k0 += 32) {
       int k = k0 + lane;
-      bool hit = k < ni && fbox_hit(&sbw[(0 * mp + (k)) * 6], &sbw[(0 * mp + (k)) * 6 + 3], bj);
+      bool hit = k < ni && fbox_hit(&sbw[(0 * mp + k) * 6], bj);
       unsigned m = __ballot_sync(0xffffffffu, hit);
       if (hit) law[na + __popc(m & ((1u << lane) - 1u))] = (unsigned short)k;
       na += __popc(m);
     }
     for (int k0 = 0; k0 < nj; k0 += 32) {
       int k = k0 + lane;
-      bool hit = k < nj && fbox_hit(&sbw[(1 * mp + (k)) * 6], &sbw[(1 * mp + (k)) * 6 + 3], bi);
+      bool hit = k < nj && fbox_hit(&sbw[(1 * mp + k) * 6], bi);
       unsigned m = __ballot_sync(0xffffffffu, hit);
       if (hit) lbw[nb + __popc(m & ((1u << lane) - 1u))] = (unsigned short)k;
       nb += __popc(m);
@@ -583,7 +1006,7 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
       int pa = 0, pb = 0;
       if (e < na * nb) {
         pa = law[e / nb]; pb = lbw[e % nb];
-        hit = fbox_hit(&sbw[(0 * mp + (pa)) * 6], &sbw[(0 * mp + (pa)) * 6 + 3], &sbw[(1 * mp + (pb)) * 6]);
+        hit = fbox_hit(&sbw[(0 * mp + pa) * 6], &sbw[(1 * mp + pb) * 6]);
       }
       unsigned m = __ballot_sync(0xffffffffu, hit);
       if (m) {
@@ -615,16 +1038,18 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   size_t psmem = (size_t)4 * 2 * mp * 6 * sizeof(float) + (size_t)4 * 2 * mp * sizeof(unsigned short);
   STIV_CUDA(h, cudaFuncSetAttribute(patch_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
   {
-  STIV_PROF(h, st, "patch_pairs");
-  patch_pairs_kernel<<<blocks, 128, psmem, st>>>(p_dev, w.vbox, w.pbox, L[0], L[1], L[2], cand->i, cand->j,
-                                                 cand->shift, cand->capacity, w.W, w.work, w.ctr, mp);
+    STIV_PROF(h, st, "patch_pairs");
+    patch_pairs_kernel<<<blocks, 128, psmem, st>>>(p_dev, w.vbox, w.pbox, L[0], L[1], L[2], cand->i, cand->j,
+                                                   cand->shift, cand->capacity, w.W, w.work, w.ctr, mp);
   }
   STIV_LAUNCH(h);
   narrow_args a;
   a.pv = p_dev; a.voff = voff; a.X = X; a.mixed = h->prm.precision == STIV_MIXED;
   a.L[0] = L[0]; a.L[1] = L[1]; a.L[2] = L[2];
   a.ci = cand->i; a.cj = cand->j; a.cs = cand->shift;
-  a.work = w.work; a.W = w.W; a.include_ee = h->prm.include_ee;
+  a.work = w.work; a.W = w.W; a.include_ee = h->prm.include_ee; a.exact_only = w.exact_only;
+  a.vorg = w.vorg; a.fprep = w.fprep; a.fstride = w.fstride;
+  a.q3 = w.q3; a.q2 = w.q2; a.Q3 = w.Q3; a.Q2 = w.Q2;
   a.C = w.C;
   a.rc_pair = w.tmp_i32; a.rc_type = w.tmp_i32 + w.C; a.rc_a = w.tmp_i32 + 2 * w.C; a.rc_b = w.tmp_i32 + 3 * w.C;
   a.rc_tau = w.tmp_f64; a.rc_w = w.tmp_f64 + w.C;
@@ -634,8 +1059,25 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   int per_sm = 0;
   STIV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, narrow_kernel, NW * 32, smem));
   if (per_sm < 1) per_sm = 1;
-  STIV_PROF(h, st, "narrow");
-  narrow_kernel<<<per_sm * num_sms, NW * 32, smem, st>>>(a);
+  {
+    STIV_PROF(h, st, "narrow");
+    narrow_kernel<<<per_sm * num_sms, NW * 32, smem, st>>>(a);
+  }
+  STIV_LAUNCH(h);
+  if (!w.exact_only) {
+    size_t psm2 = sizeof(PieceWarp) * PW;
+    STIV_CUDA(h, cudaFuncSetAttribute(pieces_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm2));
+    int per_sm2 = 0;
+    STIV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, pieces_kernel, PW * 32, psm2));
+    if (per_sm2 < 1) per_sm2 = 1;
+    STIV_PROF(h, st, "pieces");
+    pieces_kernel<<<per_sm2 * num_sms, PW * 32, psm2, st>>>(a);
+  }
+  STIV_LAUNCH(h);
+  {
+    STIV_PROF(h, st, "fp64");
+    fp64_kernel<<<num_sms * 16, 128, 0, st>>>(a);
+  }
   STIV_LAUNCH(h);
   return STIV_OK;
 }

@@ -14,9 +14,8 @@
 
 #define STIV_MAX_P 32          // largest SH order accepted (mesh order 64)
 #define STIV_MAX_PP 64         // largest mesh order P
-#define STIV_BR 4              // patch height in grid bands
-#define STIV_BC 8              // patch width in grid columns
-#define STIV_MAX_PATCH ((STIV_MAX_PP / STIV_BR) * (2 * STIV_MAX_PP / STIV_BC))
+#define STIV_BR 2              // patch height in grid bands
+#define STIV_BC 4              // patch width in grid columns
 
 // ---------------------------------------------------------------------------
 // handle and scratch
@@ -65,7 +64,11 @@ inline int stiv_sort_kernels(int key_bits) { return 3 * ((key_bits + 7) / 8); }
 // Scratch layout used by stiv_detect (byte offsets into handle->ws).
 struct detect_ws {
   double* vbox;          // [N][6]
-  float* pbox;           // [N][STIV_MAX_PATCH][6]
+  float* pbox;           // [N][pstride][6]
+  int pstride;           // patches per vesicle at the largest order
+  float* vorg;           // [N][4]  FP32 frame origin of each vesicle, and R = max |X - origin|
+  float* fprep;          // [N][fstride]  per vertex: X0 - origin (xyz), X1 - X0 (xyz), as float
+  int64_t fstride;
   double* grid;          // [16]  h, origin xyz, cell sizes, G
   int32_t* cell_count;   // [N+1]
   int32_t* cell_off;     // [N+1]
@@ -80,6 +83,9 @@ struct detect_ws {
   uint64_t* pkey2;       // [Q]
   int32_t* pval2;        // [Q]
   uint64_t* work;        // [W]  patch-pair work items
+  unsigned long long* q3;  // [Q3] primitive pairs left for the FP32 piece tests
+  unsigned long long* q2;  // [Q2] primitive pairs left for the FP64 contact test
+  int64_t Q3, Q2;
   uint64_t* ckey;        // [C]  contact sort keys
   int32_t* cval;         // [C]
   uint64_t* ckey2;       // [C]
@@ -90,6 +96,7 @@ struct detect_ws {
   void* sort_scratch;
   size_t sort_scratch_bytes;
   int64_t R, Q, W, C;
+  int exact_only;
 };
 
 // ---------------------------------------------------------------------------

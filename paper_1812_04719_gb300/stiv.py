@@ -26,8 +26,8 @@ LIB_PATH = os.path.join(HERE, "libstiv.so")
 
 STIV_OK, STIV_ERR_ARG, STIV_ERR_CAPACITY, STIV_ERR_TIMEOUT, STIV_ERR_CUDA, STIV_ERR_INPUT = range(6)
 STIV_FP64, STIV_MIXED = 0, 1
-C_PAIRS, C_PRIM, C_VF, C_EE, C_CPAIRS, C_DEGEN, C_STATUS, C_PATCH, C_FLOPS = range(9)
-NCOUNTS = 9
+C_PAIRS, C_PRIM, C_VF, C_EE, C_CPAIRS, C_DEGEN, C_STATUS, C_PATCH, C_FLOPS, C_EXACT = range(10)
+NCOUNTS = 10
 F_PAIRS_OVERFLOW, F_CONTACTS_OVERFLOW, F_BOX_TOO_SMALL, F_NONFINITE, F_WORK_OVERFLOW = 1, 2, 4, 8, 16
 
 EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_error", "stiv_mesh_topology",
@@ -44,7 +44,8 @@ class StivError(RuntimeError):
 
 class StivParams(ctypes.Structure):
     _fields_ = [("d_m", ctypes.c_double), ("eps", ctypes.c_double), ("dt", ctypes.c_double),
-                ("box_L", ctypes.c_double * 3), ("precision", ctypes.c_int32), ("include_ee", ctypes.c_int32)]
+                ("box_L", ctypes.c_double * 3), ("precision", ctypes.c_int32), ("include_ee", ctypes.c_int32),
+                ("exact_only", ctypes.c_int32)]
 
 
 class StivPairs(ctypes.Structure):
@@ -121,9 +122,10 @@ def _stream(stream=None) -> int:
 # low-level: same names as the C entry points, raw pointers
 # ---------------------------------------------------------------------------
 
-def stiv_create(d_m=0.0, eps=1.0, dt=0.1, box_L=(0.0, 0.0, 0.0), precision=STIV_FP64, include_ee=True) -> int:
+def stiv_create(d_m=0.0, eps=1.0, dt=0.1, box_L=(0.0, 0.0, 0.0), precision=STIV_FP64, include_ee=True,
+                exact_only=False) -> int:
     prm = StivParams(float(d_m), float(eps), float(dt), (ctypes.c_double * 3)(*[float(x) for x in box_L]),
-                     int(precision), int(bool(include_ee)))
+                     int(precision), int(bool(include_ee)), int(bool(exact_only)))
     h = ctypes.c_void_p()
     _check(lib().stiv_create(ctypes.byref(h), ctypes.byref(prm)), "stiv_create")
     return h.value
@@ -286,10 +288,11 @@ class Stiv:
     """One library handle plus the buffers of the per-step path."""
 
     def __init__(self, box_L=(0.0, 0.0, 0.0), eps=1.0, dt=0.1, d_m=0.0, precision=STIV_FP64, include_ee=True,
-                 pair_cap=1024, contact_cap=1 << 16, device="cuda"):
+                 pair_cap=1024, contact_cap=1 << 16, device="cuda", exact_only=False):
         self.precision = precision
         self.device = torch.device(device)
-        self.h = stiv_create(d_m=d_m, eps=eps, dt=dt, box_L=box_L, precision=precision, include_ee=include_ee)
+        self.h = stiv_create(d_m=d_m, eps=eps, dt=dt, box_L=box_L, precision=precision, include_ee=include_ee,
+                             exact_only=exact_only)
         self.pair_cap, self.contact_cap = pair_cap, contact_cap
         self.buf = None
 
@@ -344,7 +347,7 @@ class Stiv:
                 f = int(counts[C_STATUS])
                 if f & F_PAIRS_OVERFLOW or f & F_WORK_OVERFLOW:
                     self.pair_cap = max(2 * self.pair_cap, int(counts[C_PAIRS]) + 16)
-                if f & F_CONTACTS_OVERFLOW:
+                if f & F_CONTACTS_OVERFLOW or f & F_WORK_OVERFLOW:
                     self.contact_cap = max(2 * self.contact_cap, int(counts[C_VF] + counts[C_EE]) + 16)
                 continue
             _check(rc, "step")
