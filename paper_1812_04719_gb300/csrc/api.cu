@@ -243,10 +243,11 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   size_t o_wk = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.W);
   size_t o_q3 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q3);
   size_t o_q2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q2);
-  size_t o_ck = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.C);
-  size_t o_cv = off; off = align_up(off + sizeof(int32_t) * (size_t)w.C);
-  size_t o_ck2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.C);
-  size_t o_cv2 = off; off = align_up(off + sizeof(int32_t) * (size_t)w.C);
+  size_t o_pc = off; off = align_up(off + sizeof(int32_t) * (size_t)cand->capacity);
+  size_t o_pf = off; off = align_up(off + sizeof(int32_t) * (size_t)cand->capacity);
+  size_t o_po = off; off = align_up(off + sizeof(int32_t) * (size_t)(cand->capacity + 1));
+  size_t o_sg = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.C);
+  size_t o_sg2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.C);
   size_t o_ti = off; off = align_up(off + sizeof(int32_t) * 4 * (size_t)w.C);
   size_t o_tf = off; off = align_up(off + sizeof(double) * 3 * (size_t)w.C);
   size_t o_ctr = off; off = align_up(off + sizeof(int64_t) * 16);
@@ -264,8 +265,8 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   w.pkey2 = (uint64_t*)(b + o_pk2); w.pval2 = (int32_t*)(b + o_pv2);
   w.work = (uint64_t*)(b + o_wk);
   w.q3 = (unsigned long long*)(b + o_q3); w.q2 = (unsigned long long*)(b + o_q2);
-  w.ckey = (uint64_t*)(b + o_ck); w.cval = (int32_t*)(b + o_cv);
-  w.ckey2 = (uint64_t*)(b + o_ck2); w.cval2 = (int32_t*)(b + o_cv2);
+  w.pair_cnt = (int32_t*)(b + o_pc); w.pair_fill = (int32_t*)(b + o_pf); w.pair_off = (int32_t*)(b + o_po);
+  w.seg = (unsigned long long*)(b + o_sg); w.seg2 = (unsigned long long*)(b + o_sg2);
   w.tmp_i32 = (int32_t*)(b + o_ti); w.tmp_f64 = (double*)(b + o_tf);
   w.ctr = (int64_t*)(b + o_ctr);
   w.sort_scratch = b + o_ss;
@@ -292,6 +293,8 @@ extern "C" int stiv_detect(stiv_handle* h, void* stream, int32_t n_ves, int32_t 
   if (rc) return rc;
   detect_layout(h, n_ves, p_max, cand, out, w, true);
   STIV_CUDA(h, cudaMemsetAsync(w.ctr, 0, sizeof(int64_t) * 16, st));
+  STIV_CUDA(h, cudaMemsetAsync(w.pair_cnt, 0, sizeof(int32_t) * (size_t)cand->capacity, st));
+  STIV_CUDA(h, cudaMemsetAsync(w.pair_fill, 0, sizeof(int32_t) * (size_t)cand->capacity, st));
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   rc = stiv_broad_phase(h, st, n_ves, p_dev, vert_off_dev, verts_dev, cand, w, w.ctr);

@@ -186,39 +186,143 @@ __global__ void __launch_bounds__(128) stiv_kernel(stiv_args A) {
   }
 }
 
-// Per candidate pair: sum of its contacts' V (contacts sorted by pair).
+// Per candidate pair: sum of its contacts' V (contacts sorted by pair); one
+// warp per pair, fixed summation order.
 __global__ void vpair_kernel(const int32_t* pair, const int64_t* counts, int64_t ccap, const double* Vc,
                              int64_t pcap, double* Vp) {
+  int lane = threadIdx.x & 31;
   int64_t np = counts[STIV_C_PAIRS]; if (np > pcap) np = pcap;
   int64_t n = n_contacts(counts, ccap);
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < np; r += (int64_t)gridDim.x * blockDim.x) {
+  int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w0; r < np; r += nw) {
     int64_t lo = 0, hi = n;
     while (lo < hi) { int64_t mid = (lo + hi) >> 1; if (pair[mid] < r) lo = mid + 1; else hi = mid; }
     double s = 0.0;
-    for (int64_t k = lo; k < n && pair[k] == r; ++k) s += Vc[k];
-    Vp[r] = s;
+    for (int64_t k = lo + lane; k < n && pair[k] == r; k += 32) s += Vc[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) Vp[r] = s;
   }
 }
 
-// Contact ordering: key (pair, type, a, b), then gather.
-__global__ void contact_keys_kernel(const int64_t* ctr, int64_t C, const int32_t* rp, const int32_t* rt,
-                                    const int32_t* ra, const int32_t* rb, uint64_t* key, int32_t* val) {
+// Contact ordering by (pair, type, a, b): counting sort by pair, then each
+// pair's segment sorted by its (type, a, b) key.
+__global__ void pair_count_kernel(const int64_t* ctr, int64_t C, const int32_t* rp, int32_t* cnt) {
+  int64_t n = ctr[11]; if (n > C) n = C;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[rp[k]], 1);
+}
+
+// Exclusive scan of the per-pair counts (one CTA); counts pairs with contacts.
+__global__ void __launch_bounds__(1024) pair_scan_kernel(const int64_t* ctr_r, int64_t pcap, const int32_t* cnt,
+                                                         int32_t* off, int64_t* ctr_w) {
+  __shared__ int32_t part[1024];
+  __shared__ int32_t nz[1024];
+  int64_t np = ctr_r[STIV_C_PAIRS]; if (np > pcap) np = pcap;
+  int64_t per = (np + 1023) / 1024;
+  int64_t lo = threadIdx.x * per, hi = lo + per < np ? lo + per : np;
+  int32_t s = 0, z = 0;
+  for (int64_t i = lo; i < hi; ++i) { s += cnt[i]; z += cnt[i] > 0; }
+  part[threadIdx.x] = s; nz[threadIdx.x] = z;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int64_t i = lo; i < hi; ++i) { off[i] = run; run += cnt[i]; }
+  if (threadIdx.x == 1023) off[np] = part[1023];
+  for (int o = 512; o > 0; o >>= 1) {
+    if (threadIdx.x < o) nz[threadIdx.x] += nz[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ctr_w[STIV_C_CPAIRS] = nz[0];
+}
+
+__global__ void pair_scatter_kernel(const int64_t* ctr, int64_t C, const int32_t* rp, const int32_t* rt,
+                                    const int32_t* ra, const int32_t* rb, const int32_t* off, int32_t* fill,
+                                    unsigned long long* seg) {
   int64_t n = ctr[11]; if (n > C) n = C;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    key[k] = ((uint64_t)(uint32_t)rp[k] << 32) | ((uint64_t)rt[k] << 30) | ((uint64_t)ra[k] << 15) | (uint64_t)rb[k];
-    val[k] = (int32_t)k;
+    int r = rp[k];
+    int slot = off[r] + atomicAdd(&fill[r], 1);
+    unsigned key = ((unsigned)rt[k] << 30) | ((unsigned)ra[k] << 15) | (unsigned)rb[k];
+    seg[slot] = ((unsigned long long)key << 32) | (unsigned long long)(unsigned)k;
   }
 }
 
-__global__ void contact_gather_kernel(const int64_t* ctr, int64_t C, const int32_t* perm, const int32_t* rp,
+constexpr int SEG_SMEM = 4096;   // entries sorted in shared memory per pass (32 KB)
+
+__device__ void bitonic_smem(unsigned long long* x, int n2) {
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        int l = i ^ j;
+        if (l > i) {
+          unsigned long long a = x[i], b = x[l];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) { x[i] = b; x[l] = a; }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// One CTA per pair: sort its segment; long segments are sorted in chunks and
+// merged (each element placed by binary search in the other run).
+__global__ void __launch_bounds__(1024) pair_sort_kernel(const int64_t* ctr, int64_t pcap, const int32_t* off,
+                                                         unsigned long long* seg, unsigned long long* tmp) {
+  __shared__ unsigned long long x[SEG_SMEM];
+  int64_t np = ctr[STIV_C_PAIRS]; if (np > pcap) np = pcap;
+  for (int64_t r = blockIdx.x; r < np; r += gridDim.x) {
+    int o = off[r], len = off[r + 1] - o;
+    if (len <= 1) continue;
+    for (int c0 = 0; c0 < len; c0 += SEG_SMEM) {
+      int cl = min(SEG_SMEM, len - c0);
+      int n2 = 1;
+      while (n2 < cl) n2 <<= 1;
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) x[i] = i < cl ? seg[o + c0 + i] : ~0ull;
+      __syncthreads();
+      bitonic_smem(x, n2);
+      for (int i = threadIdx.x; i < cl; i += blockDim.x) seg[o + c0 + i] = x[i];
+      __syncthreads();
+    }
+    unsigned long long* src = seg + o;
+    unsigned long long* dst = tmp + o;
+    for (int wdt = SEG_SMEM; wdt < len; wdt <<= 1) {
+      for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        int run = i / (2 * wdt), a0 = run * 2 * wdt, a1 = min(a0 + wdt, len), b1 = min(a0 + 2 * wdt, len);
+        unsigned long long v = src[i];
+        int pos;
+        if (i < a1) {  // element of run A: rank among B elements smaller than v
+          int lo = a1, hi = b1;
+          while (lo < hi) { int mid = (lo + hi) >> 1; if (src[mid] < v) lo = mid + 1; else hi = mid; }
+          pos = a0 + (i - a0) + (lo - a1);
+        } else {       // element of run B: rank among A elements smaller than v
+          int lo = a0, hi = a1;
+          while (lo < hi) { int mid = (lo + hi) >> 1; if (src[mid] < v) lo = mid + 1; else hi = mid; }
+          pos = a0 + (i - a1) + (lo - a0);
+        }
+        dst[pos] = v;
+      }
+      __syncthreads();
+      unsigned long long* t = src; src = dst; dst = t;
+    }
+    if (src != seg + o)
+      for (int i = threadIdx.x; i < len; i += blockDim.x) seg[o + i] = src[i];
+    __syncthreads();
+  }
+}
+
+__global__ void contact_gather_kernel(const int64_t* ctr, int64_t C, const unsigned long long* seg, const int32_t* rp,
                                       const int32_t* rt, const int32_t* ra, const int32_t* rb, const double* rtau,
-                                      const double* rw, stiv_contacts out, int64_t* ctr_w) {
+                                      const double* rw, stiv_contacts out) {
   int64_t n = ctr[11]; if (n > C) n = C;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    int src = perm[k];
+    int src = (int)(seg[k] & 0xFFFFFFFFull);
     out.pair[k] = rp[src]; out.type[k] = rt[src]; out.a[k] = ra[src]; out.b[k] = rb[src];
     out.tau[k] = rtau[src]; out.w[2 * k] = rw[2 * src]; out.w[2 * k + 1] = rw[2 * src + 1];
-    if (k == 0 || rp[perm[k - 1]] != rp[src]) atomicAdd((unsigned long long*)&ctr_w[STIV_C_CPAIRS], 1ull);
   }
 }
 
@@ -254,75 +358,84 @@ __global__ void __launch_bounds__(256) adjoint_kernel(adj_args a) {
   int v = blockIdx.x;
   int p = a.p[v], P = 2 * p, nc = (p + 1) * (p + 1), nl = (p + 1) * (p + 2) / 2, ns = 2 * p + 1, W = 2 * P;
   int nv = stiv_nverts(P);
-  double* H = sm;  // [3][P+1][ns]: per ring, sum_j g(i,j) {1, cos m phi_j, sin m phi_j}
+  double* G = sm;                    // [n_v]       one field of gX (X1 block), staged coalesced
+  double* H = sm + nv;               // [P+1][ns]   Fourier-analysed rings of that field
+  double* Q = H + (P + 1) * ns;      // [P+1][4][P/2+1] parity combinations of the four symmetric longitudes
   const double* g = a.gX + a.vert_off[v] + (size_t)3 * nv;
   const double* T = a.trig[p];
   const double* L = a.leg[p];
-  // adjoint of the Fourier step: the forward writes four longitudes j, P-j,
-  // P+j, 2P-j (j <= P/2, duplicates skipped) from the parity sums Ce, Co, Se, So
-  for (int task = threadIdx.x; task < 3 * (P + 1) * ns; task += blockDim.x) {
-    int f = task / ((P + 1) * ns), rem = task % ((P + 1) * ns), i = rem / ns, s = rem % ns;
-    int m = (s + 1) >> 1;
-    bool is_sin = s > 0 && (s & 1) == 0;
-    const double* gr = g + (size_t)f * nv + (size_t)i * W;
-    double acc = 0.0;
-    for (int j = 0; j <= P / 2; ++j) {
+  double* out = a.gcoef + a.coef_off[v];
+  int nq = P / 2 + 1;
+  for (int k = threadIdx.x; k < 3 * nc; k += blockDim.x) out[k] = 0.0;  // X0 block
+  for (int f = 0; f < 3; ++f) {
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) G[k] = g[(size_t)f * nv + k];
+    __syncthreads();
+    // adjoint of the Fourier step.  The forward writes longitudes j, P-j, P+j,
+    // 2P-j (j <= P/2, duplicates skipped) from the parity sums Ce, Co, Se, So;
+    // their adjoints are the four combinations below.
+    for (int task = threadIdx.x; task < (P + 1) * nq; task += blockDim.x) {
+      int i = task / nq, j = task % nq;
+      const double* gr = G + (size_t)i * W;
       int j1 = P - j, j2 = P + j, j3 = (W - j) % W;
       double g0 = gr[j];
       double g1 = (j1 != j) ? gr[j1] : 0.0;
       double g2 = (j2 != j1) ? gr[j2] : 0.0;
       double g3 = (j3 != j && j3 != j2) ? gr[j3] : 0.0;
-      double w;
-      if (!is_sin) w = (m & 1) ? (g0 - g1 - g2 + g3) : (g0 + g1 + g2 + g3);
-      else w = (m & 1) ? (g0 + g1 - g2 - g3) : (g0 - g1 + g2 - g3);
-      const double* cs = T + (size_t)j * 2 * (p + 1);
-      double basis = s == 0 ? 1.0 : (is_sin ? cs[(p + 1) + m] : cs[m]);
-      acc += w * basis;
+      double* q = Q + (size_t)i * 4 * nq;
+      q[0 * nq + j] = (g0 + g1) + (g2 + g3);   // cos, even m
+      q[1 * nq + j] = (g0 - g1) - (g2 - g3);   // cos, odd m
+      q[2 * nq + j] = (g0 - g1) + (g2 - g3);   // sin, even m
+      q[3 * nq + j] = (g0 + g1) - (g2 + g3);   // sin, odd m
     }
-    H[(f * (P + 1) + i) * ns + s] = acc;
-  }
-  __syncthreads();
-  double* out = a.gcoef + a.coef_off[v];
-  for (int k = threadIdx.x; k < 3 * nc; k += blockDim.x) out[k] = 0.0;  // X0 block
-  for (int task = threadIdx.x; task < 3 * nc; task += blockDim.x) {
-    int f = task / nc, q = task % nc;
-    int n = (int)sqrt((double)q); while (n * n > q) --n; while ((n + 1) * (n + 1) <= q) ++n;
-    int m = q - n * n - n, am = m < 0 ? -m : m;
-    int s = m == 0 ? 0 : (m > 0 ? 2 * m - 1 : 2 * am);
-    double acc = 0.0;
-    for (int i = 0; i <= P; ++i) acc += L[(size_t)i * nl + n * (n + 1) / 2 + am] * H[(f * (P + 1) + i) * ns + s];
-    if (m == 0) {
-      const double* gp = g + (size_t)f * nv + (size_t)W * (P + 1);
-      acc += L[(size_t)(P + 1) * nl + n * (n + 1) / 2] * gp[0] + L[(size_t)(P + 2) * nl + n * (n + 1) / 2] * gp[1];
+    __syncthreads();
+    for (int task = threadIdx.x; task < (P + 1) * ns; task += blockDim.x) {
+      int i = task / ns, s = task % ns;
+      int m = (s + 1) >> 1;
+      bool is_sin = s > 0 && (s & 1) == 0;
+      const double* q = Q + (size_t)i * 4 * nq + (size_t)((is_sin ? 2 : 0) + (m & 1)) * nq;
+      double acc = 0.0;
+      if (s == 0) {
+        for (int j = 0; j < nq; ++j) acc += q[j];
+      } else {
+        int off = is_sin ? (p + 1) + m : m;
+        for (int j = 0; j < nq; ++j) acc = fma(q[j], T[(size_t)j * 2 * (p + 1) + off], acc);
+      }
+      H[i * ns + s] = acc;
     }
-    out[3 * nc + task] = acc;
+    __syncthreads();
+    // adjoint of the Legendre step (all rings, and the poles for m = 0)
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      int n = (int)sqrt((double)q); while (n * n > q) --n; while ((n + 1) * (n + 1) <= q) ++n;
+      int m = q - n * n - n, am = m < 0 ? -m : m;
+      int s = m == 0 ? 0 : (m > 0 ? 2 * m - 1 : 2 * am);
+      double acc = 0.0;
+      for (int i = 0; i <= P; ++i) acc = fma(L[(size_t)i * nl + n * (n + 1) / 2 + am], H[i * ns + s], acc);
+      if (m == 0) {
+        acc = fma(L[(size_t)(P + 1) * nl + n * (n + 1) / 2], G[(size_t)W * (P + 1)], acc);
+        acc = fma(L[(size_t)(P + 2) * nl + n * (n + 1) / 2], G[(size_t)W * (P + 1) + 1], acc);
+      }
+      out[3 * nc + f * nc + q] = acc;
+    }
+    __syncthreads();
   }
 }
 
 }  // namespace
-
-static int cand_bits(int64_t cap) {
-  int pbits = 1;
-  while (pbits < 32 && ((int64_t)1 << pbits) <= cap) ++pbits;
-  return pbits;
-}
 
 int stiv_contact_order(stiv_handle* h, cudaStream_t st, const stiv_pairs* cand, const stiv_contacts* out,
                        detect_ws& w) {
   int64_t C = w.C;
   int32_t* rp = w.tmp_i32; int32_t* rt = rp + C; int32_t* ra = rp + 2 * C; int32_t* rb = rp + 3 * C;
   double* rtau = w.tmp_f64; double* rw = w.tmp_f64 + C;
+  int64_t pcap = cand->capacity;
   int blocks = (int)((C + 255) / 256); if (blocks > 4096) blocks = 4096; if (blocks < 1) blocks = 1;
-  {
-  STIV_PROF_N(h, st, "contact_order", 2 + stiv_sort_kernels(32 + cand_bits(cand->capacity)));
-  contact_keys_kernel<<<blocks, 256, 0, st>>>(w.ctr, C, rp, rt, ra, rb, w.ckey, w.cval);
-  STIV_LAUNCH(h);
-  int pbits = cand_bits(cand->capacity);
-  int rc = stiv_sort_pairs_impl(st, C, 32 + pbits, w.ckey, w.cval, w.ckey2, w.cval2, w.sort_scratch,
-                                w.sort_scratch_bytes, &w.ctr[11]);
-  if (rc) return rc;
-  contact_gather_kernel<<<blocks, 256, 0, st>>>(w.ctr, C, w.cval2, rp, rt, ra, rb, rtau, rw, *out, w.ctr);
-  }
+  STIV_PROF_N(h, st, "contact_order", 5);
+  pair_count_kernel<<<blocks, 256, 0, st>>>(w.ctr, C, rp, w.pair_cnt);
+  pair_scan_kernel<<<1, 1024, 0, st>>>(w.ctr, pcap, w.pair_cnt, w.pair_off, w.ctr);
+  pair_scatter_kernel<<<blocks, 256, 0, st>>>(w.ctr, C, rp, rt, ra, rb, w.pair_off, w.pair_fill, w.seg);
+  int sblocks = (int)(pcap < 65535 ? pcap : 65535);
+  pair_sort_kernel<<<sblocks, 1024, 0, st>>>(w.ctr, pcap, w.pair_off, w.seg, w.seg2);
+  contact_gather_kernel<<<blocks, 256, 0, st>>>(w.ctr, C, w.seg, rp, rt, ra, rb, rtau, rw, *out);
   STIV_LAUNCH(h);
   return STIV_OK;
 }
@@ -357,7 +470,7 @@ static int run_stiv(stiv_handle* h, void* stream, const int32_t* p_dev, const in
   }
   if (Vp) {
     STIV_PROF(h, st, "vpair");
-    vpair_kernel<<<dev_sms * 4, 128, 0, st>>>(ct->pair, counts_dev, ct->capacity, Vtmp, cand->capacity, Vp);
+    vpair_kernel<<<dev_sms * 8, 256, 0, st>>>(ct->pair, counts_dev, ct->capacity, Vtmp, cand->capacity, Vp);
     STIV_LAUNCH(h);
   }
   return STIV_OK;
@@ -413,7 +526,9 @@ extern "C" int stiv_grad_to_coef(stiv_handle* h, void* stream, int32_t n_ves, in
     if (rc) return rc;
     a.leg[p] = h->tab[p].leg; a.trig[p] = h->tab[p].trig;
   }
-  size_t smem = sizeof(double) * (size_t)3 * (2 * p_max + 1) * (2 * p_max + 1);
+  int Pm = 2 * p_max;
+  size_t smem = sizeof(double) * ((size_t)stiv_nverts(Pm) + (size_t)(Pm + 1) * (2 * p_max + 1) +
+                                  (size_t)(Pm + 1) * 4 * (Pm / 2 + 1));
   STIV_CUDA(h, cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   STIV_PROF(h, st, "grad_to_coef");
   adjoint_kernel<<<n_ves, 256, smem, st>>>(a);

@@ -86,10 +86,11 @@ struct detect_ws {
   unsigned long long* q3;  // [Q3] primitive pairs left for the FP32 piece tests
   unsigned long long* q2;  // [Q2] primitive pairs left for the FP64 contact test
   int64_t Q3, Q2;
-  uint64_t* ckey;        // [C]  contact sort keys
-  int32_t* cval;         // [C]
-  uint64_t* ckey2;       // [C]
-  int32_t* cval2;        // [C]
+  int32_t* pair_cnt;     // [pair capacity]   contacts per candidate pair
+  int32_t* pair_fill;    // [pair capacity]
+  int32_t* pair_off;     // [pair capacity + 1]
+  unsigned long long* seg;   // [C]  (type, a, b) key << 32 | raw contact index, grouped by pair
+  unsigned long long* seg2;  // [C]
   int32_t* tmp_i32;      // [C] temporaries for the contact permutation
   double* tmp_f64;       // [3C]
   int64_t* ctr;          // [16] device counters

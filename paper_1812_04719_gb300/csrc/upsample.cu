@@ -8,8 +8,8 @@
 // Both steps use exact symmetries of the grid: Pbar_n^m(-x) = (-1)^(n+m)
 // Pbar_n^m(x) pairs ring i with ring P-i, and phi_{P-j} = pi - phi_j,
 // phi_{P+j} = pi + phi_j, phi_{2P-j} = 2 pi - phi_j give four outputs from one
-// set of parity-split partial sums.  FP64 throughout; STIV_MIXED stores the
-// result as float.
+// set of parity-split partial sums.  FP64 throughout (fused multiply-adds);
+// STIV_MIXED stores the result as float.
 #include "stiv_internal.cuh"
 
 #include <math.h>
@@ -111,10 +111,8 @@ __global__ void __launch_bounds__(256) synth_kernel(synth_args a) {
     const double* Lr = L + (size_t)i * nl;
     const double* Cf = C + f * nc;
     double E = 0.0, O = 0.0;
-    for (int n = m; n <= p; ++n) {
-      double term = Cf[n * n + n + sgn * m] * Lr[n * (n + 1) / 2 + m];
-      if (((n + m) & 1) == 0) E += term; else O += term;
-    }
+    for (int n = m; n <= p; n += 2) E = fma(Cf[n * n + n + sgn * m], Lr[n * (n + 1) / 2 + m], E);
+    for (int n = m + 1; n <= p; n += 2) O = fma(Cf[n * n + n + sgn * m], Lr[n * (n + 1) / 2 + m], O);
     G[(f * (P + 1) + i) * ns + s] = E + O;
     if (i != P - i) G[(f * (P + 1) + (P - i)) * ns + s] = E - O;
   }
@@ -128,10 +126,8 @@ __global__ void __launch_bounds__(256) synth_kernel(synth_args a) {
     const double* cs = T + (size_t)j * 2 * (p + 1);
     const double* sn = cs + (p + 1);
     double Ce = g[0], Co = 0.0, Se = 0.0, So = 0.0;
-    for (int m = 1; m <= p; ++m) {
-      double c = g[2 * m - 1] * cs[m], s = g[2 * m] * sn[m];
-      if (m & 1) { Co += c; So += s; } else { Ce += c; Se += s; }
-    }
+    for (int m = 1; m <= p; m += 2) { Co = fma(g[2 * m - 1], cs[m], Co); So = fma(g[2 * m], sn[m], So); }
+    for (int m = 2; m <= p; m += 2) { Ce = fma(g[2 * m - 1], cs[m], Ce); Se = fma(g[2 * m], sn[m], Se); }
     int W = 2 * P;
     double v0 = (Ce + Co) + (Se + So);            // phi_j
     double v1 = (Ce - Co) + (So - Se);            // pi - phi_j
@@ -158,7 +154,7 @@ __global__ void __launch_bounds__(256) synth_kernel(synth_args a) {
     int f = threadIdx.x >> 1, pole = threadIdx.x & 1;
     const double* Lr = L + (size_t)(P + 1 + pole) * nl;
     double acc = 0.0;
-    for (int n = 0; n <= p; ++n) acc += C[f * nc + n * n + n] * Lr[n * (n + 1) / 2];
+    for (int n = 0; n <= p; ++n) acc = fma(C[f * nc + n * n + n], Lr[n * (n + 1) / 2], acc);
     size_t idx = base + (size_t)f * nv + 2 * P * (P + 1) + pole;
     if (a.mixed) ((float*)a.verts)[idx] = (float)acc;
     else ((double*)a.verts)[idx] = acc;

@@ -189,3 +189,14 @@ def test_mixed_precision_lists(orc):
         assert np.array_equal(g[k], c[k]), k
     assert np.array_equal(bits(g["tau"]), bits(c["tau"]))
     assert np.all(np.abs(g["V"] - c["V"]) <= 1e-10 * np.abs(c["V"]))
+
+
+def test_contact_order_large_segments():
+    """Pairs with more contacts than one shared-memory sort chunk are merged
+    correctly: the contact list is sorted by (pair, type, a, b) and unique."""
+    sc = G.two_vesicles(p=16, seed=4, gap=0.02, approach=1.5)
+    g = run_gpu(sc, grad=False, contact_cap=1 << 16)
+    n = len(g["pair"])
+    assert n > 4096  # more than one shared-memory chunk (4096 entries)
+    key = (g["pair"].astype(np.int64) << 32) | (g["type"].astype(np.int64) << 30) | (g["a"].astype(np.int64) << 15) | g["b"]
+    assert np.all(np.diff(key) > 0)
