@@ -73,6 +73,7 @@ struct narrow_args {
   const float* vorg;
   const float* fprep;
   int64_t fstride;
+  const float4* frame;      // per candidate pair: FP32 offset of vesicle j, position error bound
   unsigned long long* q3;   // stage 3b input: (pair << 32) | (type << 30) | (a << 15) | b
   unsigned long long* q2;   // stage 4 input
   int64_t Q3, Q2;
@@ -83,6 +84,13 @@ struct narrow_args {
 };
 
 __device__ __forceinline__ int slot_of(int rr, int cc) { return rr * (STIV_BC + 1) + cc; }
+
+// Vertex coordinate as stored: double (FP64 form) or float (mixed form).
+template <bool MIXED>
+__device__ __forceinline__ double vtx(const void* X, size_t i) {
+  if (MIXED) return (double)((const float*)X)[i];
+  return ((const double*)X)[i];
+}
 
 // Order-preserving integer key of a double (-0.0 folded onto +0.0): for finite
 // a, b:  a <= b  <=>  key(a) <= key(b).
@@ -98,6 +106,7 @@ __device__ __forceinline__ long long dkey(double v) {
 // Stage patch `patch` of vesicle v; s: periodic image of the vesicle (applied
 // to both time levels in FP64, as the contact test sees it); off: FP32 offset
 // of this vesicle's frame origin from the frame of the pair.
+template <bool MIXED>
 __device__ __noinline__ void load_patch(PatchSm& S, const narrow_args& a, int v, int patch, const int* s, const float* off,
                            float dx, int lane) {
   int P = 2 * a.pv[v], W = 2 * P, nv = stiv_nverts(P);
@@ -119,8 +128,8 @@ __device__ __noinline__ void load_patch(PatchSm& S, const narrow_args& a, int v,
     if (vid >= 0) {
       for (int c = 0; c < 3; ++c) {
         size_t i0 = base + (size_t)c * nv + vid, i1 = base + (size_t)(3 + c) * nv + vid;
-        double x0 = a.mixed ? (double)((const float*)a.X)[i0] : ((const double*)a.X)[i0];
-        double x1 = a.mixed ? (double)((const float*)a.X)[i1] : ((const double*)a.X)[i1];
+        double x0 = vtx<MIXED>(a.X, i0);
+        double x1 = vtx<MIXED>(a.X, i1);
         if (s[c] != 0) { x0 = x0 + sh[c]; x1 = x1 + sh[c]; }
         long long k0 = dkey(x0), k1 = dkey(x1);
         S.key[c][k] = k0 < k1 ? k0 : k1;
@@ -234,6 +243,7 @@ __device__ __forceinline__ bool fbox_hit(const float* a, const float* b) {
 
 // Compact the primitives of S whose FP32 boxes overlap box ob.
 __device__ void filter_patch(PatchSm& S, const float* ob, int lane) {
+#pragma unroll 1
   for (int kind = 0; kind < 3; ++kind) {
     int n = kind == 0 ? S.nv : kind == 1 ? S.nt : S.ne;
     unsigned char* out = kind == 0 ? S.vf : kind == 1 ? S.tf : S.ef;
@@ -312,6 +322,7 @@ __device__ int inside_cert(int kind, const f3* x, const f3* d, float t0, float w
     gv[2] = fsub(P[2], P[1]); gd[2] = fsub(d[2], d[1]);
     gv[3] = fsub(P[3], P[1]); gd[3] = fsub(d[3], d[1]);
     bool all_in = true;
+#pragma unroll 1
     for (int k = 0; k < 3; ++k) {
       int a1 = 1 + (k + 1) % 3, a2 = 1 + (k + 2) % 3;
       gv[0] = fsub(P[a2], P[a1]); gd[0] = fsub(d[a2], d[a1]);
@@ -329,6 +340,7 @@ __device__ int inside_cert(int kind, const f3* x, const f3* d, float t0, float w
   f3 e2v = fsub(P[3], P[2]), e2d = fsub(d[3], d[2]);
   const int va[4] = {2, 2, 2, 3}, vb[4] = {0, 1, 0, 0};
   int sgn[4];
+#pragma unroll 1
   for (int k = 0; k < 4; ++k) {
     gv[0] = fsub(P[va[k]], P[vb[k]]); gd[0] = fsub(d[va[k]], d[vb[k]]);
     gv[1] = k < 2 ? e2v : e1v; gd[1] = k < 2 ? e2d : e1d;
@@ -416,6 +428,7 @@ __device__ __forceinline__ bool is_pos(double v) { return __double_as_longlong(v
 __device__ double bisect64(double k0, double k1, double k2, double k3, double lo, double hi, double flo,
                            long long& flops) {
   bool neg_lo = is_neg(flo);
+#pragma unroll 1
   for (int it = 0; it < 64; ++it) {
     double mid = __dmul_rn(__dadd_rn(lo, hi), 0.5);
     flops += 2;
@@ -504,6 +517,7 @@ __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w
   for (int i = 0; i < ncp; ++i) ends[ne++] = cp[i];
   ends[ne++] = 1.0;
   bool degen = false;
+#pragma unroll 1
   for (int s = 0; s + 1 < ne; ++s) {
     double l = ends[s], rr = ends[s + 1];
     double fl = horner3(k0, k1, k2, k3, l), fr = horner3(k0, k1, k2, k3, rr), t;
@@ -576,19 +590,12 @@ __device__ __forceinline__ void desc_points(const narrow_args& a, unsigned long 
 }
 
 // FP32 frame of pair r: origin of vesicle i; offset of vesicle j's origin
-// (with its periodic image) and the bound on the FP32 position error.
+// (with its periodic image) and the bound on the FP32 position error, computed
+// once per candidate pair by patch_pairs_kernel.
 __device__ __forceinline__ float pair_frame(const narrow_args& a, int r, float* offB) {
-  int vi = a.ci[r], vj = a.cj[r], code = a.cs[r];
-  int s1[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
-  float dmax = 0.f;
-  for (int c = 0; c < 3; ++c) {
-    double o = ((double)a.vorg[4 * vj + c] + s1[c] * a.L[c]) - (double)a.vorg[4 * vi + c];
-    offB[c] = (float)o;
-    dmax = fmaxf(dmax, fabsf(offB[c]));
-  }
-  // |FP32 position - exact position| per component: rounding of X0 - origin,
-  // of the frame offset and of the frame change (generous)
-  return 2.3841858e-7f * (a.vorg[4 * vi + 3] + a.vorg[4 * vj + 3] + 2.0f * dmax);  // 2^-22 (...)
+  float4 f = a.frame[r];
+  offB[0] = f.x; offB[1] = f.y; offB[2] = f.z;
+  return f.w;
 }
 
 // FP32 points of a descriptor in the frame of its pair (for stage 3b).
@@ -692,6 +699,7 @@ __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, in
 }
 
 // Stages 1-3a: one warp per patch pair.
+template <bool MIXED>
 __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
   extern __shared__ unsigned char smraw[];
   WarpSm& ws = ((WarpSm*)smraw)[threadIdx.x >> 5];
@@ -712,13 +720,14 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
     float offA[3] = {0.f, 0.f, 0.f}, offB[3];
     float dx = pair_frame(a, r, offB);
     if (lane == 0) ws.dx = dx;
-    load_patch(ws.A, a, vi, pa, s0, offA, dx, lane);
-    load_patch(ws.B, a, vj, pb, s1, offB, dx, lane);
+    load_patch<MIXED>(ws.A, a, vi, pa, s0, offA, dx, lane);
+    load_patch<MIXED>(ws.B, a, vj, pb, s1, offB, dx, lane);
     filter_patch(ws.A, ws.B.box, lane);
     filter_patch(ws.B, ws.A.box, lane);
     if (lane == 0) ws.n1 = 0;
     __syncwarp();
     // stage 1: FP32 boxes.  VF: vertices of A vs triangles of B (0), vertices of B vs triangles of A (1)
+#pragma unroll 1
     for (int dir = 0; dir < 2; ++dir) {
       const PatchSm& V = dir == 0 ? ws.A : ws.B;
       const PatchSm& T = dir == 0 ? ws.B : ws.A;
@@ -728,6 +737,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
         int y = valid ? T.tf[yk] : 0;
         float tb[6];
         tri_box(T, y, tb);
+#pragma unroll 1
         for (int xk = 0; xk < V.nvf; ++xk) {
           int x = V.vf[xk];
           float vb[6];
@@ -744,6 +754,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
         int y = valid ? ws.B.ef[yk] : 0;
         float eb[6];
         edge_box(ws.B, y, eb);
+#pragma unroll 1
         for (int xk = 0; xk < ws.A.nef; ++xk) {
           int x = ws.A.ef[xk];
           float ab[6];
@@ -808,6 +819,7 @@ __global__ void __launch_bounds__(PW * 32) pieces_kernel(narrow_args a) {
         W.fail[lane] = 1;   // may vanish identically: FP64 decides (degenerate)
       } else {
         const float w = 1.0f / NPIECE;
+#pragma unroll 2
         for (int p = 0; p < NPIECE; ++p) {
           float t0 = p * w;
           float f0 = fmaf(fmaf(fmaf(q.k3, t0, q.k2), t0, q.k1), t0, q.k0);
@@ -832,6 +844,7 @@ __global__ void __launch_bounds__(PW * 32) pieces_kernel(narrow_args a) {
     if (lane == 0) W.ntask2 = 0;
     __syncwarp();
     if (total > MAXTASK) total = MAXTASK;
+#pragma unroll 1
     for (int t0 = 0; t0 < total; t0 += 32) {
       int t = t0 + lane;
       if (t < total) {
@@ -852,6 +865,7 @@ __global__ void __launch_bounds__(PW * 32) pieces_kernel(narrow_args a) {
     }
     __syncwarp();
     int total2 = min(W.ntask2, MAXTASK);
+#pragma unroll 1
     for (int t0 = 0; t0 < total2; t0 += 32) {
       int t = t0 + lane;
       if (t < total2) {
@@ -881,6 +895,7 @@ __global__ void __launch_bounds__(PW * 32) pieces_kernel(narrow_args a) {
 // ---------------------------------------------------------------------------
 // stage 4: the FP64 contact test, one descriptor per thread.
 // ---------------------------------------------------------------------------
+template <bool MIXED>
 __global__ void __launch_bounds__(128) fp64_kernel(narrow_args a) {
   int lane = threadIdx.x & 31;
   int64_t n2 = a.ctr[15];
@@ -906,8 +921,8 @@ __global__ void __launch_bounds__(128) fp64_kernel(narrow_args a) {
         double p0[3], p1[3];
         for (int c = 0; c < 3; ++c) {
           size_t i0 = vb + (size_t)c * nv, i1 = vb + (size_t)(3 + c) * nv;
-          p0[c] = a.mixed ? (double)((const float*)a.X)[i0] : ((const double*)a.X)[i0];
-          p1[c] = a.mixed ? (double)((const float*)a.X)[i1] : ((const double*)a.X)[i1];
+          p0[c] = vtx<MIXED>(a.X, i0);
+          p1[c] = vtx<MIXED>(a.X, i1);
           if (onj[q] && sB[c] != 0) { double sh = sB[c] * a.L[c]; p0[c] = p0[c] + sh; p1[c] = p1[c] + sh; }
         }
         X0[q] = {p0[0], p0[1], p0[2]};
@@ -951,7 +966,8 @@ __global__ void __launch_bounds__(128) fp64_kernel(narrow_args a) {
 __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, const double* vbox, const float* pbox,
                                                           double Lx, double Ly, double Lz, const int32_t* ci,
                                                           const int32_t* cj, const int32_t* cs, int64_t cap,
-                                                          int64_t W, uint64_t* work, int64_t* ctr, int mp) {
+                                                          int64_t W, uint64_t* work, int64_t* ctr, int mp,
+                                                          const float* vorg, float4* frame) {
   extern __shared__ float psm[];
   int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* sbw = psm + (size_t)wid * 2 * mp * 6;                       // [2][mp][6]
@@ -964,6 +980,18 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
     int i = ci[r], j = cj[r], code = cs[r];
     int s[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
     int Pi = 2 * pv[i], Pj = 2 * pv[j];
+    if (lane == 0) {
+      // FP32 frame of the pair: origin of vesicle i; |FP32 position - exact
+      // position| per component is bounded by 2^-22 (R_i + R_j + 2 |offset|)
+      // (rounding of X0 - origin, of the offset and of the frame change)
+      float o[3], dmax = 0.f;
+      for (int c = 0; c < 3; ++c) {
+        double d = ((double)vorg[4 * j + c] + s[c] * L[c]) - (double)vorg[4 * i + c];
+        o[c] = (float)d;
+        dmax = fmaxf(dmax, fabsf(o[c]));
+      }
+      frame[r] = make_float4(o[0], o[1], o[2], 2.3841858e-7f * (vorg[4 * i + 3] + vorg[4 * j + 3] + 2.0f * dmax));
+    }
     int ni = stiv_npatches(Pi), nj = stiv_npatches(Pj);
     float shlo[3], shhi[3];
     for (int c = 0; c < 3; ++c) {
@@ -1040,11 +1068,14 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   {
     STIV_PROF(h, st, "patch_pairs");
     patch_pairs_kernel<<<blocks, 128, psmem, st>>>(p_dev, w.vbox, w.pbox, L[0], L[1], L[2], cand->i, cand->j,
-                                                   cand->shift, cand->capacity, w.W, w.work, w.ctr, mp);
+                                                   cand->shift, cand->capacity, w.W, w.work, w.ctr, mp, w.vorg,
+                                                   w.frame);
   }
   STIV_LAUNCH(h);
   narrow_args a;
-  a.pv = p_dev; a.voff = voff; a.X = X; a.mixed = h->prm.precision == STIV_MIXED;
+  bool mixed = h->prm.precision == STIV_MIXED;
+  a.pv = p_dev; a.voff = voff; a.X = X; a.mixed = mixed;
+  a.frame = w.frame;
   a.L[0] = L[0]; a.L[1] = L[1]; a.L[2] = L[2];
   a.ci = cand->i; a.cj = cand->j; a.cs = cand->shift;
   a.work = w.work; a.W = w.W; a.include_ee = h->prm.include_ee; a.exact_only = w.exact_only;
@@ -1055,13 +1086,14 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   a.rc_tau = w.tmp_f64; a.rc_w = w.tmp_f64 + w.C;
   a.ctr = w.ctr;
   size_t smem = stiv_narrow_smem();
-  STIV_CUDA(h, cudaFuncSetAttribute(narrow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto nk = mixed ? narrow_kernel<true> : narrow_kernel<false>;
+  STIV_CUDA(h, cudaFuncSetAttribute(nk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  STIV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, narrow_kernel, NW * 32, smem));
+  STIV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nk, NW * 32, smem));
   if (per_sm < 1) per_sm = 1;
   {
     STIV_PROF(h, st, "narrow");
-    narrow_kernel<<<per_sm * num_sms, NW * 32, smem, st>>>(a);
+    nk<<<per_sm * num_sms, NW * 32, smem, st>>>(a);
   }
   STIV_LAUNCH(h);
   if (!w.exact_only) {
@@ -1076,7 +1108,8 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   STIV_LAUNCH(h);
   {
     STIV_PROF(h, st, "fp64");
-    fp64_kernel<<<num_sms * 16, 128, 0, st>>>(a);
+    auto fk = mixed ? fp64_kernel<true> : fp64_kernel<false>;
+    fk<<<num_sms * 16, 128, 0, st>>>(a);
   }
   STIV_LAUNCH(h);
   return STIV_OK;

@@ -83,6 +83,7 @@ struct detect_ws {
   uint64_t* pkey2;       // [Q]
   int32_t* pval2;        // [Q]
   uint64_t* work;        // [W]  patch-pair work items
+  float4* frame;         // [pair capacity]  FP32 frame of each candidate pair
   unsigned long long* q3;  // [Q3] primitive pairs left for the FP32 piece tests
   unsigned long long* q2;  // [Q2] primitive pairs left for the FP64 contact test
   int64_t Q3, Q2;
