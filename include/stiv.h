@@ -150,7 +150,7 @@ int stiv_upsample(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, co
                   const int64_t* coef_off_dev, const double* coef_dev,
                   const int64_t* vert_off_dev, void* verts_dev);
 
-/* Alg. 2 lines 2-6 without the distribution steps: vesicle space-time boxes,
+/* Alg. 2's detection part without the distribution steps: vesicle space-time boxes,
  * candidate pairs (Alg. 1: Morton-grid sort and bbiCheck), then every
  * vertex-triangle pair (both directions) and edge-edge pair of each candidate
  * whose swept boxes overlap is tested with Eq. 3.1 (d_m = 0).  cand and out
@@ -224,7 +224,7 @@ int stiv_profile_read(stiv_handle* h, int32_t max_names, char* names, int64_t* l
 int stiv_sync_counts(void* stream, const int64_t* counts_dev, int64_t* counts_host);
 
 /* Stable LSD radix sort of (key, value) pairs on the low key_bits bits of the
- * 64-bit keys (Alg. 1 line 4, the check-point sort, on one GPU).  scratch:
+ * 64-bit keys (Alg. 1's check-point sort, on one GPU).  scratch:
  * at least stiv_sort_scratch_bytes(n) bytes of device memory. */
 size_t stiv_sort_scratch_bytes(int64_t n);
 int stiv_sort_pairs(void* stream, int64_t n, int32_t key_bits, const uint64_t* keys_in,

@@ -4,15 +4,15 @@
 //   1. vesicle boxes: exact FP64 min/max of X0 and X1 over all vertices, padded
 //      by d_m; patch boxes (4 x 8 grid quads and their vertices) in FP32,
 //      rounded outward, for the narrow phase;
-//   2. h_m = mean box diagonal (Alg. 1 line 1), cell size of a uniform grid
+//   2. h_m = mean box diagonal (Alg. 1, grid spacing), cell size of a uniform grid
 //      (periodic axes: L / floor(L / h_m));
 //   3. each box lists the cells it overlaps (an exact cell-range enumeration
-//      standing in for the check points of Alg. 1 line 2), keyed by the
+//      standing in for the check points of Alg. 1), keyed by the
 //      Morton id of the (wrapped) cell;
-//   4. stable radix sort by Morton id (Alg. 1 line 4);
+//   4. stable radix sort by Morton id (Alg. 1, check-point sort);
 //   5. all box pairs within a cell: the image shift follows from the unwrapped
-//      cell coordinates, then bbiCheck in FP64 (Alg. 1 lines 5-9);
-//   6. sort + unique (Alg. 1 line 11) -> pairs (i < j, shift), ascending.
+//      cell coordinates, then bbiCheck in FP64 (Alg. 1, per-cell loop);
+//   6. sort + unique (Alg. 1, final step) -> pairs (i < j, shift), ascending.
 #include "stiv_internal.cuh"
 
 #include <math.h>
@@ -235,7 +235,7 @@ __device__ __forceinline__ bool bbi(const double* a, const double* b) {
   return a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] && b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
 }
 
-// Alg. 1 lines 5-9: every record against the later records of its cell.
+// Alg. 1, per-cell loop: every record against the later records of its cell.
 __global__ void cell_pairs_kernel(const int64_t* nrec_dev, int64_t R, const uint64_t* key, const int32_t* val,
                                   const int32_t* rbox, const int32_t* rcell, const double* vbox,
                                   const double* grid, double Lx, double Ly, double Lz, int64_t Q,
@@ -283,7 +283,7 @@ __global__ void cell_pairs_kernel(const int64_t* nrec_dev, int64_t R, const uint
   }
 }
 
-// Alg. 1 line 11: unique sorted keys -> output pair list; one CTA.
+// Alg. 1, final step: unique sorted keys -> output pair list; one CTA.
 __global__ void __launch_bounds__(1024) unique_pairs_kernel(const int64_t* nkey_dev, int64_t Q, const uint64_t* key,
                                                             int64_t cap, int32_t* oi, int32_t* oj, int32_t* os,
                                                             int64_t* ctr) {

@@ -1,6 +1,6 @@
 // Stable LSD radix sort of (64-bit key, int32 value) pairs, 8-bit digits.
 //
-// Replaces the distributed hypercube quicksort of Alg. 1 line 4 (Sec. 3.3.1,
+// Replaces the distributed hypercube quicksort of Alg. 1's check-point sort (Sec. 3.3.1,
 // Table 3) on one GPU: equal keys keep their input order, so the payload is
 // "scattered" exactly as in Table 3.  The item count may live on the device
 // (n_dev); the host passes an upper bound for the launch shapes.

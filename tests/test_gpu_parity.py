@@ -28,7 +28,7 @@ def test_mesh_topology(orc, P):
 
 
 def test_sort_table3_fixture():
-    """Alg. 1 line 4 on the GPU: Table 3's keys and payloads."""
+    """Alg. 1's check-point sort on the GPU: Table 3's keys and payloads."""
     t = load_table3()
     n = 8
     keys = torch.tensor(t["unsorted_M"], dtype=torch.int64, device="cuda")
