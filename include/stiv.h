@@ -231,6 +231,28 @@ int stiv_sort_pairs(void* stream, int64_t n, int32_t key_bits, const uint64_t* k
                     const int32_t* vals_in, uint64_t* keys_out, int32_t* vals_out,
                     void* scratch, size_t scratch_bytes);
 
+/* Allocation-free stiv_sort_pairs (the paper has no counterpart: this is an
+ * interface for callers, not part of the method).  For callers that cannot
+ * hand the library a scratch buffer or let it call cudaMalloc: code running
+ * under another framework's device memory pool that owns all device memory,
+ * latency-bound loops where cudaMalloc/cudaFree could synchronise the device,
+ * or processes at their allocation limit.  Same sort and same result as
+ * stiv_sort_pairs; its scratch is a fixed static device array inside the
+ * library (about 13.6 MB, held on every GPU that loads the library until the
+ * process exits).
+ *   - n <= STIV_SORT_STATIC_MAX, else STIV_ERR_ARG (nothing is launched);
+ *   - keys_in/vals_in are left intact; keys_out/vals_out receive the result;
+ *   - calls no cudaMalloc, cudaFree or allocating library routine;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture on the device;
+ *   - all calls on a device share the one array, which keeps the previous
+ *     call's contents: calls that overlap on the GPU (different streams, or
+ *     concurrent host threads) race and must be serialised by the caller. */
+#define STIV_SORT_STATIC_MAX (1 << 20)
+int stiv_sort_pairs_static(void* stream, int64_t n, int32_t key_bits, const uint64_t* keys_in,
+                           const int32_t* vals_in, uint64_t* keys_out, int32_t* vals_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,8 @@ F_PAIRS_OVERFLOW, F_CONTACTS_OVERFLOW, F_BOX_TOO_SMALL, F_NONFINITE, F_WORK_OVER
 EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_error", "stiv_mesh_topology",
            "stiv_upsample", "stiv_detect", "stiv_stiv", "stiv_stiv_grad", "stiv_grad_scatter",
            "stiv_grad_to_coef", "stiv_step", "stiv_sync_counts", "stiv_sort_scratch_bytes", "stiv_sort_pairs",
-           "stiv_profile", "stiv_profile_read"]
+           "stiv_profile", "stiv_profile_read", "stiv_sort_pairs_static"]
+SORT_STATIC_MAX = 1 << 20
 
 
 class StivError(RuntimeError):
@@ -90,6 +91,7 @@ def lib() -> ctypes.CDLL:
     L.stiv_sort_scratch_bytes.argtypes = [i64]
     L.stiv_sort_scratch_bytes.restype = ctypes.c_size_t
     L.stiv_sort_pairs.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, ctypes.c_size_t]
+    L.stiv_sort_pairs_static.argtypes = [vp, i64, i32, vp, vp, vp, vp]
     L.stiv_profile.argtypes = [vp, i32]
     L.stiv_profile_read.argtypes = [vp, i32, vp, vp, vp, vp]
     _lib = L
@@ -190,6 +192,14 @@ def stiv_sort_pairs(stream, n, key_bits, keys_in_ptr, vals_in_ptr, keys_out_ptr,
                     scratch_bytes):
     _check(lib().stiv_sort_pairs(stream, n, key_bits, keys_in_ptr, vals_in_ptr, keys_out_ptr, vals_out_ptr,
                                  scratch_ptr, scratch_bytes), "stiv_sort_pairs")
+
+
+def stiv_sort_pairs_static(stream, n, key_bits, keys_in_ptr, vals_in_ptr, keys_out_ptr, vals_out_ptr):
+    """Same sort as stiv_sort_pairs without caller scratch: it runs on a fixed
+    static device array of the library (n <= SORT_STATIC_MAX).  For callers
+    that cannot allocate device memory; calls that overlap on the GPU race."""
+    _check(lib().stiv_sort_pairs_static(stream, n, key_bits, keys_in_ptr, vals_in_ptr, keys_out_ptr,
+                                        vals_out_ptr), "stiv_sort_pairs_static")
 
 
 def stiv_profile(h: int, enable: bool):

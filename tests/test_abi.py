@@ -36,3 +36,10 @@ def test_status_strings_without_gpu():
     from paper_1812_04719_gb300 import stiv
     assert stiv.status_string(0) == "ok"
     assert "capacity" in stiv.status_string(2)
+
+
+def test_static_sort_limit_matches_header():
+    from paper_1812_04719_gb300 import stiv
+    src = open(os.path.join(ROOT, "include", "stiv.h")).read()
+    m = re.search(r"#define\s+STIV_SORT_STATIC_MAX\s+\(1 << (\d+)\)", src)
+    assert m and stiv.SORT_STATIC_MAX == 1 << int(m.group(1))
