@@ -202,7 +202,7 @@ def contacts(P_ves, X_list_or_flat, pairs, L, eps_dt: float, prune: bool = True,
     a flat float64 array with offsets ``voff``.  pairs: rows (i, j, sx, sy, sz).
     Returns a dict: pair, type, a, b, tau, w[.,2], V (per contact), V_pair (per
     pair row), grad [.,4,3], gves/gvid [.,4], counts (contacts, prim pairs
-    tested, degenerate)."""
+    tested, degenerate, floating-point operations of the contact tests)."""
     P_ves = np.ascontiguousarray(P_ves, dtype=np.int32)
     if voff is None:
         sizes = [6 * nverts(int(P)) for P in P_ves]
@@ -214,7 +214,7 @@ def contacts(P_ves, X_list_or_flat, pairs, L, eps_dt: float, prune: bool = True,
     pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 5)
     Lv = np.ascontiguousarray(np.broadcast_to(np.asarray(L, dtype=np.float64), (3,)))
     npairs = pairs.shape[0]
-    counts = np.zeros(3, dtype=np.int64)
+    counts = np.zeros(4, dtype=np.int64)
     V_pair = np.zeros(max(npairs, 1))
     L_ = lib()
     args_head = (len(P_ves), _i(P_ves), _l(voff), _d(flat), npairs, _i(pairs if npairs else np.zeros((1, 5), np.int32)),

@@ -313,19 +313,24 @@ static void cubic_coeffs(v3 a, v3 b, v3 c, v3 da, v3 db, v3 dc, double k[4]) {
 
 static double horner(const double k[4], double t) { return fma(fma(fma(k[3], t, k[2]), t, k[1]), t, k[0]); }
 
-/* Critical points of f in the open interval (0,1), ascending; returns count. */
-static int critical_points(const double k[4], double cp[2]) {
+/* Critical points of f in the open interval (0,1), ascending; returns count.
+ * *ops counts the floating-point operations executed (see ccd_pair). */
+static int critical_points(const double k[4], double cp[2], int64_t* ops) {
   double d0 = k[1], d1 = 2.0 * k[2], d2 = 3.0 * k[3];
   double r[2]; int nr = 0;
+  *ops += 2;
   if (d2 != 0.0) {
     double disc = fma(d1, d1, -((4.0 * d2) * d0));
+    *ops += 4;
     if (disc > 0.0) {
       double sq = sqrt(disc);
       double q = -0.5 * (d1 + (d1 >= 0.0 ? sq : -sq));
       r[0] = q / d2; r[1] = d0 / q; nr = 2;
+      *ops += 5;
     }
   } else if (d1 != 0.0) {
     r[0] = -d0 / d1; nr = 1;
+    *ops += 1;
   }
   int n = 0;
   for (int i = 0; i < nr; ++i) if (r[i] > 0.0 && r[i] < 1.0) cp[n++] = r[i];
@@ -340,11 +345,13 @@ static int critical_points(const double k[4], double cp[2]) {
  * at most 64 halvings; stops when the midpoint equals an end or f(mid) == 0.
  * Returns the left end of the final bracket (the last time before the sign
  * change), or mid when f(mid) == 0. */
-static double bisect(const double k[4], double lo, double hi, double flo) {
+static double bisect(const double k[4], double lo, double hi, double flo, int64_t* ops) {
   for (int it = 0; it < 64; ++it) {
     double mid = (lo + hi) * 0.5;
+    *ops += 2;
     if (!(mid > lo && mid < hi)) break;
     double fm = horner(k, mid);
+    *ops += 6;
     if (fm == 0.0) return mid;
     if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; }
     else hi = mid;
@@ -360,13 +367,15 @@ enum { ORC_HIT = 1, ORC_DEGEN = 2 };
  * EE: parameters (s, u) of the closest points p0 + s d1 and q0 + u d2 of the
  * two lines; inside iff both in [0, 1].  Y: positions at t (4 points: VF
  * xp,x0,x1,x2; EE p0,p1,q0,q1).  Returns 1 inside, 0 outside, -1 degenerate. */
-static int inside_test(int kind, const v3* Y, double* w1, double* w2) {
+static int inside_test(int kind, const v3* Y, double* w1, double* w2, int64_t* ops) {
+  *ops += 9 + 25 + 3;  /* 3 differences, 5 dot products, determinant */
   if (kind == ORC_VF) {
     v3 a = v3sub(Y[2], Y[1]), b = v3sub(Y[3], Y[1]), c = v3sub(Y[0], Y[1]);
     double d00 = v3dot(a, a), d01 = v3dot(a, b), d11 = v3dot(b, b);
     double d20 = v3dot(c, a), d21 = v3dot(c, b);
     double den = fma(d00, d11, -(d01 * d01));
     if (!(den > 0.0)) return -1;
+    *ops += 4 + 4 + 2;
     double b1 = fma(d11, d20, -(d01 * d21)) / den;
     double b2 = fma(d00, d21, -(d01 * d20)) / den;
     double b0 = (1.0 - b1) - b2;
@@ -378,6 +387,7 @@ static int inside_test(int kind, const v3* Y, double* w1, double* w2) {
     double C = v3dot(d1, r), F = v3dot(d2, r);
     double den = fma(A, E, -(B * B));
     if (!(den > 0.0)) return -1;
+    *ops += 4 + 4;
     double s = fma(B, F, -(C * E)) / den;
     double u = fma(A, F, -(B * C)) / den;
     *w1 = s; *w2 = u;
@@ -393,8 +403,12 @@ static int inside_test(int kind, const v3* Y, double* w1, double* w2) {
  * that passes the inside test is the contact time.  f identically zero
  * (coplanar for the whole step) or a degenerate inside test is reported as
  * ORC_DEGEN and is not a contact.  Returns 0 (no contact), ORC_HIT or
- * ORC_DEGEN; on a hit writes tau and the two inside-test weights. */
-static int ccd_pair(int kind, const v3* P0, const v3* D, double* tau, double* w1, double* w2) {
+ * ORC_DEGEN; on a hit writes tau and the two inside-test weights.
+ * *ops (if not NULL) is increased by the number of floating-point operations
+ * the procedure executed on this pair: +, -, *, /, sqrt count 1, fma 2,
+ * negation and comparisons 0 (the algorithmic work of the contact test). */
+static int ccd_pair(int kind, const v3* P0, const v3* D, double* tau, double* w1, double* w2, int64_t* ops_out) {
+  int64_t ops = 18 + 39 + 32;  /* 6 differences, 4 cross products + sum, 6 dot products + 2 sums */
   v3 a, b, c, da, db, dc;
   if (kind == ORC_VF) {  /* points: xp, x0, x1, x2 */
     a = v3sub(P0[2], P0[1]); b = v3sub(P0[3], P0[1]); c = v3sub(P0[0], P0[1]);
@@ -405,9 +419,12 @@ static int ccd_pair(int kind, const v3* P0, const v3* D, double* tau, double* w1
   }
   double k[4];
   cubic_coeffs(a, b, c, da, db, dc, k);
-  if (k[0] == 0.0 && k[1] == 0.0 && k[2] == 0.0 && k[3] == 0.0) return ORC_DEGEN;
+  if (k[0] == 0.0 && k[1] == 0.0 && k[2] == 0.0 && k[3] == 0.0) {
+    if (ops_out) *ops_out += ops;
+    return ORC_DEGEN;
+  }
   double cp[2];
-  int ncp = critical_points(k, cp);
+  int ncp = critical_points(k, cp, &ops);
   double ends[4]; int ne = 0;
   ends[ne++] = 0.0;
   for (int i = 0; i < ncp; ++i) ends[ne++] = cp[i];
@@ -416,17 +433,24 @@ static int ccd_pair(int kind, const v3* P0, const v3* D, double* tau, double* w1
   for (int s = 0; s + 1 < ne; ++s) {
     double l = ends[s], r = ends[s + 1];
     double fl = horner(k, l), fr = horner(k, r), t;
+    ops += 12;
     if (fl == 0.0) t = l;
     else if (fr == 0.0) t = r;
-    else if ((fl < 0.0) != (fr < 0.0)) t = bisect(k, l, r, fl);
+    else if ((fl < 0.0) != (fr < 0.0)) t = bisect(k, l, r, fl, &ops);
     else continue;
     v3 Y[4];
     for (int q = 0; q < 4; ++q) Y[q] = v3lerp(P0[q], t, D[q]);
+    ops += 24;
     double u1 = 0.0, u2 = 0.0;
-    int in = inside_test(kind, Y, &u1, &u2);
+    int in = inside_test(kind, Y, &u1, &u2, &ops);
     if (in < 0) { degen = 1; continue; }
-    if (in == 1) { *tau = t; *w1 = u1; *w2 = u2; return ORC_HIT; }
+    if (in == 1) {
+      *tau = t; *w1 = u1; *w2 = u2;
+      if (ops_out) *ops_out += ops;
+      return ORC_HIT;
+    }
   }
+  if (ops_out) *ops_out += ops;
   return degen ? ORC_DEGEN : 0;
 }
 
@@ -439,7 +463,7 @@ int orc_ccd_primitive(int kind, const double* X0, const double* X1, double* out)
     D[q].x = X1[3 * q] - X0[3 * q]; D[q].y = X1[3 * q + 1] - X0[3 * q + 1]; D[q].z = X1[3 * q + 2] - X0[3 * q + 2];
   }
   double t = 0.0, w1 = 0.0, w2 = 0.0;
-  int st = ccd_pair(kind, P0, D, &t, &w1, &w2);
+  int st = ccd_pair(kind, P0, D, &t, &w1, &w2, NULL);
   out[0] = t; out[1] = w1; out[2] = w2;
   return st;
 }
@@ -560,7 +584,7 @@ int orc_stiv_primitive(int kind, const double* X0, const double* X1, double eps_
     D[q] = v3sub(P1[q], P0[q]);
   }
   double t, w1, w2;
-  int st = ccd_pair(kind, P0, D, &t, &w1, &w2);
+  int st = ccd_pair(kind, P0, D, &t, &w1, &w2, NULL);
   memset(out, 0, sizeof(double) * 13);
   if (st != ORC_HIT) return st;
   out[0] = stiv_pair_dual(kind, P0, P1, t, eps_dt, out + 1);
@@ -611,7 +635,7 @@ typedef struct {
   int64_t cap, n;
   int32_t* type; int32_t* a; int32_t* b;
   double* tau; double* w;   /* w: [cap][2] */
-  int64_t n_boxpairs, n_degen;
+  int64_t n_boxpairs, n_degen, n_ops;
 } contact_out;
 
 static void push_contact(contact_out* o, int type, int a, int b, double tau, double w1, double w2) {
@@ -678,8 +702,9 @@ static void pair_contacts(const ves_view* A, const ves_view* B, int prune, int i
         }
         o->n_boxpairs++;
         for (int q = 0; q < 4; ++q) D[q] = v3sub(P1[q], P0[q]);
+        o->n_ops += 12;  /* the displacements */
         double tau, w1, w2;
-        int st = ccd_pair(ORC_VF, P0, D, &tau, &w1, &w2);
+        int st = ccd_pair(ORC_VF, P0, D, &tau, &w1, &w2, &o->n_ops);
         if (st == ORC_HIT) push_contact(o, dir, vp, t, tau, w1, w2);
         else if (st == ORC_DEGEN) o->n_degen++;
       }
@@ -700,8 +725,9 @@ static void pair_contacts(const ves_view* A, const ves_view* B, int prune, int i
         }
         o->n_boxpairs++;
         for (int q = 0; q < 4; ++q) D[q] = v3sub(P1[q], P0[q]);
+        o->n_ops += 12;  /* the displacements */
         double tau, w1, w2;
-        int st = ccd_pair(ORC_EE, P0, D, &tau, &w1, &w2);
+        int st = ccd_pair(ORC_EE, P0, D, &tau, &w1, &w2, &o->n_ops);
         if (st == ORC_HIT) push_contact(o, 2, ea, eb, tau, w1, w2);
         else if (st == ORC_DEGEN) o->n_degen++;
       }
@@ -768,7 +794,8 @@ static ves_view make_view(topo_cache* tc, const int* Pv, const int64_t* voff, co
  * sum of the pair's V_k in that order.  If grad != NULL, per contact the
  * gradient [4][3] w.r.t. X1 of the 4 points and, per point, its vesicle
  * (gves) and local vertex id (gvid) are written.
- * counts[0] = contacts, [1] = primitive pairs tested, [2] = degenerate.
+ * counts[0] = contacts, [1] = primitive pairs tested, [2] = degenerate,
+ * [3] = floating-point operations of the contact tests (ccd_pair's count).
  * OpenMP over pairs when compiled with it (nthreads <= 0: default). */
 int64_t orc_contacts(int nv_ves, const int* Pv, const int64_t* voff, const double* X,
                      int64_t npairs, const int32_t* pairs, const double* L,
@@ -784,10 +811,10 @@ int64_t orc_contacts(int nv_ves, const int* Pv, const int64_t* voff, const doubl
   }
   int64_t* pcnt = (int64_t*)calloc(npairs + 1, sizeof(int64_t));
   contact_out* outs = (contact_out*)calloc(npairs, sizeof(contact_out));
-  int64_t nbox = 0, ndeg = 0;
+  int64_t nbox = 0, ndeg = 0, nops = 0;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbox, ndeg)
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbox, ndeg, nops)
 #endif
   for (int64_t r = 0; r < npairs; ++r) {
     int i = pairs[5 * r], j = pairs[5 * r + 1];
@@ -797,7 +824,7 @@ int64_t orc_contacts(int nv_ves, const int* Pv, const int64_t* voff, const doubl
     memset(&outs[r], 0, sizeof(contact_out));
     pair_contacts(&A, &B, prune, include_ee, &outs[r]);
     int64_t n = outs[r].n;
-    nbox += outs[r].n_boxpairs; ndeg += outs[r].n_degen;
+    nbox += outs[r].n_boxpairs; ndeg += outs[r].n_degen; nops += outs[r].n_ops;
     pcnt[r] = n;
   }
   int64_t total = 0;
@@ -831,7 +858,7 @@ int64_t orc_contacts(int nv_ves, const int* Pv, const int64_t* voff, const doubl
   }
   for (int i = 0; i < ncache; ++i) { free(cache[i].tri); free(cache[i].edge); }
   free(pcnt); free(outs);
-  if (counts) { counts[0] = total; counts[1] = nbox; counts[2] = ndeg; }
+  if (counts) { counts[0] = total; counts[1] = nbox; counts[2] = ndeg; counts[3] = nops; }
   return total;
 }
 

@@ -423,8 +423,9 @@ __device__ __forceinline__ bool is_neg(double v) {  // v < 0.0
 }
 __device__ __forceinline__ bool is_pos(double v) { return __double_as_longlong(v) > 0; }  // v > 0.0, v not NaN
 
-// FP64 flops of the procedure, counted as executed (fma = 2): the
-// algorithmic work of the exact contact test, reported for the roofline.
+// FP64 operations of the procedure, counted as executed (+ - * / sqrt = 1,
+// fma = 2, negations and comparisons 0): the algorithmic work of the exact
+// contact test, reported for the roofline.
 __device__ double bisect64(double k0, double k1, double k2, double k3, double lo, double hi, double flo,
                            long long& flops) {
   bool neg_lo = is_neg(flo);
@@ -474,7 +475,7 @@ __device__ int inside64(int kind, const d3* Y, double& w1, double& w2) {
 
 // 0 no contact, 1 contact, 2 degenerate.
 __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w1, double& w2, long long& flops) {
-  flops += 18 + 9 + 21 + 9 + 32;  // differences, three cross products (+ sum), four dot products
+  flops += 18 + 9 + 21 + 9 + 32;  // differences, cross products (+ sum), 6 dot products + 2 sums
   d3 a, b, c, da, db, dc;
   if (kind == KIND_VF) {
     a = d3_sub(X0[2], X0[1]); b = d3_sub(X0[3], X0[1]); c = d3_sub(X0[0], X0[1]);
@@ -498,13 +499,14 @@ __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w
     double disc = __fma_rn(e1, e1, -__dmul_rn(__dmul_rn(4.0, e2), e0));
     flops += 4;
     if (is_pos(disc)) {
-      flops += 6;
+      flops += 5;
       double sq = __dsqrt_rn(disc);
       double q = __dmul_rn(-0.5, __dadd_rn(e1, !is_neg(e1) ? sq : -sq));
       r[0] = __ddiv_rn(q, e2); r[1] = __ddiv_rn(e0, q); nr = 2;
     }
   } else if (!is_zero(e1)) {
     r[0] = __ddiv_rn(-e0, e1); nr = 1;
+    flops += 1;
   }
   double cp[2]; int ncp = 0;
   for (int i = 0; i < nr; ++i) if (r[i] > 0.0 && r[i] < 1.0) cp[ncp++] = r[i];
@@ -526,11 +528,12 @@ __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w
     else if (is_zero(fr)) t = rr;
     else if (is_neg(fl) != is_neg(fr)) t = bisect64(k0, k1, k2, k3, l, rr, fl, flops);
     else continue;
-    flops += 24 + 9 + 25 + 3 + 6 + 2 + 2;  // positions, differences, dots, determinant, numerators, divisions
+    flops += 24 + 9 + 25 + 3;  // positions, differences, dot products, determinant
     d3 Y[4];
     for (int q = 0; q < 4; ++q) Y[q] = d3_at(X0[q], t, D[q]);
     double u1 = 0.0, u2 = 0.0;
     int in = inside64(kind, Y, u1, u2);
+    if (in >= 0) flops += kind == KIND_VF ? 10 : 8;  // numerators, divisions (and 1 - b1 - b2)
     if (in < 0) { degen = true; continue; }
     if (in == 1) { tau = t; w1 = u1; w2 = u2; return 1; }
   }

@@ -120,6 +120,22 @@ def test_detect_bit_exact(orc, name):
     assert g["counts"][S.C_CPAIRS] == int((c["V_pair"] > 0).sum())
 
 
+@pytest.mark.parametrize("name", ["cluster_p4", "periodic_p3", "uneven_p234"])
+def test_operation_count_exact_mode(orc, name):
+    """With the FP32 rejection off every primitive pair of the exact box test
+    reaches the FP64 contact test, so the operations the kernel counts equal
+    the oracle's count of the same procedure (the roofline's algorithmic
+    work), operation for operation."""
+    sc = SCENES[name]()
+    eng = S.Stiv.for_scene(sc, pair_cap=256, contact_cap=4096, exact_only=True)
+    g = run_gpu(sc, eng=eng)
+    Xs = verts_list(sc, g["verts"])
+    c = orc.contacts(sc.P, Xs, gpu_pairs_rows(g), sc.L, sc.eps * sc.dt)
+    assert g["counts"][S.C_PRIM] == c["counts"][1]
+    assert g["counts"][S.C_EXACT] == c["counts"][1]
+    assert g["counts"][S.C_FLOPS] == c["counts"][3]
+
+
 @pytest.mark.parametrize("name", list(SCENES))
 def test_stiv_and_gradient(orc, name):
     sc = SCENES[name]()
