@@ -410,4 +410,4 @@ def scene_small(n_side=(2, 1, 1), p: int = 4, seed: int = 7, phi: float = 0.55, 
 C1440_TRANS = 0.20
 C4096_TRANS = 0.06
 C4096_FLOW = 0.25
-C256_TRANS = 0.10
+C256_TRANS = 0.40

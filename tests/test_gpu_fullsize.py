@@ -1,0 +1,72 @@
+"""Parity at the benchmark's full size: the 1440-vesicle 58% lattice workload
+(p = 16 -> 32), run as the benchmark runs it (graph replay of the whole
+step).  The whole candidate-pair list is compared with the oracle's all-pairs
+box test bit for bit; contacts, volumes and gradient rows are compared on a
+sample of vesicle pairs that the oracle recomputes one by one."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1812_04719_gb300 import scenegen as G
+from paper_1812_04719_gb300 import stiv as S
+from tests.gpu_run import gpu_pairs_rows, verts_list
+
+pytestmark = pytest.mark.gpu
+
+
+def bits(x):
+    return np.ascontiguousarray(x, dtype=np.float64).view(np.int64)
+
+
+@pytest.fixture(scope="module", params=[S.STIV_FP64, S.STIV_MIXED], ids=["fp64", "mixed"])
+def full(request):
+    prec = request.param
+    sc = G.scene_1440()
+    eng = S.Stiv.for_scene(sc, precision=prec, pair_cap=8192, contact_cap=1 << 20)
+    ds = S.DeviceScene.from_scene(sc, precision=prec)
+    for _ in range(3):   # capture, then replays
+        r = eng.step(ds, grad=True, use_graph=True)
+    torch.cuda.synchronize()
+    g = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
+    g["verts"] = ds.verts.double().cpu().numpy()
+    return sc, g
+
+
+def test_candidate_pairs_full(orc, full):
+    sc, g = full
+    Xs = verts_list(sc, g["verts"])
+    boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
+    pairs = orc.candidate_pairs(boxes, sc.L)
+    assert len(pairs) > 5000
+    assert np.array_equal(gpu_pairs_rows(g), pairs)
+    assert g["counts"][S.C_STATUS] == 0
+
+
+def test_sampled_pairs_contacts_volumes_gradients(orc, full):
+    sc, g = full
+    Xs = verts_list(sc, g["verts"])
+    rows = gpu_pairs_rows(g)
+    rng = np.random.default_rng(11)
+    hit = np.nonzero(g["V_pair"] > 0)[0]
+    miss = np.nonzero(g["V_pair"] == 0)[0]
+    sample = np.sort(np.concatenate([rng.choice(hit, 24, replace=False), rng.choice(miss, 8, replace=False)]))
+    c = orc.contacts(sc.P, Xs, rows[sample], sc.L, sc.eps * sc.dt, grad=True)
+    n_checked = 0
+    for k, r in enumerate(sample):
+        gm = g["pair"] == r
+        cm = c["pair"] == k
+        for key in ("type", "a", "b"):
+            assert np.array_equal(g[key][gm], c[key][cm]), (r, key)
+        assert np.array_equal(bits(g["tau"][gm]), bits(c["tau"][cm]))
+        assert np.array_equal(bits(g["w"][gm]), bits(c["w"][cm]))
+        assert abs(g["V_pair"][r] - c["V_pair"][k]) <= 1e-10 * abs(c["V_pair"][k])
+        assert np.all(np.abs(g["V"][gm] - c["V"][cm]) <= 1e-10 * np.abs(c["V"][cm]))
+        gr, cr = g["grad"][gm], c["grad"][cm]
+        if len(cr):
+            scale = np.abs(cr).reshape(len(cr), -1).max(axis=1)
+            err = np.abs(gr - cr).reshape(len(cr), -1).max(axis=1)
+            assert np.all(err <= 1e-9 * scale + 1e-300)
+            assert np.array_equal(g["gvid"][gm], c["gvid"][cm])
+            assert np.array_equal(g["gves"][gm], c["gves"][cm])
+        n_checked += int(gm.sum())
+    assert n_checked > 1000
