@@ -241,7 +241,7 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   size_t o_pk2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q);
   size_t o_pv2 = off; off = align_up(off + sizeof(int32_t) * (size_t)w.Q);
   size_t o_wk = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.W);
-  size_t o_fr = off; off = align_up(off + sizeof(float) * 4 * (size_t)cand->capacity);
+  size_t o_fr = off; off = align_up(off + sizeof(stiv_pair_info) * (size_t)cand->capacity);
   size_t o_q3 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q3);
   size_t o_q2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q2);
   size_t o_pc = off; off = align_up(off + sizeof(int32_t) * (size_t)cand->capacity);
@@ -266,7 +266,7 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   w.pkey2 = (uint64_t*)(b + o_pk2); w.pval2 = (int32_t*)(b + o_pv2);
   w.work = (uint64_t*)(b + o_wk);
   w.q3 = (unsigned long long*)(b + o_q3); w.q2 = (unsigned long long*)(b + o_q2);
-  w.frame = (float4*)(b + o_fr);
+  w.pinfo = (stiv_pair_info*)(b + o_fr);
   w.pair_cnt = (int32_t*)(b + o_pc); w.pair_fill = (int32_t*)(b + o_pf); w.pair_off = (int32_t*)(b + o_po);
   w.seg = (unsigned long long*)(b + o_sg); w.seg2 = (unsigned long long*)(b + o_sg2);
   w.tmp_i32 = (int32_t*)(b + o_ti); w.tmp_f64 = (double*)(b + o_tf);

@@ -36,14 +36,27 @@ constexpr int MAXV = 16, MAXT = 32, MAXE = 48;
 constexpr int NW = 8;                                  // warps per CTA
 constexpr int QCAP = 64;                               // queue entries
 
+// Primitives of one patch in terms of its vertex slots.  P is even, so every
+// patch spans exactly STIV_BR bands and STIV_BC columns; the lists depend only
+// on whether the patch touches the north pole (first band), the south pole
+// (last band) and whether it owns the pole vertices (first column block):
+// 8 variants, built once per CTA.
+struct PatchTopo {
+  unsigned char v_slot[MAXV];      // vertices owned by the patch
+  int t_slots[MAXT];               // triangles: 3 slots, 6 bits each
+  short e_slots[MAXE];             // edges: 2 slots, 6 bits each (either order)
+  int nv, nt, ne;
+};
+constexpr int NVAR = 8;
+static_assert(NS <= 32, "one lane per vertex slot");
+static_assert(STIV_BR == 2 && STIV_BC % 2 == 0, "patches tile every even-order grid exactly");
+
 struct PatchSm {
   long long key[6][NS];            // exact swept box of each slot: order keys of lo xyz, hi xyz
   float x[3][NS], d[3][NS];        // FP32: X0 - origin of vesicle i, X1 - X0
   float lo[3][NS], hi[3][NS];      // FP32 conservative swept box of each slot (frame of vesicle i)
   int vid[NS];                     // global vertex id of each slot (-1: unused)
-  unsigned char v_slot[MAXV];
-  int t_slots[MAXT];               // 3 slots, 6 bits each
-  int e_slots[MAXE];               // 2 slots (min vertex id first)
+  const PatchTopo* tp;
   unsigned char vf[MAXV], tf[MAXT], ef[MAXE];
   int nv, nt, ne, nvf, ntf, nef;
   int P, I, J, ves;
@@ -73,7 +86,7 @@ struct narrow_args {
   const float* vorg;
   const float* fprep;
   int64_t fstride;
-  const float4* frame;      // per candidate pair: FP32 offset of vesicle j, position error bound
+  const stiv_pair_info* pinfo;  // per candidate pair: vesicles, orders, offsets, FP32 frame
   unsigned long long* q3;   // stage 3b input: (pair << 32) | (type << 30) | (a << 15) | b
   unsigned long long* q2;   // stage 4 input
   int64_t Q3, Q2;
@@ -103,65 +116,24 @@ __device__ __forceinline__ long long dkey(double v) {
 // ---------------------------------------------------------------------------
 // staging
 // ---------------------------------------------------------------------------
-// Stage patch `patch` of vesicle v; s: periodic image of the vesicle (applied
-// to both time levels in FP64, as the contact test sees it); off: FP32 offset
-// of this vesicle's frame origin from the frame of the pair.
-template <bool MIXED>
-__device__ __noinline__ void load_patch(PatchSm& S, const narrow_args& a, int v, int patch, const int* s, const float* off,
-                           float dx, int lane) {
-  int P = 2 * a.pv[v], W = 2 * P, nv = stiv_nverts(P);
-  int nbr = stiv_nband_blocks(P), nbc = stiv_ncol_blocks(P);
-  int I = patch / nbc, J = patch % nbc;
-  int r0 = I * STIV_BR, rq = min(STIV_BR, P - r0), c0 = J * STIV_BC, ncol = min(STIV_BC, W - c0);
-  bool first = I == 0, last = I == nbr - 1;
-  size_t base = a.voff[v];
-  const float* fp = a.fprep + (size_t)v * a.fstride;
-  double sh[3] = {s[0] * a.L[0], s[1] * a.L[1], s[2] * a.L[2]};
-  for (int k = lane; k < NS; k += 32) {
-    int vid = -1;
-    if (k < SN) {
-      int rr = k / (STIV_BC + 1), cc = k % (STIV_BC + 1);
-      if (rr <= rq && cc <= ncol) { int col = c0 + cc; if (col >= W) col -= W; vid = (r0 + rr) * W + col; }
-    } else if (k == SN && first) vid = W * (P + 1);
-    else if (k == SS && last) vid = W * (P + 1) + 1;
-    S.vid[k] = vid;
-    if (vid >= 0) {
-      for (int c = 0; c < 3; ++c) {
-        size_t i0 = base + (size_t)c * nv + vid, i1 = base + (size_t)(3 + c) * nv + vid;
-        double x0 = vtx<MIXED>(a.X, i0);
-        double x1 = vtx<MIXED>(a.X, i1);
-        if (s[c] != 0) { x0 = x0 + sh[c]; x1 = x1 + sh[c]; }
-        long long k0 = dkey(x0), k1 = dkey(x1);
-        S.key[c][k] = k0 < k1 ? k0 : k1;
-        S.key[3 + c][k] = k0 < k1 ? k1 : k0;
-        float xf = fp[(size_t)c * nv + vid] + off[c];
-        float df = fp[(size_t)(3 + c) * nv + vid];
-        S.x[c][k] = xf;
-        S.d[c][k] = df;
-        float m = dx + 4.7683716e-7f * (fabsf(xf) + fabsf(df));  // 2^-21 (|x| + |d|)
-        S.lo[c][k] = fminf(xf, xf + df) - m;
-        S.hi[c][k] = fmaxf(xf, xf + df) + m;
-      }
-    } else {
-      for (int c = 0; c < 3; ++c) { S.lo[c][k] = INFINITY; S.hi[c][k] = -INFINITY; }
-    }
-  }
-  __syncwarp();
+// Topology variant var = first | last << 1 | pole-owner << 2 (see PatchTopo),
+// built by one warp.
+__device__ void build_topo(PatchTopo& T, int var, int lane) {
+  const int rq = STIV_BR, ncol = STIV_BC;
+  bool first = var & 1, last = (var >> 1) & 1, j0 = (var >> 2) & 1;
   int rown = rq + (last ? 1 : 0);
   int nvg = rown * ncol;
-  int npole = (first && J == 0 ? 1 : 0) + (last && J == 0 ? 1 : 0);
+  int npole = (first && j0 ? 1 : 0) + (last && j0 ? 1 : 0);
   int ntq = 2 * rq * ncol;
   int nfan = (first ? ncol : 0) + (last ? ncol : 0);
-  if (lane == 0) {
-    S.nv = nvg + npole; S.nt = ntq + nfan; S.ne = rown * ncol + 2 * rq * ncol + nfan;
-    S.P = P; S.I = I; S.J = J; S.ves = v;
-  }
+  int ne = rown * ncol + 2 * rq * ncol + nfan;
+  if (lane == 0) { T.nv = nvg + npole; T.nt = ntq + nfan; T.ne = ne; }
   for (int k = lane; k < nvg + npole; k += 32) {
     int slot;
     if (k < nvg) slot = slot_of(k / ncol, k % ncol);
-    else if (first && J == 0 && k == nvg) slot = SN;
+    else if (first && j0 && k == nvg) slot = SN;
     else slot = SS;
-    S.v_slot[k] = (unsigned char)slot;
+    T.v_slot[k] = (unsigned char)slot;
   }
   for (int k = lane; k < ntq + nfan; k += 32) {
     int s0, s1, s2;
@@ -174,9 +146,9 @@ __device__ __noinline__ void load_patch(PatchSm& S, const narrow_args& a, int v,
       if (first && k2 < ncol) { s0 = SN; s1 = slot_of(0, k2); s2 = slot_of(0, k2 + 1); }
       else { int cc = first ? k2 - ncol : k2; s0 = SS; s1 = slot_of(rq, cc + 1); s2 = slot_of(rq, cc); }
     }
-    S.t_slots[k] = s0 | (s1 << 6) | (s2 << 12);
+    T.t_slots[k] = s0 | (s1 << 6) | (s2 << 12);
   }
-  for (int k = lane; k < rown * ncol + 2 * rq * ncol + nfan; k += 32) {
+  for (int k = lane; k < ne; k += 32) {
     int sa, sb;
     int nh = rown * ncol;
     if (k < nh) {
@@ -191,15 +163,105 @@ __device__ __noinline__ void load_patch(PatchSm& S, const narrow_args& a, int v,
       if (first && k2 < ncol) { sa = slot_of(0, k2); sb = SN; }
       else { int cc = first ? k2 - ncol : k2; sa = slot_of(rq, cc); sb = SS; }
     }
-    if (S.vid[sb] < S.vid[sa]) { int t = sa; sa = sb; sb = t; }
-    S.e_slots[k] = sa | (sb << 6);
+    T.e_slots[k] = (short)(sa | (sb << 6));
   }
-  __syncwarp();
-  if (lane < 6) {
-    float acc = lane < 3 ? INFINITY : -INFINITY;
-    int c = lane % 3;
-    for (int k = 0; k < NS; ++k) acc = lane < 3 ? fminf(acc, S.lo[c][k]) : fmaxf(acc, S.hi[c][k]);
-    S.box[lane] = acc;
+}
+
+// Global vertex id of slot k of the patch starting at grid row r0, column c0.
+__device__ __forceinline__ int slot_vid(int k, int r0, int c0, int W, int P, bool first, bool last) {
+  if (k < SN) {
+    int rr = k / (STIV_BC + 1), cc = k % (STIV_BC + 1), col = c0 + cc;
+    if (col >= W) col -= W;
+    return (r0 + rr) * W + col;
+  }
+  if (k == SN) return first ? W * (P + 1) : -1;
+  return last ? W * (P + 1) + 1 : -1;
+}
+
+// One vertex slot: exact FP64 swept-box keys, FP32 frame coordinates and the
+// slot's conservative FP32 swept box (also returned in b).  s: periodic image
+// of the vesicle (applied to both time levels in FP64, as the contact test
+// sees it); off: FP32 offset of the vesicle's frame origin in the pair frame.
+template <bool MIXED>
+__device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int64_t base, const float* fp, int nv,
+                                           int vid, int k, const int* s, const double* sh, const float* off, float dx,
+                                           float* b) {
+  int v = vid >= 0 ? vid : 0;
+  S.vid[k] = vid;
+  double x0[3], x1[3];
+  float xf[3], df[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    x0[c] = vtx<MIXED>(a.X, (size_t)base + (size_t)c * nv + v);
+    x1[c] = vtx<MIXED>(a.X, (size_t)base + (size_t)(3 + c) * nv + v);
+    xf[c] = fp[(size_t)c * nv + v];
+    df[c] = fp[(size_t)(3 + c) * nv + v];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double p0 = x0[c], p1 = x1[c];
+    if (s[c] != 0) { p0 = p0 + sh[c]; p1 = p1 + sh[c]; }
+    long long k0 = dkey(p0), k1 = dkey(p1);
+    S.key[c][k] = k0 < k1 ? k0 : k1;
+    S.key[3 + c][k] = k0 < k1 ? k1 : k0;
+    float x = xf[c] + off[c], d = df[c];
+    S.x[c][k] = x;
+    S.d[c][k] = d;
+    float m = dx + 4.7683716e-7f * (fabsf(x) + fabsf(d));  // 2^-21 (|x| + |d|)
+    float lo = vid >= 0 ? fminf(x, x + d) - m : INFINITY;
+    float hi = vid >= 0 ? fmaxf(x, x + d) + m : -INFINITY;
+    S.lo[c][k] = lo;
+    S.hi[c][k] = hi;
+    b[c] = lo;
+    b[3 + c] = hi;
+  }
+}
+
+// Stage the two patches of a patch pair (A: patch pa of vesicle i, unshifted;
+// B: patch pb of vesicle j at its periodic image), lanes over slots, both
+// patches' loads in flight together; patch boxes by warp reduction.
+template <bool MIXED>
+__device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const PatchTopo* topo,
+                                        const stiv_pair_info& pi, int pa, int pb, int lane) {
+  int vi = pi.vi, vj = pi.vj, code = pi.code;
+  int s0[3] = {0, 0, 0};
+  int s1[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
+  double sh0[3] = {0.0, 0.0, 0.0};
+  double sh1[3] = {s1[0] * a.L[0], s1[1] * a.L[1], s1[2] * a.L[2]};
+  float offA[3] = {0.f, 0.f, 0.f}, offB[3] = {pi.frame.x, pi.frame.y, pi.frame.z};
+  float dx = pi.frame.w;
+  int PA = pi.Pij & 0xFFFF, PB = pi.Pij >> 16;
+  int WA = 2 * PA, WB = 2 * PB, nvA = stiv_nverts(PA), nvB = stiv_nverts(PB);
+  int nbcA = stiv_ncol_blocks(PA), nbcB = stiv_ncol_blocks(PB);
+  int IA = pa / nbcA, JA = pa % nbcA, IB = pb / nbcB, JB = pb % nbcB;
+  bool fA = IA == 0, lA = IA == stiv_nband_blocks(PA) - 1, fB = IB == 0, lB = IB == stiv_nband_blocks(PB) - 1;
+  float bA[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  float bB[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  if (lane < NS) {
+    int vidA = slot_vid(lane, IA * STIV_BR, JA * STIV_BC, WA, PA, fA, lA);
+    int vidB = slot_vid(lane, IB * STIV_BR, JB * STIV_BC, WB, PB, fB, lB);
+    stage_slot<MIXED>(ws.A, a, pi.voff_i, a.fprep + (size_t)vi * a.fstride, nvA, vidA, lane, s0, sh0, offA, dx, bA);
+    stage_slot<MIXED>(ws.B, a, pi.voff_j, a.fprep + (size_t)vj * a.fstride, nvB, vidB, lane, s1, sh1, offB, dx, bB);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      bA[c] = fminf(bA[c], __shfl_xor_sync(0xffffffffu, bA[c], off));
+      bA[3 + c] = fmaxf(bA[3 + c], __shfl_xor_sync(0xffffffffu, bA[3 + c], off));
+      bB[c] = fminf(bB[c], __shfl_xor_sync(0xffffffffu, bB[c], off));
+      bB[3 + c] = fmaxf(bB[3 + c], __shfl_xor_sync(0xffffffffu, bB[3 + c], off));
+    }
+  }
+  if (lane < 6) { ws.A.box[lane] = bA[lane]; ws.B.box[lane] = bB[lane]; }
+  if (lane == 0) {
+    const PatchTopo* tA = topo + ((fA ? 1 : 0) | (lA ? 2 : 0) | (JA == 0 ? 4 : 0));
+    const PatchTopo* tB = topo + ((fB ? 1 : 0) | (lB ? 2 : 0) | (JB == 0 ? 4 : 0));
+    ws.A.tp = tA; ws.A.nv = tA->nv; ws.A.nt = tA->nt; ws.A.ne = tA->ne;
+    ws.A.P = PA; ws.A.I = IA; ws.A.J = JA; ws.A.ves = vi;
+    ws.B.tp = tB; ws.B.nv = tB->nv; ws.B.nt = tB->nt; ws.B.ne = tB->ne;
+    ws.B.P = PB; ws.B.I = IB; ws.B.J = JB; ws.B.ves = vj;
+    ws.dx = dx;
   }
   __syncwarp();
 }
@@ -207,9 +269,10 @@ __device__ __noinline__ void load_patch(PatchSm& S, const narrow_args& a, int v,
 // Global id of primitive k of a staged patch (vertex id, triangle id, or edge index).
 __device__ int prim_gid(const PatchSm& S, int kind, int k) {
   int P = S.P, W = 2 * P;
-  int r0 = S.I * STIV_BR, rq = min(STIV_BR, P - r0), c0 = S.J * STIV_BC, ncol = min(STIV_BC, W - c0);
+  const int rq = STIV_BR, ncol = STIV_BC;
+  int r0 = S.I * STIV_BR, c0 = S.J * STIV_BC;
   bool first = S.I == 0;
-  if (kind == 0) return S.vid[S.v_slot[k]];
+  if (kind == 0) return S.vid[S.tp->v_slot[k]];
   if (kind == 1) {
     int ntq = 2 * rq * ncol;
     if (k < ntq) { int q = k >> 1, rr = q / ncol, cc = q % ncol; return 2 * ((r0 + rr) * W + c0 + cc) + (k & 1); }
@@ -217,8 +280,9 @@ __device__ int prim_gid(const PatchSm& S, int kind, int k) {
     if (first && k2 < ncol) return 4 * P * P + c0 + k2;
     return 4 * P * P + W + c0 + (first ? k2 - ncol : k2);
   }
-  int e = S.e_slots[k];
-  return stiv_edge_index(P, S.vid[e & 63], S.vid[(e >> 6) & 63]);
+  int e = S.tp->e_slots[k];
+  int u = S.vid[e & 63], v = S.vid[(e >> 6) & 63];
+  return stiv_edge_index(P, min(u, v), max(u, v));
 }
 
 __device__ __forceinline__ void slot_box(const PatchSm& S, int sl, float* b) {
@@ -230,11 +294,11 @@ __device__ __forceinline__ void merge_box(const PatchSm& S, int sl, float* b) {
   b[3] = fmaxf(b[3], S.hi[0][sl]); b[4] = fmaxf(b[4], S.hi[1][sl]); b[5] = fmaxf(b[5], S.hi[2][sl]);
 }
 __device__ __forceinline__ void tri_box(const PatchSm& S, int k, float* b) {
-  int t = S.t_slots[k];
+  int t = S.tp->t_slots[k];
   slot_box(S, t & 63, b); merge_box(S, (t >> 6) & 63, b); merge_box(S, (t >> 12) & 63, b);
 }
 __device__ __forceinline__ void edge_box(const PatchSm& S, int k, float* b) {
-  int e = S.e_slots[k];
+  int e = S.tp->e_slots[k];
   slot_box(S, e & 63, b); merge_box(S, (e >> 6) & 63, b);
 }
 __device__ __forceinline__ bool fbox_hit(const float* a, const float* b) {
@@ -253,7 +317,7 @@ __device__ void filter_patch(PatchSm& S, const float* ob, int lane) {
       bool hit = false;
       if (k < n) {
         float b[6];
-        if (kind == 0) slot_box(S, S.v_slot[k], b);
+        if (kind == 0) slot_box(S, S.tp->v_slot[k], b);
         else if (kind == 1) tri_box(S, k, b);
         else edge_box(S, k, b);
         hit = fbox_hit(b, ob);
@@ -423,23 +487,94 @@ __device__ __forceinline__ bool is_neg(double v) {  // v < 0.0
 }
 __device__ __forceinline__ bool is_pos(double v) { return __double_as_longlong(v) > 0; }  // v > 0.0, v not NaN
 
+// (lo + hi) * 0.5 rounded as FP64 does it (nearest, ties to even), for
+// 0 <= lo < hi, computed on the integer pipe: add the 53-bit significands
+// with guard, round and sticky bits, round, halve the exponent.  ok = false
+// when the operands or the result leave the normal range; the caller then
+// uses the FP64 instructions.
+__device__ __forceinline__ double mid_rn(double lo, double hi, bool& ok) {
+  const unsigned long long FR = (1ull << 52) - 1, HID = 1ull << 52;
+  unsigned long long a = (unsigned long long)__double_as_longlong(lo), b = (unsigned long long)__double_as_longlong(hi);
+  int eb = (int)(b >> 52);
+  ok = true;
+  if (a == 0) {                                 // lo = 0: the sum is hi
+    if (eb < 2) { ok = false; return 0.0; }
+    return __longlong_as_double((long long)(b - HID));
+  }
+  int ea = (int)(a >> 52);
+  if (ea == 0) { ok = false; return 0.0; }
+  unsigned long long ma = (a & FR) | HID, mb = (b & FR) | HID;
+  int d = eb - ea;                              // >= 0 because lo < hi
+  unsigned long long M = mb << 3;
+  if (d < 56) {
+    unsigned long long sa = ma << 3, sh = sa >> d;
+    M += sh | (unsigned long long)((sh << d) != sa);
+  } else {
+    M += 1;                                     // lo only sets the sticky bit
+  }
+  int e = eb;
+  if (M >> 56) { M = (M >> 1) | (M & 1); ++e; }
+  unsigned low = (unsigned)(M & 7);
+  M >>= 3;
+  if (low > 4 || (low == 4 && (M & 1))) ++M;
+  if (M >> 53) { M >>= 1; ++e; }
+  if (e < 2 || e > 2046) { ok = false; return 0.0; }
+  return __longlong_as_double((long long)(((unsigned long long)(e - 1) << 52) | (M & FR)));
+}
+
+// FP32 image of t in [0, 1] by truncating the significand: |t - m| <= 2^-23 t
+// (m = 0 below 2^-126, where |t - m| <= 2^-126).
+__device__ __forceinline__ float trunc_f32(double t) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(t);
+  int e = (int)(b >> 52) - 1023 + 127;
+  if (e < 1) return 0.0f;
+  return __uint_as_float(((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7FFFFF));
+}
+
 // FP64 operations of the procedure, counted as executed (+ - * / sqrt = 1,
 // fma = 2, negations and comparisons 0): the algorithmic work of the exact
 // contact test, reported for the roofline.
+//
+// The bisection takes exactly the FP64 path: every midpoint is the FP64
+// midpoint (mid_rn), and every sign is the sign of the FP64 Horner value.
+// That sign is read from an FP32 Horner evaluation when its error bound
+// proves it:  |f64(mid) - f32| <= gamma_6(2^-53) S + 2^-24 S + gamma_6(2^-24) S
+// (1 + 2^-24) + 2^-23 S1 <= 4.2e-7 S + 1.2e-7 S1, with S = sum |k_i| and S1 =
+// |k1| + 2|k2| + 3|k3| (t in [0, 1]; Horner error bounds, coefficient
+// rounding, and the truncation of the midpoint times max |f'|).  When
+// |f32| > E the FP64 value has the same sign and is not zero; otherwise the
+// FP64 Horner value is computed.  Coefficients outside [1e-25, 1e25] keep
+// every FP32 term far from underflow and overflow, else only FP64 is used.
 __device__ double bisect64(double k0, double k1, double k2, double k3, double lo, double hi, double flo,
                            long long& flops) {
   bool neg_lo = is_neg(flo);
+  float f0 = __double2float_rn(k0), f1 = __double2float_rn(k1), f2 = __double2float_rn(k2),
+        f3 = __double2float_rn(k3);
+  float a0 = fabsf(f0), a1 = fabsf(f1), a2 = fabsf(f2), a3 = fabsf(f3);
+  float mk = fmaxf(fmaxf(a0, a1), fmaxf(a2, a3));
+  float E = 1.01f * (4.5e-7f * (((a0 + a1) + a2) + a3) + 1.25e-7f * ((a1 + 2.0f * a2) + 3.0f * a3));
+  if (!(mk > 1e-25f && mk < 1e25f)) E = INFINITY;
 #pragma unroll 1
   for (int it = 0; it < 64; ++it) {
-    double mid = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+    bool ok;
+    double mid = mid_rn(lo, hi, ok);
+    if (!ok) mid = __dmul_rn(__dadd_rn(lo, hi), 0.5);
     flops += 2;
     // lo, mid, hi are non-negative: compare bit patterns
     long long bm = __double_as_longlong(mid);
     if (!(bm > __double_as_longlong(lo) && bm < __double_as_longlong(hi))) break;
     flops += 6;
-    double fm = horner3(k0, k1, k2, k3, mid);
-    if (is_zero(fm)) return mid;
-    if (is_neg(fm) == neg_lo) lo = mid;
+    float m = trunc_f32(mid);
+    float fs = fmaf(fmaf(fmaf(f3, m, f2), m, f1), m, f0);
+    bool neg;
+    if (fabsf(fs) > E) {
+      neg = fs < 0.0f;
+    } else {
+      double fm = horner3(k0, k1, k2, k3, mid);
+      if (is_zero(fm)) return mid;
+      neg = is_neg(fm);
+    }
+    if (neg == neg_lo) lo = mid;
     else hi = mid;
   }
   return lo;
@@ -550,11 +685,11 @@ __device__ __forceinline__ void entry_slots(const WarpSm& ws, unsigned e, int& k
   SA = (kind == 1) ? &ws.B : &ws.A;   // side holding the first primitive (vertex / edge)
   SB = (kind == 1) ? &ws.A : &ws.B;
   if (kind < 2) {
-    sl[0] = SA->v_slot[x];
-    int t = SB->t_slots[y];
+    sl[0] = SA->tp->v_slot[x];
+    int t = SB->tp->t_slots[y];
     sl[1] = t & 63; sl[2] = (t >> 6) & 63; sl[3] = (t >> 12) & 63;
   } else {
-    int ea = SA->e_slots[x], eb = SB->e_slots[y];
+    int ea = SA->tp->e_slots[x], eb = SB->tp->e_slots[y];
     sl[0] = ea & 63; sl[1] = (ea >> 6) & 63; sl[2] = eb & 63; sl[3] = (eb >> 6) & 63;
   }
 }
@@ -596,7 +731,7 @@ __device__ __forceinline__ void desc_points(const narrow_args& a, unsigned long 
 // (with its periodic image) and the bound on the FP32 position error, computed
 // once per candidate pair by patch_pairs_kernel.
 __device__ __forceinline__ float pair_frame(const narrow_args& a, int r, float* offB) {
-  float4 f = a.frame[r];
+  float4 f = a.pinfo[r].frame;
   offB[0] = f.x; offB[1] = f.y; offB[2] = f.z;
   return f.w;
 }
@@ -703,28 +838,27 @@ __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, in
 
 // Stages 1-3a: one warp per patch pair.
 template <bool MIXED>
-__global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
+__global__ void __launch_bounds__(NW * 32, 3) narrow_kernel(narrow_args a) {
   extern __shared__ unsigned char smraw[];
+  __shared__ PatchTopo topo[NVAR];
   WarpSm& ws = ((WarpSm*)smraw)[threadIdx.x >> 5];
   int lane = threadIdx.x & 31;
+  for (int var = threadIdx.x >> 5; var < NVAR; var += NW) build_topo(topo[var], var, lane);
+  __syncthreads();
   int64_t nwork = a.ctr[STIV_C_PATCH];
   if (nwork > a.W) nwork = a.W;
   long long nprim = 0;
-  while (true) {
-    long long item = 0;
-    if (lane == 0) item = (long long)atomicAdd((unsigned long long*)&a.ctr[10], 1ull);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= nwork) break;
+  long long item = 0;
+  if (lane == 0) item = (long long)atomicAdd((unsigned long long*)&a.ctr[10], 1ull);
+  item = __shfl_sync(0xffffffffu, item, 0);
+  while (item < nwork) {
+    // the next item's index is fetched now and read at the end of this one
+    long long next = 0;
+    if (lane == 0) next = (long long)atomicAdd((unsigned long long*)&a.ctr[10], 1ull);
     uint64_t w = a.work[item];
     int r = (int)(w >> 32), pa = (int)((w >> 16) & 0xFFFF), pb = (int)(w & 0xFFFF);
-    int vi = a.ci[r], vj = a.cj[r], code = a.cs[r];
-    int s0[3] = {0, 0, 0};
-    int s1[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
-    float offA[3] = {0.f, 0.f, 0.f}, offB[3];
-    float dx = pair_frame(a, r, offB);
-    if (lane == 0) ws.dx = dx;
-    load_patch<MIXED>(ws.A, a, vi, pa, s0, offA, dx, lane);
-    load_patch<MIXED>(ws.B, a, vj, pb, s1, offB, dx, lane);
+    stiv_pair_info pi = a.pinfo[r];
+    stage_pair<MIXED>(ws, a, topo, pi, pa, pb, lane);
     filter_patch(ws.A, ws.B.box, lane);
     filter_patch(ws.B, ws.A.box, lane);
     if (lane == 0) ws.n1 = 0;
@@ -744,7 +878,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
         for (int xk = 0; xk < V.nvf; ++xk) {
           int x = V.vf[xk];
           float vb[6];
-          slot_box(V, V.v_slot[x], vb);
+          slot_box(V, V.tp->v_slot[x], vb);
           bool hit = valid && fbox_hit(vb, tb);
           enqueue(ws, hit, ((unsigned)dir << 16) | ((unsigned)x << 8) | (unsigned)y, lane, r, a, nprim);
         }
@@ -769,6 +903,7 @@ __global__ void __launch_bounds__(NW * 32) narrow_kernel(narrow_args a) {
     }
     int n1 = ws.n1;
     if (n1 > 0) stage_filter(ws, n1, lane, r, a, nprim);
+    item = __shfl_sync(0xffffffffu, next, 0);
   }
   for (int off = 16; off > 0; off >>= 1) nprim += __shfl_down_sync(0xffffffffu, nprim, off);
   if (lane == 0 && nprim) atomicAdd((unsigned long long*)&a.ctr[STIV_C_PRIM], (unsigned long long)nprim);
@@ -948,7 +1083,11 @@ __global__ void __launch_bounds__(128) fp64_kernel(narrow_args a) {
           a.rc_pair[k] = r; a.rc_type[k] = type; a.rc_a[k] = ga; a.rc_b[k] = gb;
           a.rc_tau[k] = tau; a.rc_w[2 * k] = w1; a.rc_w[2 * k + 1] = w2;
         }
-        atomicAdd((unsigned long long*)&a.ctr[type == 2 ? STIV_C_EE : STIV_C_VF], 1ull);
+      }
+      unsigned mee = __ballot_sync(0xffffffffu, type == 2);
+      if (lane == leader) {
+        if (mee) atomicAdd((unsigned long long*)&a.ctr[STIV_C_EE], (unsigned long long)__popc(mee));
+        if (m & ~mee) atomicAdd((unsigned long long*)&a.ctr[STIV_C_VF], (unsigned long long)__popc(m & ~mee));
       }
     }
   }
@@ -970,7 +1109,8 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
                                                           double Lx, double Ly, double Lz, const int32_t* ci,
                                                           const int32_t* cj, const int32_t* cs, int64_t cap,
                                                           int64_t W, uint64_t* work, int64_t* ctr, int mp,
-                                                          const float* vorg, float4* frame) {
+                                                          const float* vorg, const int64_t* voff,
+                                                          stiv_pair_info* pinfo) {
   extern __shared__ float psm[];
   int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* sbw = psm + (size_t)wid * 2 * mp * 6;                       // [2][mp][6]
@@ -993,7 +1133,11 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
         o[c] = (float)d;
         dmax = fmaxf(dmax, fabsf(o[c]));
       }
-      frame[r] = make_float4(o[0], o[1], o[2], 2.3841858e-7f * (vorg[4 * i + 3] + vorg[4 * j + 3] + 2.0f * dmax));
+      stiv_pair_info p;
+      p.frame = make_float4(o[0], o[1], o[2], 2.3841858e-7f * (vorg[4 * i + 3] + vorg[4 * j + 3] + 2.0f * dmax));
+      p.vi = i; p.vj = j; p.code = code; p.Pij = Pi | (Pj << 16);
+      p.voff_i = voff[i]; p.voff_j = voff[j];
+      pinfo[r] = p;
     }
     int ni = stiv_npatches(Pi), nj = stiv_npatches(Pj);
     float shlo[3], shhi[3];
@@ -1072,13 +1216,13 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
     STIV_PROF(h, st, "patch_pairs");
     patch_pairs_kernel<<<blocks, 128, psmem, st>>>(p_dev, w.vbox, w.pbox, L[0], L[1], L[2], cand->i, cand->j,
                                                    cand->shift, cand->capacity, w.W, w.work, w.ctr, mp, w.vorg,
-                                                   w.frame);
+                                                   voff, w.pinfo);
   }
   STIV_LAUNCH(h);
   narrow_args a;
   bool mixed = h->prm.precision == STIV_MIXED;
   a.pv = p_dev; a.voff = voff; a.X = X; a.mixed = mixed;
-  a.frame = w.frame;
+  a.pinfo = w.pinfo;
   a.L[0] = L[0]; a.L[1] = L[1]; a.L[2] = L[2];
   a.ci = cand->i; a.cj = cand->j; a.cs = cand->shift;
   a.work = w.work; a.W = w.W; a.include_ee = h->prm.include_ee; a.exact_only = w.exact_only;

@@ -61,6 +61,16 @@ struct stiv_prof_scope {
 // kernels launched by one radix sort of key_bits bits (histogram, scan, scatter per 8-bit digit)
 inline int stiv_sort_kernels(int key_bits) { return 3 * ((key_bits + 7) / 8); }
 
+// Per candidate vesicle pair, written by the narrow phase's first kernel:
+// FP32 frame (offset of vesicle j's origin with its periodic image from
+// vesicle i's origin, bound on the FP32 position error), the two vesicles,
+// the shift code, the two mesh orders (P_i | P_j << 16), vertex offsets.
+struct __align__(16) stiv_pair_info {
+  float4 frame;
+  int32_t vi, vj, code, Pij;
+  long long voff_i, voff_j;
+};
+
 // Scratch layout used by stiv_detect (byte offsets into handle->ws).
 struct detect_ws {
   double* vbox;          // [N][6]
@@ -83,7 +93,7 @@ struct detect_ws {
   uint64_t* pkey2;       // [Q]
   int32_t* pval2;        // [Q]
   uint64_t* work;        // [W]  patch-pair work items
-  float4* frame;         // [pair capacity]  FP32 frame of each candidate pair
+  stiv_pair_info* pinfo; // [pair capacity]
   unsigned long long* q3;  // [Q3] primitive pairs left for the FP32 piece tests
   unsigned long long* q2;  // [Q2] primitive pairs left for the FP64 contact test
   int64_t Q3, Q2;
