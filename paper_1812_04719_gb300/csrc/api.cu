@@ -224,7 +224,7 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   size_t o_vbox = off; off = align_up(off + sizeof(double) * 6 * (size_t)n);
   w.pstride = stiv_npatches(2 * p_max);
   size_t o_pbox = off; off = align_up(off + sizeof(float) * 6 * (size_t)w.pstride * n);
-  w.fstride = 6 * (int64_t)stiv_nverts(2 * p_max);
+  w.fstride = 8 * (int64_t)stiv_nverts(2 * p_max);
   size_t o_vorg = off; off = align_up(off + sizeof(float) * 4 * (size_t)n);
   size_t o_fprep = off; off = align_up(off + sizeof(float) * (size_t)w.fstride * n);
   size_t o_grid = off; off = align_up(off + sizeof(double) * 16);
@@ -242,8 +242,8 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   size_t o_pv2 = off; off = align_up(off + sizeof(int32_t) * (size_t)w.Q);
   size_t o_wk = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.W);
   size_t o_fr = off; off = align_up(off + sizeof(stiv_pair_info) * (size_t)cand->capacity);
-  size_t o_q3 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q3);
-  size_t o_q2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.Q2);
+  size_t o_q3 = off; off = align_up(off + sizeof(ulonglong2) * (size_t)w.Q3);
+  size_t o_q2 = off; off = align_up(off + sizeof(ulonglong2) * (size_t)w.Q2);
   size_t o_pc = off; off = align_up(off + sizeof(int32_t) * (size_t)cand->capacity);
   size_t o_pf = off; off = align_up(off + sizeof(int32_t) * (size_t)cand->capacity);
   size_t o_po = off; off = align_up(off + sizeof(int32_t) * (size_t)(cand->capacity + 1));
@@ -265,7 +265,7 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   w.pkey = (uint64_t*)(b + o_pk); w.pval = (int32_t*)(b + o_pv);
   w.pkey2 = (uint64_t*)(b + o_pk2); w.pval2 = (int32_t*)(b + o_pv2);
   w.work = (uint64_t*)(b + o_wk);
-  w.q3 = (unsigned long long*)(b + o_q3); w.q2 = (unsigned long long*)(b + o_q2);
+  w.q3 = (ulonglong2*)(b + o_q3); w.q2 = (ulonglong2*)(b + o_q2);
   w.pinfo = (stiv_pair_info*)(b + o_fr);
   w.pair_cnt = (int32_t*)(b + o_pc); w.pair_fill = (int32_t*)(b + o_pf); w.pair_off = (int32_t*)(b + o_po);
   w.seg = (unsigned long long*)(b + o_sg); w.seg2 = (unsigned long long*)(b + o_sg2);

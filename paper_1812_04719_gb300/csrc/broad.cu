@@ -77,14 +77,20 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
     for (int c = 0; c < 3; ++c) R = fmax(R, fmax(red[3 + c][0] - (double)sorg[c], (double)sorg[c] - red[c][0]));
     vorg[4 * v + 3] = __double2float_ru(R);
   }
-  // per-vertex FP32 data: position at t_n relative to the origin, displacement X1 - X0
-  for (int k = threadIdx.x; k < nv; k += blockDim.x)
+  // per-vertex FP32 data (two float4): position at t_n relative to the
+  // origin, displacement X1 - X0
+  float4* f4 = (float4*)(fprep + (size_t)v * fstride);
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    float xo[3], dd[3];
     for (int c = 0; c < 3; ++c) {
       double x0 = vload(X, mixed, base + (size_t)c * nv + k);
       double x1 = vload(X, mixed, base + (size_t)(3 + c) * nv + k);
-      fprep[(size_t)v * fstride + (size_t)c * nv + k] = (float)(x0 - (double)sorg[c]);
-      fprep[(size_t)v * fstride + (size_t)(3 + c) * nv + k] = (float)(x1 - x0);
+      xo[c] = (float)(x0 - (double)sorg[c]);
+      dd[c] = (float)(x1 - x0);
     }
+    f4[2 * k] = make_float4(xo[0], xo[1], xo[2], 0.f);
+    f4[2 * k + 1] = make_float4(dd[0], dd[1], dd[2], 0.f);
+  }
   // patch boxes: vertex rows [I*BR, min(I*BR+BR, P)], columns [J*BC, J*BC+ncol] (wrapping), poles
   int nbr = stiv_nband_blocks(P), nbc = stiv_ncol_blocks(P), W = 2 * P;
   for (int patch = threadIdx.x; patch < nbr * nbc; patch += blockDim.x) {

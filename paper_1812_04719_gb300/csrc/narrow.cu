@@ -87,8 +87,11 @@ struct narrow_args {
   const float* fprep;
   int64_t fstride;
   const stiv_pair_info* pinfo;  // per candidate pair: vesicles, orders, offsets, FP32 frame
-  unsigned long long* q3;   // stage 3b input: (pair << 32) | (type << 30) | (a << 15) | b
-  unsigned long long* q2;   // stage 4 input
+  // descriptors of primitive pairs: x = pair << 32 | type << 30 | a << 15 | b
+  // (primitive ids), y = the 4 vertex ids, 16 bits each, in the order the
+  // contact test takes its points (VF: vertex, triangle; EE: p0 < p1, q0 < q1)
+  ulonglong2* q3;           // stage 3b input
+  ulonglong2* q2;           // stage 4 input
   int64_t Q3, Q2;
   int64_t C;  // raw contact capacity
   int32_t* rc_pair; int32_t* rc_type; int32_t* rc_a; int32_t* rc_b;
@@ -189,14 +192,13 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
   int v = vid >= 0 ? vid : 0;
   S.vid[k] = vid;
   double x0[3], x1[3];
-  float xf[3], df[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     x0[c] = vtx<MIXED>(a.X, (size_t)base + (size_t)c * nv + v);
     x1[c] = vtx<MIXED>(a.X, (size_t)base + (size_t)(3 + c) * nv + v);
-    xf[c] = fp[(size_t)c * nv + v];
-    df[c] = fp[(size_t)(3 + c) * nv + v];
   }
+  float4 fx = ((const float4*)fp)[2 * v], fd = ((const float4*)fp)[2 * v + 1];
+  float xf[3] = {fx.x, fx.y, fx.z}, df[3] = {fd.x, fd.y, fd.z};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     double p0 = x0[c], p1 = x1[c];
@@ -341,7 +343,13 @@ __device__ __forceinline__ f3 fcross(f3 u, f3 v) {
   return {fmaf(u.y, v.z, -(u.z * v.y)), fmaf(u.z, v.x, -(u.x * v.z)), fmaf(u.x, v.y, -(u.y * v.x))};
 }
 __device__ __forceinline__ float fdot(f3 u, f3 v) { return fmaf(u.z, v.z, fmaf(u.y, v.y, u.x * v.x)); }
-__device__ __forceinline__ float fnorm(f3 u) { return sqrtf(fdot(u, u)); }
+// Upper bound of the Euclidean norm: s * rsqrtf(s) with rsqrtf's maximum
+// error of 2 ulp (2^-22 relative) widened by 2^-20; the rounding of s itself
+// is covered by the margins of the callers.
+__device__ __forceinline__ float fnorm(f3 u) {
+  float s = fdot(u, u);
+  return s > 1e-30f ? s * rsqrtf(s) * 1.000001f : 1e-15f;
+}
 __device__ __forceinline__ f3 fat(f3 x, float t, f3 d) { return {fmaf(t, d.x, x.x), fmaf(t, d.y, x.y), fmaf(t, d.z, x.z)}; }
 __device__ __forceinline__ float amax3(f3 u) { return fmaxf(fabsf(u.x), fmaxf(fabsf(u.y), fabsf(u.z))); }
 
@@ -706,57 +714,41 @@ __device__ __forceinline__ unsigned long long make_desc(int r, int type, int ga,
          (unsigned long long)gb;
 }
 
-// The 4 points of a descriptor: vesicle, vertex id, and whether the point
-// belongs to vesicle j (periodic image applied).
-__device__ __forceinline__ void desc_points(const narrow_args& a, unsigned long long e, int& r, int& type, int& ga,
-                                            int& gb, int* ves, int* vid, bool* onj) {
-  r = (int)(e >> 32); type = (int)((e >> 30) & 3); ga = (int)((e >> 15) & 0x7FFF); gb = (int)(e & 0x7FFF);
-  int vi = a.ci[r], vj = a.cj[r];
-  if (type < 2) {
-    int vv = type == 0 ? vi : vj, vt = type == 0 ? vj : vi;
-    ves[0] = vv; vid[0] = ga; onj[0] = type == 1;
-    int tv[3];
-    stiv_tri_verts(2 * a.pv[vt], gb, tv);
-    for (int q = 0; q < 3; ++q) { ves[1 + q] = vt; vid[1 + q] = tv[q]; onj[1 + q] = type == 0; }
-  } else {
-    int u, v;
-    stiv_edge_verts(2 * a.pv[vi], ga, &u, &v);
-    ves[0] = vi; vid[0] = u; ves[1] = vi; vid[1] = v; onj[0] = onj[1] = false;
-    stiv_edge_verts(2 * a.pv[vj], gb, &u, &v);
-    ves[2] = vj; vid[2] = u; ves[3] = vj; vid[3] = v; onj[2] = onj[3] = true;
-  }
-}
-
-// FP32 frame of pair r: origin of vesicle i; offset of vesicle j's origin
-// (with its periodic image) and the bound on the FP32 position error, computed
-// once per candidate pair by patch_pairs_kernel.
-__device__ __forceinline__ float pair_frame(const narrow_args& a, int r, float* offB) {
-  float4 f = a.pinfo[r].frame;
-  offB[0] = f.x; offB[1] = f.y; offB[2] = f.z;
-  return f.w;
+// The 4 points of a descriptor: vertex id and whether the point belongs to
+// vesicle j (periodic image applied).  VF type 0: vertex of i, triangle of j;
+// type 1: vertex of j, triangle of i; EE: edge of i, edge of j.
+__device__ __forceinline__ void desc_points(ulonglong2 e, int& r, int& type, int& ga, int& gb, int* vid, bool* onj) {
+  r = (int)(e.x >> 32); type = (int)((e.x >> 30) & 3); ga = (int)((e.x >> 15) & 0x7FFF); gb = (int)(e.x & 0x7FFF);
+  for (int q = 0; q < 4; ++q) vid[q] = (int)((e.y >> (16 * q)) & 0xFFFF);
+  onj[0] = type == 1;
+  onj[1] = type == 0;
+  onj[2] = type != 1;
+  onj[3] = type != 1;
 }
 
 // FP32 points of a descriptor in the frame of its pair (for stage 3b).
-__device__ __forceinline__ void desc_points_f32(const narrow_args& a, unsigned long long e, int& kind, f3* xq, f3* dq,
+__device__ __forceinline__ void desc_points_f32(const narrow_args& a, ulonglong2 e, int& kind, f3* xq, f3* dq,
                                                 float& ep) {
-  int r, ty, ga, gb, ves[4], vid[4];
+  int r, ty, ga, gb, vid[4];
   bool onj[4];
-  desc_points(a, e, r, ty, ga, gb, ves, vid, onj);
-  float offB[3];
-  ep = pair_frame(a, r, offB);
+  desc_points(e, r, ty, ga, gb, vid, onj);
+  const stiv_pair_info* pi = a.pinfo + r;
+  float4 fr = pi->frame;
+  int vi = pi->vi, vj = pi->vj;
+  ep = fr.w;
   kind = ty == 2 ? 1 : 0;
   for (int q = 0; q < 4; ++q) {
-    int nv = stiv_nverts(2 * a.pv[ves[q]]);
-    const float* fp = a.fprep + (size_t)ves[q] * a.fstride + vid[q];
-    float o0 = onj[q] ? offB[0] : 0.f, o1 = onj[q] ? offB[1] : 0.f, o2 = onj[q] ? offB[2] : 0.f;
-    xq[q] = {fp[0] + o0, fp[(size_t)nv] + o1, fp[(size_t)2 * nv] + o2};
-    dq[q] = {fp[(size_t)3 * nv], fp[(size_t)4 * nv], fp[(size_t)5 * nv]};
+    const float4* fp = (const float4*)(a.fprep + (size_t)(onj[q] ? vj : vi) * a.fstride) + 2 * (size_t)vid[q];
+    float4 x = fp[0], d = fp[1];
+    float o0 = onj[q] ? fr.x : 0.f, o1 = onj[q] ? fr.y : 0.f, o2 = onj[q] ? fr.z : 0.f;
+    xq[q] = {x.x + o0, x.y + o1, x.z + o2};
+    dq[q] = {d.x, d.y, d.z};
   }
 }
 
 // Append a descriptor to a global list (warp-aggregated; lanes with keep).
-__device__ __forceinline__ void push_global(unsigned long long* list, int64_t cap, int64_t* count, int64_t* status,
-                                            bool keep, unsigned long long e, int lane) {
+__device__ __forceinline__ void push_global(ulonglong2* list, int64_t cap, int64_t* count, int64_t* status,
+                                            bool keep, ulonglong2 e, int lane) {
   unsigned m = __ballot_sync(0xffffffffu, keep);
   if (!m) return;
   unsigned long long base = 0;
@@ -785,7 +777,7 @@ __device__ __forceinline__ void load_f32(const int* sl, int kind, const PatchSm*
 __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, const narrow_args& a,
                                           long long& nprim) {
   bool keep = false;
-  unsigned long long desc = 0;
+  ulonglong2 desc = make_ulonglong2(0ull, 0ull);
   if (lane < n) {
     unsigned e = ws.q1[lane];
     int kind, x, y, sl[4];
@@ -810,7 +802,19 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
         cubic32 q = cubic_fp32(kind == 2 ? 1 : 0, xq, dq, ws.dx);
         keep = !bernstein_reject(q);
       }
-      if (keep) desc = make_desc(r, kind, prim_gid(*SA, kind == 2 ? 2 : 0, x), prim_gid(*SB, kind == 2 ? 2 : 1, y));
+      if (keep) {
+        unsigned long long v0 = (unsigned)SA->vid[sl[0]], v1, v2, v3;
+        if (kind < 2) {
+          v1 = (unsigned)SB->vid[sl[1]]; v2 = (unsigned)SB->vid[sl[2]]; v3 = (unsigned)SB->vid[sl[3]];
+        } else {
+          unsigned long long u = (unsigned)SA->vid[sl[1]];
+          if (u < v0) { v1 = v0; v0 = u; } else v1 = u;
+          unsigned long long p = (unsigned)SB->vid[sl[2]], q = (unsigned)SB->vid[sl[3]];
+          v2 = p < q ? p : q; v3 = p < q ? q : p;
+        }
+        desc.x = make_desc(r, kind, prim_gid(*SA, kind == 2 ? 2 : 0, x), prim_gid(*SB, kind == 2 ? 2 : 1, y));
+        desc.y = v0 | (v1 << 16) | (v2 << 32) | (v3 << 48);
+      }
     }
   }
   if (a.exact_only) push_global(a.q2, a.Q2, &a.ctr[15], &a.ctr[STIV_C_STATUS], keep, desc, lane);
@@ -838,7 +842,7 @@ __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, in
 
 // Stages 1-3a: one warp per patch pair.
 template <bool MIXED>
-__global__ void __launch_bounds__(NW * 32, 3) narrow_kernel(narrow_args a) {
+__global__ void __launch_bounds__(NW * 32, 4) narrow_kernel(narrow_args a) {
   extern __shared__ unsigned char smraw[];
   __shared__ PatchTopo topo[NVAR];
   WarpSm& ws = ((WarpSm*)smraw)[threadIdx.x >> 5];
@@ -938,7 +942,7 @@ __global__ void __launch_bounds__(PW * 32) pieces_kernel(narrow_args a) {
   for (int64_t b = gw; b < nb; b += nw) {
     int64_t idx = b * 32 + lane;
     bool valid = idx < n3;
-    unsigned long long e = valid ? a.q3[idx] : 0ull;
+    ulonglong2 e = valid ? a.q3[idx] : make_ulonglong2(0ull, 0ull);
     unsigned mask = 0;
     W.fail[lane] = 0;
     if (valid) {
@@ -1046,16 +1050,19 @@ __global__ void __launch_bounds__(128) fp64_kernel(narrow_args a) {
     double tau = 0.0, w1 = 0.0, w2 = 0.0;
     if (idx < n2) {
       ++nexact;
-      int ves[4], vid[4];
+      int vid[4];
       bool onj[4];
       int ty;
-      desc_points(a, a.q2[idx], r, ty, ga, gb, ves, vid, onj);
-      int code = a.cs[r];
+      desc_points(a.q2[idx], r, ty, ga, gb, vid, onj);
+      const stiv_pair_info* pi = a.pinfo + r;
+      int code = pi->code, Pij = pi->Pij;
+      long long voi = pi->voff_i, voj = pi->voff_j;
       int sB[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
+      int nvi = stiv_nverts(Pij & 0xFFFF), nvj = stiv_nverts(Pij >> 16);
       d3 X0[4], D[4];
       for (int q = 0; q < 4; ++q) {
-        int nv = stiv_nverts(2 * a.pv[ves[q]]);
-        size_t vb = a.voff[ves[q]] + vid[q];
+        int nv = onj[q] ? nvj : nvi;
+        size_t vb = (size_t)(onj[q] ? voj : voi) + vid[q];
         double p0[3], p1[3];
         for (int c = 0; c < 3; ++c) {
           size_t i0 = vb + (size_t)c * nv, i1 = vb + (size_t)(3 + c) * nv;

@@ -77,7 +77,7 @@ struct detect_ws {
   float* pbox;           // [N][pstride][6]
   int pstride;           // patches per vesicle at the largest order
   float* vorg;           // [N][4]  FP32 frame origin of each vesicle, and R = max |X - origin|
-  float* fprep;          // [N][fstride]  per vertex: X0 - origin (xyz), X1 - X0 (xyz), as float
+  float* fprep;          // [N][fstride]  per vertex 8 floats: X0 - origin (xyz, 0), X1 - X0 (xyz, 0)
   int64_t fstride;
   double* grid;          // [16]  h, origin xyz, cell sizes, G
   int32_t* cell_count;   // [N+1]
@@ -94,8 +94,8 @@ struct detect_ws {
   int32_t* pval2;        // [Q]
   uint64_t* work;        // [W]  patch-pair work items
   stiv_pair_info* pinfo; // [pair capacity]
-  unsigned long long* q3;  // [Q3] primitive pairs left for the FP32 piece tests
-  unsigned long long* q2;  // [Q2] primitive pairs left for the FP64 contact test
+  ulonglong2* q3;         // [Q3] primitive pairs left for the FP32 piece tests
+  ulonglong2* q2;         // [Q2] primitive pairs left for the FP64 contact test
   int64_t Q3, Q2;
   int32_t* pair_cnt;     // [pair capacity]   contacts per candidate pair
   int32_t* pair_fill;    // [pair capacity]
