@@ -82,7 +82,8 @@ enum stiv_flag {
   STIV_F_CONTACTS_OVERFLOW = 2,  /* contacts exceeded stiv_contacts.capacity    */
   STIV_F_BOX_TOO_SMALL = 4,      /* a vesicle box spans >= L/2 on a periodic axis */
   STIV_F_NONFINITE = 8,          /* a vertex coordinate is NaN or infinite      */
-  STIV_F_WORK_OVERFLOW = 16      /* internal work list overflow (re-run)         */
+  STIV_F_WORK_OVERFLOW = 16,     /* internal work list overflow (re-run)         */
+  STIV_F_TIMEOUT = 32            /* a bounded device wait gave up (mixed-form synthesis) */
 };
 
 typedef struct stiv_params {
@@ -145,7 +146,12 @@ int stiv_mesh_topology(int32_t P, int32_t* tri_dev, int32_t* edge_dev, void* str
 
 /* Sec. 3.1.2 upsampling: evaluate each vesicle's order-p series for X0 and X1
  * on its order-2p mesh (grid and poles).  p_dev[v] in [1, p_max], p_max <= 32.
- * Writes doubles (STIV_FP64) or floats (STIV_MIXED) into verts_dev. */
+ * STIV_FP64: FP64 synthesis, doubles in verts_dev.  STIV_MIXED: the synthesis
+ * runs on the tensor cores as one contraction per order with 3xTF32 split
+ * products accumulated in FP32 (the degree-0 term added in the epilogue) and
+ * writes floats; the handle keeps per-order tables and scratch (allocated on
+ * the first call with a given n_ves and p_max).  A bounded wait that gives up
+ * sets STIV_F_TIMEOUT in the next stiv_detect's counts. */
 int stiv_upsample(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
                   const int64_t* coef_off_dev, const double* coef_dev,
                   const int64_t* vert_off_dev, void* verts_dev);

@@ -32,9 +32,10 @@ __global__ void topology_kernel(int P, int32_t* tri, int32_t* edge) {
   }
 }
 
-__global__ void finalize_kernel(int64_t* ctr, int64_t C, int64_t* counts) {
+__global__ void finalize_kernel(int64_t* ctr, int64_t C, int64_t* counts, int* tc_status) {
   if (threadIdx.x == 0) {
     if (ctr[11] > C) ctr[STIV_C_STATUS] |= STIV_F_CONTACTS_OVERFLOW;
+    if (tc_status && *tc_status) { ctr[STIV_C_STATUS] |= STIV_F_TIMEOUT; *tc_status = 0; }
     for (int k = 0; k < 8; ++k) counts[k] = ctr[k];
     counts[STIV_C_FLOPS] = ctr[12];
     counts[STIV_C_EXACT] = ctr[13];
@@ -181,8 +182,11 @@ extern "C" int stiv_create(stiv_handle** out, const stiv_params* prm) {
 
 extern "C" int stiv_destroy(stiv_handle* h) {
   if (!h) return STIV_ERR_ARG;
-  for (int p = 0; p <= STIV_MAX_P; ++p)
+  for (int p = 0; p <= STIV_MAX_P; ++p) {
     if (h->tab_ready[p]) { cudaFree(h->tab[p].leg); cudaFree(h->tab[p].trig); cudaFree(h->tab[p].theta); }
+    if (h->ytab[p]) cudaFree(h->ytab[p]);
+  }
+  if (h->tc_ws) cudaFree(h->tc_ws);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->ws) cudaFree(h->ws);
   stiv_profile(h, 0);
@@ -306,7 +310,7 @@ extern "C" int stiv_detect(stiv_handle* h, void* stream, int32_t n_ves, int32_t 
   rc = stiv_contact_order(h, st, cand, out, w);
   if (rc) return rc;
   STIV_PROF(h, st, "finalize");
-  finalize_kernel<<<1, 32, 0, st>>>(w.ctr, w.C, counts_dev);
+  finalize_kernel<<<1, 32, 0, st>>>(w.ctr, w.C, counts_dev, h->tc_status);
   STIV_LAUNCH(h);
   return STIV_OK;
 }
@@ -319,6 +323,7 @@ extern "C" int stiv_sync_counts(void* stream, const int64_t* counts_dev, int64_t
   int64_t f = counts_host[STIV_C_STATUS];
   if (f & (STIV_F_PAIRS_OVERFLOW | STIV_F_CONTACTS_OVERFLOW | STIV_F_WORK_OVERFLOW)) return STIV_ERR_CAPACITY;
   if (f & (STIV_F_BOX_TOO_SMALL | STIV_F_NONFINITE)) return STIV_ERR_INPUT;
+  if (f & STIV_F_TIMEOUT) return STIV_ERR_TIMEOUT;
   return STIV_OK;
 }
 

@@ -32,6 +32,12 @@ struct stiv_handle {
   int last_cuda_error;
   stiv_tables tab[STIV_MAX_P + 1];
   bool tab_ready[STIV_MAX_P + 1];
+  // tensor-core synthesis (STIV_MIXED): synthesis-matrix blocks per order,
+  // per-call scratch, and the device status word of its bounded waits
+  float* ytab[STIV_MAX_P + 1];
+  void* tc_ws;
+  size_t tc_ws_bytes;
+  int* tc_status;
   void* ws;
   size_t ws_bytes;
   // CUDA graph of stiv_step
@@ -133,6 +139,10 @@ struct detect_ws {
   } while (0)
 
 int stiv_ensure_tables(stiv_handle* h, cudaStream_t st, int p);
+// STIV_MIXED synthesis on the tensor cores (3xTF32), FP32 vertices.
+int stiv_upsample_tc(stiv_handle* h, cudaStream_t st, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                     const int64_t* coef_off_dev, const double* coef_dev, const int64_t* vert_off_dev,
+                     float* verts_dev);
 int stiv_ws_reserve(stiv_handle* h, size_t bytes);
 int stiv_sort_pairs_impl(cudaStream_t st, int64_t n, int key_bits, const uint64_t* kin, const int32_t* vin,
                          uint64_t* kout, int32_t* vout, void* scratch, size_t scratch_bytes,

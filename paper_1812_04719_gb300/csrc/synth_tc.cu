@@ -1,0 +1,451 @@
+// Sec. 3.1.1-3.1.2 synthesis in the reduced-precision form (STIV_MIXED) on the
+// 5th-generation tensor cores: 3xTF32 products accumulated in FP32.
+//
+// For one SH order p the synthesis of every field (vesicle, time, coordinate)
+// is one dense contraction
+//     X[row][col] = sum_q Y[row][q] C[q][col],
+// Y the (n_v x (p+1)^2) synthesis matrix of the order-2p grid and its poles
+// (real orthonormal SH, Gauss-Legendre rings, uniform longitudes), C the
+// coefficient columns.  The degree-0 term (Y[row][0] = 1/sqrt(4 pi) for every
+// row: the vesicle's centre) is kept out of the contraction and added in the
+// epilogue, so the FP32 error is relative to the vesicle's size, not to its
+// position in the box.
+//
+// Split products: a = a_hi + a_lo with a_hi = tf32(a) and a_lo = tf32(a -
+// a_hi) (both rounded to nearest, exactly representable in TF32), and
+// A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi, each TF32 x TF32 product exact in
+// the FP32 accumulator.
+//
+// Data layout: both operands are K-major and stored in global memory already
+// in the tensor cores' shared-memory layout, in blocks of 128 rows x 32 k
+// (hi block 16 KB followed by lo block 16 KB):
+//     block[kg][row][4 floats],  kg = k / 4 (8 groups), 16 bytes per row,
+// i.e. the canonical no-swizzle K-major layout: core matrices of 8 rows x 16
+// bytes (128 contiguous bytes), 8-row groups 128 bytes apart (stride byte
+// offset), k groups 2048 bytes apart (leading byte offset).  One block is one
+// 32 KB bulk copy (cp.async.bulk) into shared memory.
+//
+// Kernels:
+//   ytab_kernel   Y blocks per order p (once per handle and order)
+//   group_kernel  vesicles bucketed by order, per-order tile counts and offsets
+//   bprep_kernel  coefficient blocks (FP64 -> FP32 split) and per-column
+//                 output address and degree-0 term
+//   gemm_kernel   persistent: per tile (order, 128 rows, 128 columns) one
+//                 thread streams A and B blocks through a 2-stage shared-memory
+//                 ring (bulk copies completing on mbarriers) and issues
+//                 tcgen05.mma (M = 128, N = 128, K = 8, kind::tf32) into a TMEM
+//                 accumulator; the 4 warps then read TMEM (tcgen05.ld
+//                 32x32b) and write the FP32 vertices.
+// Every wait on an mbarrier is bounded; a wait that gives up sets a status
+// word (reported as STIV_F_TIMEOUT) and the tile is abandoned.
+#include "stiv_internal.cuh"
+
+#include <math.h>
+
+namespace {
+
+constexpr int TM = 128;                 // tile rows (vertices)
+constexpr int TN = 128;                 // tile columns (fields)
+constexpr int TK = 32;                  // k per block
+constexpr int BLK_FLOATS = 8 * TM * 4;  // one hi or lo block: 4096 floats = 16 KB
+constexpr int BLK_BYTES = 2 * BLK_FLOATS * 4;  // hi + lo = 32 KB
+constexpr int STAGE_BYTES = 2 * BLK_BYTES;     // A + B
+constexpr unsigned WAIT_LIMIT = 1u << 24;      // try_wait polls before giving up
+constexpr double Y00 = 0.28209479177387814347;  // 1 / sqrt(4 pi)
+
+__host__ __device__ inline int tc_mtiles(int p) { return (stiv_nverts(2 * p) + TM - 1) / TM; }
+__host__ __device__ inline int tc_kblocks(int p) { return ((p + 1) * (p + 1) - 1 + TK - 1) / TK; }
+
+// tf32 rounding to nearest (ties to even) of a finite float
+__device__ __forceinline__ float tf32_rn(float x) {
+  unsigned b = __float_as_uint(x);
+  b += 0x0FFFu + ((b >> 13) & 1u);
+  return __uint_as_float(b & 0xFFFFE000u);
+}
+
+// index of element (row, k) inside a hi or lo block
+__device__ __forceinline__ int blk_index(int row, int k) { return (k >> 2) * (TM * 4) + row * 4 + (k & 3); }
+
+// ---------------------------------------------------------------------------
+// Y blocks of order p: [mtile][kblock][hi | lo][8][128][4]
+// ---------------------------------------------------------------------------
+__global__ void ytab_kernel(int p, const double* leg, float* ytab) {
+  int P = 2 * p, W = 2 * P, nv = stiv_nverts(P), nc = (p + 1) * (p + 1), nl = (p + 1) * (p + 2) / 2;
+  int MT = tc_mtiles(p), KB = tc_kblocks(p);
+  int64_t total = (int64_t)MT * KB * TM * TK;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int k = (int)(t % TK);
+    int64_t rest = t / TK;
+    int r = (int)(rest % TM);
+    rest /= TM;
+    int kb = (int)(rest % KB), mt = (int)(rest / KB);
+    int row = mt * TM + r, q = kb * TK + k + 1;
+    double y = 0.0;
+    if (row < nv && q < nc) {
+      int n = (int)sqrt((double)q);
+      while (n * n > q) --n;
+      while ((n + 1) * (n + 1) <= q) ++n;
+      int m = q - n * n - n, am = m < 0 ? -m : m;
+      if (row < W * (P + 1)) {
+        int i = row / W, j = row % W;
+        double L = leg[(size_t)i * nl + n * (n + 1) / 2 + am];
+        double tr = 1.0;
+        if (m != 0) {
+          double sv, cv;
+          sincospi((double)((am * j) % W) / P, &sv, &cv);
+          tr = m > 0 ? cv : sv;
+        }
+        y = L * tr;
+      } else if (m == 0) {
+        int pole = row - W * (P + 1);
+        y = leg[(size_t)(P + 1 + pole) * nl + n * (n + 1) / 2];
+      }
+    }
+    float yf = (float)y, hi = tf32_rn(yf), lo = tf32_rn(yf - hi);
+    float* blk = ytab + ((size_t)mt * KB + kb) * (2 * BLK_FLOATS);
+    blk[blk_index(r, k)] = hi;
+    blk[BLK_FLOATS + blk_index(r, k)] = lo;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-call grouping by order
+// ---------------------------------------------------------------------------
+struct tc_group {
+  int cnt, list_off, ntn, mt, kb, tile_off;  // vesicles, list offset, column tiles, row tiles, k blocks, first tile
+  long long boff;                            // first B block of the group
+  long long coff;                            // first column (of all groups' padded columns)
+};
+
+// tc_ws layout: [status int][ntiles int][pad][groups (STIV_MAX_P+1)][list n][colinfo][B blocks]
+struct tc_colinfo {
+  long long dst;  // element offset of row 0 of this field in the vertex array (-1: padding column)
+  float bias;     // degree-0 term
+  float pad;
+};
+
+__global__ void group_kernel(int n, int p_max, const int32_t* pv, tc_group* g, int* ntiles, int* list) {
+  __shared__ int cnt[STIV_MAX_P + 1], fill[STIV_MAX_P + 1], off[STIV_MAX_P + 1];
+  for (int p = threadIdx.x; p <= STIV_MAX_P; p += blockDim.x) { cnt[p] = 0; fill[p] = 0; }
+  __syncthreads();
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    int p = pv[v];
+    if (p >= 1 && p <= p_max) atomicAdd(&cnt[p], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int lo = 0, to = 0;
+    long long bo = 0, co = 0;
+    for (int p = 0; p <= STIV_MAX_P; ++p) {
+      tc_group G;
+      G.cnt = (p >= 1 && p <= p_max) ? cnt[p] : 0;
+      G.list_off = lo;
+      G.ntn = (6 * G.cnt + TN - 1) / TN;
+      G.mt = p >= 1 ? tc_mtiles(p) : 0;
+      G.kb = p >= 1 ? tc_kblocks(p) : 0;
+      G.tile_off = to;
+      G.boff = bo;
+      G.coff = co;
+      off[p] = lo;
+      lo += G.cnt;
+      to += G.mt * G.ntn;
+      bo += (long long)G.ntn * G.kb;
+      co += (long long)G.ntn * TN;
+      g[p] = G;
+    }
+    *ntiles = to;
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < n; v += blockDim.x) {
+    int p = pv[v];
+    if (p >= 1 && p <= p_max) list[off[p] + atomicAdd(&fill[p], 1)] = v;
+  }
+}
+
+// B blocks: column c of order group p is field (c % 6) of vesicle list[c / 6];
+// thread per (group, column, k block, k group of 4).
+__global__ void bprep_kernel(int p_max, const tc_group* g, const int* list, const int64_t* coef_off,
+                             const double* coef, const int64_t* vert_off, float* bblk, tc_colinfo* ci) {
+  for (int p = 1; p <= p_max; ++p) {
+    tc_group G = g[p];
+    if (G.cnt == 0) continue;
+    int nc = (p + 1) * (p + 1), nv = stiv_nverts(2 * p);
+    long long ncols = (long long)G.ntn * TN;
+    long long items = ncols * G.kb * (TK / 4);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < items;
+         t += (long long)gridDim.x * blockDim.x) {
+      int kg = (int)(t % (TK / 4));
+      long long rest = t / (TK / 4);
+      long long c = rest % ncols;
+      int kb = (int)(rest / ncols);
+      int v = c / 6 < G.cnt ? list[G.list_off + c / 6] : -1;
+      int f = (int)(c % 6);
+      float hi[4], lo[4];
+      for (int e = 0; e < 4; ++e) {
+        int q = kb * TK + kg * 4 + e + 1;
+        float x = 0.f;
+        if (v >= 0 && q < nc) x = __double2float_rn(coef[coef_off[v] + (size_t)f * nc + q]);
+        hi[e] = tf32_rn(x);
+        lo[e] = tf32_rn(x - hi[e]);
+      }
+      int nt = (int)(c / TN), r = (int)(c % TN);
+      float* blk = bblk + ((size_t)G.boff + (size_t)nt * G.kb + kb) * (2 * BLK_FLOATS);
+      *(float4*)(blk + blk_index(r, kg * 4)) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      *(float4*)(blk + BLK_FLOATS + blk_index(r, kg * 4)) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      if (kb == 0 && kg == 0) {
+        tc_colinfo info;
+        info.dst = v >= 0 ? (long long)vert_off[v] + (long long)f * nv : -1;
+        info.bias = v >= 0 ? (float)(Y00 * coef[coef_off[v] + (size_t)f * nc]) : 0.f;
+        info.pad = 0.f;
+        ci[(size_t)G.coff + c] = info;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 / bulk-copy / mbarrier primitives (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// true once the phase with the given parity has completed; gives up after WAIT_LIMIT polls
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// shared-memory matrix descriptor, no swizzle: start, leading byte offset (k
+// direction), stride byte offset (8-row groups), version 1
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((addr & 0x3FFFFu) >> 4) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor: D f32, A and B tf32, both K-major, N = TN, M = TM
+constexpr unsigned IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(TN >> 3) << 17) | ((unsigned)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(unsigned tmem, unsigned long long ad, unsigned long long bd, unsigned acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct gemm_args {
+  const tc_group* g;
+  const int* ntiles;
+  const float* ytab[STIV_MAX_P + 1];
+  const float* bblk;
+  const tc_colinfo* ci;
+  float* X;
+  int* status;
+  int p_max;
+};
+
+__global__ void __launch_bounds__(128, 1) gemm_kernel(gemm_args a) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ tc_group G[STIV_MAX_P + 1];
+  __shared__ __align__(8) unsigned long long bars[4];   // load[2], mma[2]
+  __shared__ unsigned tmem_base;
+  __shared__ int abandon;
+  int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* sm = (unsigned char*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
+  for (int p = tid; p <= STIV_MAX_P; p += blockDim.x) G[p] = a.g[p];
+  if (tid == 0) {
+    for (int b = 0; b < 4; ++b) mbar_init(smem_u32(&bars[b]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"((unsigned)TN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  unsigned tmem = tmem_base;
+  unsigned load_bar[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
+  unsigned mma_bar[2] = {smem_u32(&bars[2]), smem_u32(&bars[3])};
+  unsigned load_cnt[2] = {0, 0}, mma_cnt[2] = {0, 0};   // completions issued per barrier (thread 0)
+  int ntiles = *a.ntiles;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int p = 1;
+    while (p <= a.p_max && tile >= G[p].tile_off + G[p].mt * G[p].ntn) ++p;
+    if (p > a.p_max) break;
+    tc_group g = G[p];
+    int local = tile - g.tile_off, mt = local / g.ntn, nt = local % g.ntn, KB = g.kb;
+    const unsigned char* asrc = (const unsigned char*)(a.ytab[p] + (size_t)mt * KB * (2 * BLK_FLOATS));
+    const unsigned char* bsrc = (const unsigned char*)(a.bblk + ((size_t)g.boff + (size_t)nt * KB) * (2 * BLK_FLOATS));
+    if (tid == 0) {
+      bool ok = true;
+      // prologue: block 0 -> stage 0
+      mbar_expect_tx(load_bar[0], STAGE_BYTES);
+      bulk_g2s(smem_u32(sm), asrc, BLK_BYTES, load_bar[0]);
+      bulk_g2s(smem_u32(sm + BLK_BYTES), bsrc, BLK_BYTES, load_bar[0]);
+      ++load_cnt[0];
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        int s = kb & 1;
+        if (kb + 1 < KB) {
+          int s2 = s ^ 1;
+          // the stage is free once the MMAs that last read it have completed
+          if (mma_cnt[s2] > 0) ok = mbar_wait(mma_bar[s2], (mma_cnt[s2] - 1) & 1);
+          if (!ok) break;
+          unsigned char* dst = sm + (size_t)s2 * STAGE_BYTES;
+          mbar_expect_tx(load_bar[s2], STAGE_BYTES);
+          bulk_g2s(smem_u32(dst), asrc + (size_t)(kb + 1) * BLK_BYTES, BLK_BYTES, load_bar[s2]);
+          bulk_g2s(smem_u32(dst + BLK_BYTES), bsrc + (size_t)(kb + 1) * BLK_BYTES, BLK_BYTES, load_bar[s2]);
+          ++load_cnt[s2];
+        }
+        ok = mbar_wait(load_bar[s], (load_cnt[s] - 1) & 1);
+        if (!ok) break;
+        tc_fence_after();
+        unsigned abase = smem_u32(sm + (size_t)s * STAGE_BYTES), bbase = abase + BLK_BYTES;
+#pragma unroll
+        for (int ks = 0; ks < TK / 8; ++ks) {
+          unsigned off = ks * 2 * (TM * 16);   // two k groups of 2048 bytes per K = 8
+          unsigned long long ahi = smem_desc(abase + off, TM * 16, 128);
+          unsigned long long alo = smem_desc(abase + BLK_BYTES / 2 + off, TM * 16, 128);
+          unsigned long long bhi = smem_desc(bbase + off, TN * 16, 128);
+          unsigned long long blo = smem_desc(bbase + BLK_BYTES / 2 + off, TN * 16, 128);
+          mma_tf32(tmem, ahi, bhi, (kb | ks) != 0);
+          mma_tf32(tmem, ahi, blo, 1u);
+          mma_tf32(tmem, alo, bhi, 1u);
+        }
+        mma_commit(mma_bar[s]);
+        ++mma_cnt[s];
+      }
+      if (ok) {
+        int sl = (KB - 1) & 1;
+        ok = mbar_wait(mma_bar[sl], (mma_cnt[sl] - 1) & 1);
+      }
+      abandon = ok ? 0 : 1;
+      if (!ok) atomicOr(a.status, 1);
+    }
+    __syncthreads();
+    if (abandon) break;   // state of the barriers is unknown: stop this CTA
+    tc_fence_after();
+    // epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w + 31
+    int row = mt * TM + warp * 32 + lane;
+    int nv = stiv_nverts(2 * p);
+    const tc_colinfo* cinfo = a.ci + (size_t)g.coff + (size_t)nt * TN;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        tc_colinfo info = cinfo[c0 + i];
+        if (info.dst >= 0 && row < nv) a.X[info.dst + row] = v[i] + info.bias;
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)TN));
+}
+
+}  // namespace
+
+// Y blocks of order p for this handle (built once).
+static int ensure_ytab(stiv_handle* h, cudaStream_t st, int p) {
+  if (h->ytab[p]) return STIV_OK;
+  int rc = stiv_ensure_tables(h, st, p);
+  if (rc) return rc;
+  size_t bytes = (size_t)tc_mtiles(p) * tc_kblocks(p) * BLK_BYTES;
+  STIV_CUDA(h, cudaMalloc(&h->ytab[p], bytes));
+  ytab_kernel<<<1024, 256, 0, st>>>(p, h->tab[p].leg, h->ytab[p]);
+  STIV_LAUNCH(h);
+  return STIV_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int stiv_upsample_tc(stiv_handle* h, cudaStream_t st, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                     const int64_t* coef_off_dev, const double* coef_dev, const int64_t* vert_off_dev,
+                     float* verts_dev) {
+  for (int p = 1; p <= p_max; ++p) {
+    int rc = ensure_ytab(h, st, p);
+    if (rc) return rc;
+  }
+  // scratch bounds from n_ves and p_max only (sizes must not depend on device data)
+  long long max_ntn = (6LL * n_ves + TN - 1) / TN + p_max;
+  long long max_blocks = max_ntn * tc_kblocks(p_max);
+  size_t o_status = 0;
+  size_t o_g = 256;
+  size_t o_list = align256(o_g + sizeof(tc_group) * (STIV_MAX_P + 1));
+  size_t o_ci = align256(o_list + sizeof(int) * (size_t)n_ves);
+  size_t o_b = align256(o_ci + sizeof(tc_colinfo) * (size_t)max_ntn * TN);
+  size_t total = o_b + (size_t)max_blocks * BLK_BYTES;
+  if (total > h->tc_ws_bytes) {
+    if (h->tc_ws) { STIV_CUDA(h, cudaFree(h->tc_ws)); h->tc_ws = nullptr; h->tc_ws_bytes = 0; }
+    STIV_CUDA(h, cudaMalloc(&h->tc_ws, total));
+    STIV_CUDA(h, cudaMemsetAsync(h->tc_ws, 0, 256, st));
+    h->tc_ws_bytes = total;
+  }
+  char* w = (char*)h->tc_ws;
+  int* status = (int*)(w + o_status);
+  int* ntiles = status + 1;
+  tc_group* g = (tc_group*)(w + o_g);
+  int* list = (int*)(w + o_list);
+  tc_colinfo* ci = (tc_colinfo*)(w + o_ci);
+  float* bblk = (float*)(w + o_b);
+  h->tc_status = status;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  STIV_PROF_N(h, st, "synth", 3);
+  group_kernel<<<1, 1024, 0, st>>>(n_ves, p_max, p_dev, g, ntiles, list);
+  bprep_kernel<<<sms * 8, 256, 0, st>>>(p_max, g, list, coef_off_dev, coef_dev, vert_off_dev, bblk, ci);
+  gemm_args A;
+  A.g = g; A.ntiles = ntiles; A.bblk = bblk; A.ci = ci; A.X = verts_dev; A.status = status; A.p_max = p_max;
+  for (int p = 0; p <= STIV_MAX_P; ++p) A.ytab[p] = p >= 1 && p <= p_max ? h->ytab[p] : nullptr;
+  // 2 stages, plus 64 KB that no copy writes: every address a descriptor can
+  // form from these tiles stays inside the allocation
+  size_t smem = 3 * (size_t)STAGE_BYTES + 1024;
+  STIV_CUDA(h, cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  long long tiles_bound = max_ntn * tc_mtiles(p_max);
+  int grid = (int)(tiles_bound < sms ? tiles_bound : sms);
+  gemm_kernel<<<grid, 128, smem, st>>>(A);
+  STIV_LAUNCH(h);
+  return STIV_OK;
+}

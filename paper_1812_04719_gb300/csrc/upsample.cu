@@ -190,6 +190,8 @@ extern "C" int stiv_upsample(stiv_handle* h, void* stream, int32_t n_ves, int32_
   if (n_ves == 0) return STIV_OK;
   if (!p_dev || !coef_off_dev || !coef_dev || !vert_off_dev || !verts_dev) return STIV_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  if (h->prm.precision == STIV_MIXED)
+    return stiv_upsample_tc(h, st, n_ves, p_max, p_dev, coef_off_dev, coef_dev, vert_off_dev, (float*)verts_dev);
   synth_args a;
   a.p = p_dev; a.coef_off = coef_off_dev; a.coef = coef_dev; a.vert_off = vert_off_dev;
   a.verts = verts_dev; a.mixed = h->prm.precision == STIV_MIXED;

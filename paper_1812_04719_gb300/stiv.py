@@ -28,7 +28,7 @@ STIV_OK, STIV_ERR_ARG, STIV_ERR_CAPACITY, STIV_ERR_TIMEOUT, STIV_ERR_CUDA, STIV_
 STIV_FP64, STIV_MIXED = 0, 1
 C_PAIRS, C_PRIM, C_VF, C_EE, C_CPAIRS, C_DEGEN, C_STATUS, C_PATCH, C_FLOPS, C_EXACT = range(10)
 NCOUNTS = 10
-F_PAIRS_OVERFLOW, F_CONTACTS_OVERFLOW, F_BOX_TOO_SMALL, F_NONFINITE, F_WORK_OVERFLOW = 1, 2, 4, 8, 16
+F_PAIRS_OVERFLOW, F_CONTACTS_OVERFLOW, F_BOX_TOO_SMALL, F_NONFINITE, F_WORK_OVERFLOW, F_TIMEOUT = 1, 2, 4, 8, 16, 32
 
 EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_error", "stiv_mesh_topology",
            "stiv_upsample", "stiv_detect", "stiv_stiv", "stiv_stiv_grad", "stiv_grad_scatter",

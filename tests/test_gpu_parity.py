@@ -99,6 +99,29 @@ def test_upsample_matches_oracle(orc, name):
     assert np.abs(g["verts"] - Xo).max() < 1e-13 * max(scale, 1.0)
 
 
+@pytest.mark.parametrize("name", list(SCENES) + ["lattice_144_p16"])
+def test_upsample_mixed_tensor_cores(orc, name):
+    """STIV_MIXED synthesis (tensor cores, 3xTF32 products, FP32 accumulation,
+    degree-0 term added in the epilogue) against the FP64 oracle.  Bound per
+    vertex of field (vesicle, time, coordinate) with coefficients a_q:
+    2^-23 |X| (FP32 result and degree-0 rounding) + 2^-19 sum_{q>0} |a_q| Ymax,
+    Ymax = sqrt((2p+1) / (2 pi)) >= |Y_q| (each split product keeps a relative
+    error near 2^-22; FP32 accumulation over the terms)."""
+    sc = G.scene_lattice58((6, 6, 2)) if name == "lattice_144_p16" else SCENES[name]()
+    g = run_gpu(sc, precision=S.STIV_MIXED, grad=False, pair_cap=2048, contact_cap=1 << 17)
+    worst = 0.0
+    offs = sc.vert_off()
+    for v in range(sc.n):
+        p, P = int(sc.p[v]), int(sc.P[v])
+        Xo = orc.synth_vesicle(p, P, sc.coef_of(v))
+        Xg = g["verts"][offs[v]:offs[v] + Xo.size].reshape(Xo.shape)
+        a1 = np.abs(sc.coef_of(v)[:, :, 1:]).sum(axis=-1)[:, :, None]
+        bound = 2.0 ** -23 * np.abs(Xo) + 2.0 ** -19 * a1 * np.sqrt((2 * p + 1) / (2 * np.pi))
+        assert np.all(np.abs(Xg - Xo) <= bound), v
+        worst = max(worst, float((np.abs(Xg - Xo) / bound).max()))
+    print(f"mixed synthesis: max error / bound = {worst:.3f}")
+
+
 @pytest.mark.parametrize("name", list(SCENES))
 def test_detect_bit_exact(orc, name):
     """Candidate pairs and contacts (keys, tau and weights bit for bit) equal
