@@ -30,12 +30,13 @@
 //   group_kernel  vesicles bucketed by order, per-order tile counts and offsets
 //   bprep_kernel  coefficient blocks (FP64 -> FP32 split) and per-column
 //                 output address and degree-0 term
-//   gemm_kernel   persistent: per tile (order, 128 rows, 128 columns) one
-//                 thread streams A and B blocks through a 2-stage shared-memory
-//                 ring (bulk copies completing on mbarriers) and issues
-//                 tcgen05.mma (M = 128, N = 128, K = 8, kind::tf32) into a TMEM
-//                 accumulator; the 4 warps then read TMEM (tcgen05.ld
-//                 32x32b) and write the FP32 vertices.
+//   gemm_kernel   persistent, warp-specialised: per tile (order, 128 rows,
+//                 128 columns) warp 0 streams the A and B blocks through a
+//                 3-stage shared-memory ring (bulk copies completing on
+//                 mbarriers), warp 1 issues tcgen05.mma (M = 128, N = 128,
+//                 K = 8, kind::tf32) into one of two TMEM accumulators, and
+//                 warps 2-5 read the other accumulator (tcgen05.ld 32x32b) and
+//                 write the FP32 vertices while the next tile accumulates.
 // Every wait on an mbarrier is bounded; a wait that gives up sets a status
 // word (reported as STIV_F_TIMEOUT) and the tile is abandoned.
 #include "stiv_internal.cuh"
@@ -50,7 +51,7 @@ constexpr int TK = 32;                  // k per block
 constexpr int BLK_FLOATS = 8 * TM * 4;  // one hi or lo block: 4096 floats = 16 KB
 constexpr int BLK_BYTES = 2 * BLK_FLOATS * 4;  // hi + lo = 32 KB
 constexpr int STAGE_BYTES = 2 * BLK_BYTES;     // A + B
-constexpr unsigned WAIT_LIMIT = 1u << 24;      // try_wait polls before giving up
+constexpr long long WAIT_CYCLES = 2000000000LL; // bound of every mbarrier wait (SM clocks)
 constexpr double Y00 = 0.28209479177387814347;  // 1 / sqrt(4 pi)
 
 __host__ __device__ inline int tc_mtiles(int p) { return (stiv_nverts(2 * p) + TM - 1) / TM; }
@@ -214,9 +215,12 @@ __device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-// true once the phase with the given parity has completed; gives up after WAIT_LIMIT polls
+// true once the phase with the given parity has completed; gives up after
+// WAIT_CYCLES SM clocks (about a second), however long each try_wait
+// suspends the thread
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+  long long t0 = clock64();
+  while (true) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -226,8 +230,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if (clock64() - t0 > WAIT_CYCLES) return false;
   }
-  return false;
 }
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -281,108 +285,147 @@ struct gemm_args {
   int p_max;
 };
 
-__global__ void __launch_bounds__(128, 1) gemm_kernel(gemm_args a) {
+constexpr int NSTAGE = 3;               // shared-memory ring of (A, B) blocks
+constexpr int NACC = 2;                 // TMEM accumulators (MMA of tile t+1 overlaps the epilogue of tile t)
+constexpr int GEMM_THREADS = 192;       // warp 0 copies, warp 1 issues MMAs, warps 2-5 epilogue
+
+// Tile t of this CTA's sequence: order group, row tile, column tile.
+__device__ __forceinline__ bool tile_of(const tc_group* G, int p_max, int tile, int& p, int& mt, int& nt) {
+  p = 1;
+  while (p <= p_max && tile >= G[p].tile_off + G[p].mt * G[p].ntn) ++p;
+  if (p > p_max) return false;
+  int local = tile - G[p].tile_off;
+  mt = local / G[p].ntn;
+  nt = local % G[p].ntn;
+  return true;
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(gemm_args a) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ tc_group G[STIV_MAX_P + 1];
-  __shared__ __align__(8) unsigned long long bars[4];   // load[2], mma[2]
+  // full[NSTAGE], empty[NSTAGE], acc_full[NACC], acc_empty[NACC]
+  __shared__ __align__(8) unsigned long long bars[2 * NSTAGE + 2 * NACC];
   __shared__ unsigned tmem_base;
-  __shared__ int abandon;
   int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char* sm = (unsigned char*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
   for (int p = tid; p <= STIV_MAX_P; p += blockDim.x) G[p] = a.g[p];
   if (tid == 0) {
-    for (int b = 0; b < 4; ++b) mbar_init(smem_u32(&bars[b]), 1);
+    for (int b = 0; b < NSTAGE; ++b) { mbar_init(smem_u32(&bars[b]), 1); mbar_init(smem_u32(&bars[NSTAGE + b]), 1); }
+    for (int b = 0; b < NACC; ++b) {
+      mbar_init(smem_u32(&bars[2 * NSTAGE + b]), 1);
+      mbar_init(smem_u32(&bars[2 * NSTAGE + NACC + b]), 4);   // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"((unsigned)TN));
+                 "r"((unsigned)(NACC * TN)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   unsigned tmem = tmem_base;
-  unsigned load_bar[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
-  unsigned mma_bar[2] = {smem_u32(&bars[2]), smem_u32(&bars[3])};
-  unsigned load_cnt[2] = {0, 0}, mma_cnt[2] = {0, 0};   // completions issued per barrier (thread 0)
+  auto full = [&](int s) { return smem_u32(&bars[s]); };
+  auto empty = [&](int s) { return smem_u32(&bars[NSTAGE + s]); };
+  auto acc_full = [&](int b) { return smem_u32(&bars[2 * NSTAGE + b]); };
+  auto acc_empty = [&](int b) { return smem_u32(&bars[2 * NSTAGE + NACC + b]); };
   int ntiles = *a.ntiles;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int p = 1;
-    while (p <= a.p_max && tile >= G[p].tile_off + G[p].mt * G[p].ntn) ++p;
-    if (p > a.p_max) break;
-    tc_group g = G[p];
-    int local = tile - g.tile_off, mt = local / g.ntn, nt = local % g.ntn, KB = g.kb;
-    const unsigned char* asrc = (const unsigned char*)(a.ytab[p] + (size_t)mt * KB * (2 * BLK_FLOATS));
-    const unsigned char* bsrc = (const unsigned char*)(a.bblk + ((size_t)g.boff + (size_t)nt * KB) * (2 * BLK_FLOATS));
-    if (tid == 0) {
-      bool ok = true;
-      // prologue: block 0 -> stage 0
-      mbar_expect_tx(load_bar[0], STAGE_BYTES);
-      bulk_g2s(smem_u32(sm), asrc, BLK_BYTES, load_bar[0]);
-      bulk_g2s(smem_u32(sm + BLK_BYTES), bsrc, BLK_BYTES, load_bar[0]);
-      ++load_cnt[0];
-      for (int kb = 0; kb < KB && ok; ++kb) {
-        int s = kb & 1;
-        if (kb + 1 < KB) {
-          int s2 = s ^ 1;
-          // the stage is free once the MMAs that last read it have completed
-          if (mma_cnt[s2] > 0) ok = mbar_wait(mma_bar[s2], (mma_cnt[s2] - 1) & 1);
-          if (!ok) break;
-          unsigned char* dst = sm + (size_t)s2 * STAGE_BYTES;
-          mbar_expect_tx(load_bar[s2], STAGE_BYTES);
-          bulk_g2s(smem_u32(dst), asrc + (size_t)(kb + 1) * BLK_BYTES, BLK_BYTES, load_bar[s2]);
-          bulk_g2s(smem_u32(dst + BLK_BYTES), bsrc + (size_t)(kb + 1) * BLK_BYTES, BLK_BYTES, load_bar[s2]);
-          ++load_cnt[s2];
+  bool ok = true;
+  if (warp == 0) {
+    // producer: one lane streams the A and B blocks of every tile through the ring
+    if (lane == 0) {
+      unsigned it = 0;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        int p, mt, nt;
+        if (!tile_of(G, a.p_max, tile, p, mt, nt)) break;
+        int KB = G[p].kb;
+        const unsigned char* asrc = (const unsigned char*)(a.ytab[p] + (size_t)mt * KB * (2 * BLK_FLOATS));
+        const unsigned char* bsrc =
+            (const unsigned char*)(a.bblk + ((size_t)G[p].boff + (size_t)nt * KB) * (2 * BLK_FLOATS));
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          int s = it % NSTAGE;
+          unsigned ph = (it / NSTAGE) & 1;
+          if (!mbar_wait(empty(s), ph ^ 1)) { ok = false; break; }
+          unsigned char* dst = sm + (size_t)s * STAGE_BYTES;
+          mbar_expect_tx(full(s), STAGE_BYTES);
+          bulk_g2s(smem_u32(dst), asrc + (size_t)kb * BLK_BYTES, BLK_BYTES, full(s));
+          bulk_g2s(smem_u32(dst + BLK_BYTES), bsrc + (size_t)kb * BLK_BYTES, BLK_BYTES, full(s));
         }
-        ok = mbar_wait(load_bar[s], (load_cnt[s] - 1) & 1);
-        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    // MMA issuer: one lane; accumulator b = (tile count) % NACC
+    if (lane == 0) {
+      unsigned it = 0, tc = 0;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tc) {
+        int p, mt, nt;
+        if (!tile_of(G, a.p_max, tile, p, mt, nt)) break;
+        int KB = G[p].kb;
+        int b = tc % NACC;
+        if (!mbar_wait(acc_empty(b), ((tc / NACC) & 1) ^ 1)) { ok = false; break; }
         tc_fence_after();
-        unsigned abase = smem_u32(sm + (size_t)s * STAGE_BYTES), bbase = abase + BLK_BYTES;
+        unsigned dtm = tmem + (unsigned)(b * TN);
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          int s = it % NSTAGE;
+          if (!mbar_wait(full(s), (it / NSTAGE) & 1)) { ok = false; break; }
+          tc_fence_after();
+          unsigned abase = smem_u32(sm + (size_t)s * STAGE_BYTES), bbase = abase + BLK_BYTES;
 #pragma unroll
-        for (int ks = 0; ks < TK / 8; ++ks) {
-          unsigned off = ks * 2 * (TM * 16);   // two k groups of 2048 bytes per K = 8
-          unsigned long long ahi = smem_desc(abase + off, TM * 16, 128);
-          unsigned long long alo = smem_desc(abase + BLK_BYTES / 2 + off, TM * 16, 128);
-          unsigned long long bhi = smem_desc(bbase + off, TN * 16, 128);
-          unsigned long long blo = smem_desc(bbase + BLK_BYTES / 2 + off, TN * 16, 128);
-          mma_tf32(tmem, ahi, bhi, (kb | ks) != 0);
-          mma_tf32(tmem, ahi, blo, 1u);
-          mma_tf32(tmem, alo, bhi, 1u);
+          for (int ks = 0; ks < TK / 8; ++ks) {
+            unsigned off = ks * 2 * (TM * 16);   // two k groups of 2048 bytes per K = 8
+            unsigned long long ahi = smem_desc(abase + off, TM * 16, 128);
+            unsigned long long alo = smem_desc(abase + BLK_BYTES / 2 + off, TM * 16, 128);
+            unsigned long long bhi = smem_desc(bbase + off, TN * 16, 128);
+            unsigned long long blo = smem_desc(bbase + BLK_BYTES / 2 + off, TN * 16, 128);
+            mma_tf32(dtm, ahi, bhi, (kb | ks) != 0);
+            mma_tf32(dtm, ahi, blo, 1u);
+            mma_tf32(dtm, alo, bhi, 1u);
+          }
+          mma_commit(empty(s));      // the stage is free once these MMAs have read it
         }
-        mma_commit(mma_bar[s]);
-        ++mma_cnt[s];
+        if (!ok) break;
+        mma_commit(acc_full(b));     // accumulator b holds the finished tile
       }
-      if (ok) {
-        int sl = (KB - 1) & 1;
-        ok = mbar_wait(mma_bar[sl], (mma_cnt[sl] - 1) & 1);
-      }
-      abandon = ok ? 0 : 1;
-      if (!ok) atomicOr(a.status, 1);
     }
-    __syncthreads();
-    if (abandon) break;   // state of the barriers is unknown: stop this CTA
-    tc_fence_after();
-    // epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w + 31
-    int row = mt * TM + warp * 32 + lane;
-    int nv = stiv_nverts(2 * p);
-    const tc_colinfo* cinfo = a.ci + (size_t)g.coff + (size_t)nt * TN;
+  } else {
+    // epilogue warps 2-5: TMEM lanes 32 (w % 4) .. + 31 are tile rows
+    int q = warp & 3;
+    unsigned tc = 0;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tc) {
+      int p, mt, nt;
+      if (!tile_of(G, a.p_max, tile, p, mt, nt)) break;
+      int b = tc % NACC;
+      if (!mbar_wait(acc_full(b), (tc / NACC) & 1)) { ok = false; break; }
+      tc_fence_after();
+      int row = mt * TM + q * 32 + lane;
+      int nv = stiv_nverts(2 * p);
+      const tc_colinfo* cinfo = a.ci + (size_t)G[p].coff + (size_t)nt * TN;
 #pragma unroll 1
-    for (int c0 = 0; c0 < TN; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+      for (int c0 = 0; c0 < TN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * TN + c0), v);
+        tc_colinfo mine = cinfo[c0 + (lane & 15)];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        tc_colinfo info = cinfo[c0 + i];
-        if (info.dst >= 0 && row < nv) a.X[info.dst + row] = v[i] + info.bias;
+        for (int i = 0; i < 16; ++i) {
+          long long dst = __shfl_sync(0xffffffffu, mine.dst, i);
+          float bias = __shfl_sync(0xffffffffu, mine.bias, i);
+          if (dst >= 0 && row < nv) a.X[dst + row] = v[i] + bias;
+        }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acc_empty(b)) : "memory");
     }
-    tc_fence_before();
-    __syncthreads();
   }
+  if (!ok) atomicOr(a.status, 1);
+  tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)TN));
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((unsigned)(NACC * TN)));
+  }
 }
 
 }  // namespace
@@ -439,13 +482,11 @@ int stiv_upsample_tc(stiv_handle* h, cudaStream_t st, int32_t n_ves, int32_t p_m
   gemm_args A;
   A.g = g; A.ntiles = ntiles; A.bblk = bblk; A.ci = ci; A.X = verts_dev; A.status = status; A.p_max = p_max;
   for (int p = 0; p <= STIV_MAX_P; ++p) A.ytab[p] = p >= 1 && p <= p_max ? h->ytab[p] : nullptr;
-  // 2 stages, plus 64 KB that no copy writes: every address a descriptor can
-  // form from these tiles stays inside the allocation
-  size_t smem = 3 * (size_t)STAGE_BYTES + 1024;
+  size_t smem = (size_t)NSTAGE * STAGE_BYTES + 1024;
   STIV_CUDA(h, cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   long long tiles_bound = max_ntn * tc_mtiles(p_max);
   int grid = (int)(tiles_bound < sms ? tiles_bound : sms);
-  gemm_kernel<<<grid, 128, smem, st>>>(A);
+  gemm_kernel<<<grid, GEMM_THREADS, smem, st>>>(A);
   STIV_LAUNCH(h);
   return STIV_OK;
 }
