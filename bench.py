@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=None, help="scene seed (default: the workload's own)")
+    ap.add_argument("--workload", default="1440", choices=["1440", "4096", "256", "64"],
+                    help="1440: 58%% lattice, p=16->32 (default); 4096: 40%%, p in {8,12,16}, batched uneven "
+                         "orders; 256: 50%%, p=12->24; 64: 30%% random, p=16->32")
     ap.add_argument("--cells", default=None,
                     help="smaller piece of the 58%% lattice (e.g. 6,6,2) for profiling; default: the 1440 scene")
     ap.add_argument("--no-e2e", action="store_true")
@@ -195,13 +198,23 @@ def oracle_sample(sc, target_s: float, rng_seed: int = 0):
     return nv, secs, osc.threads, desc
 
 
+def make_scene(args, seed):
+    from paper_1812_04719_gb300 import scenegen as G
+    if args.cells:
+        return G.scene_lattice58(tuple(int(x) for x in args.cells.split(",")), seed=seed)
+    return {"1440": G.scene_1440, "4096": G.scene_4096, "256": G.scene_256, "64": G.scene_64}[args.workload](seed=seed)
+
+
+def default_seed(args):
+    return {"1440": 3, "4096": 4, "256": 5, "64": 2}[args.workload] if args.seed is None else args.seed
+
+
 # ---------------------------------------------------------------------------
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle, timed on this host's cores."""
     if rank != 0:
         return
-    from paper_1812_04719_gb300 import scenegen as G
-    sc = G.scene_1440(seed=args.seed)
+    sc = make_scene(args, default_seed(args))
     osc = OracleScene(sc)
     threads = osc.threads
     budget = max(2.0, 150.0 / max(args.steps + args.warmup, 1))
@@ -239,10 +252,7 @@ def run_ours(args, rank, world, local):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     prec = S.STIV_MIXED if args.precision == "mixed" else S.STIV_FP64
-    if args.cells:
-        sc = G.scene_lattice58(tuple(int(x) for x in args.cells.split(",")), seed=args.seed + rank)
-    else:
-        sc = G.scene_1440(seed=args.seed + rank)
+    sc = make_scene(args, default_seed(args) + rank)
     eng = S.Stiv.for_scene(sc, precision=prec, pair_cap=8192, contact_cap=1 << 20, device=dev)
     ds = S.DeviceScene.from_scene(sc, precision=prec, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -381,7 +391,8 @@ def run_ours(args, rank, world, local):
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if prec == S.STIV_FP64 else "f32+f64",
                 "data": "synthetic",
-                "config": {"workload": sc.name, "n_vesicles": sc.n, "p": 16, "P": 32,
+                "config": {"workload": sc.name, "n_vesicles": sc.n, "p": sorted(set(int(x) for x in sc.p)),
+                           "P": sorted(set(int(x) for x in sc.P)),
                            "precision": args.precision, "l2": "flushed (256 MB write) before every timed step",
                            "step": "upsample X0,X1 + boxes + Alg.1 pairs + VF/EE contact tests + V + dV/dX1 "
                                    "+ adjoint to SH coefficients",

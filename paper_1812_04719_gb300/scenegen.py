@@ -408,6 +408,6 @@ def scene_small(n_side=(2, 1, 1), p: int = 4, seed: int = 7, phi: float = 0.55, 
 
 # step sizes (in R0) tuned once so the scenes have the contact density named above
 C1440_TRANS = 0.20
-C4096_TRANS = 0.06
-C4096_FLOW = 0.25
+C4096_TRANS = 0.30
+C4096_FLOW = 2.0
 C256_TRANS = 0.40

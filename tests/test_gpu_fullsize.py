@@ -1,5 +1,6 @@
-"""Parity at the benchmark's full size: the 1440-vesicle 58% lattice workload
-(p = 16 -> 32), run as the benchmark runs it (graph replay of the whole
+"""Parity at the benchmark's full sizes: the 1440-vesicle 58% lattice workload
+(p = 16 -> 32) and the 4096-vesicle 40% workload of uneven orders (p in
+{8, 12, 16}), run as the benchmark runs them (graph replay of the whole
 step).  The whole candidate-pair list is compared with the oracle's all-pairs
 box test bit for bit; contacts, volumes and gradient rows are compared on a
 sample of vesicle pairs that the oracle recomputes one by one."""
@@ -18,10 +19,11 @@ def bits(x):
     return np.ascontiguousarray(x, dtype=np.float64).view(np.int64)
 
 
-@pytest.fixture(scope="module", params=[S.STIV_FP64, S.STIV_MIXED], ids=["fp64", "mixed"])
+@pytest.fixture(scope="module", params=[("1440", S.STIV_FP64), ("1440", S.STIV_MIXED), ("4096", S.STIV_MIXED)],
+                ids=["1440-fp64", "1440-mixed", "4096-mixed"])
 def full(request):
-    prec = request.param
-    sc = G.scene_1440()
+    name, prec = request.param
+    sc = G.scene_1440() if name == "1440" else G.scene_4096()
     eng = S.Stiv.for_scene(sc, precision=prec, pair_cap=8192, contact_cap=1 << 20)
     ds = S.DeviceScene.from_scene(sc, precision=prec)
     for _ in range(3):   # capture, then replays
