@@ -327,7 +327,8 @@ def run_ours(args, rank, world, local):
     dom = max(stage_group, key=stage_group.get)
     peaks, peak_src = load_peaks()
     with open(NARROW_OPS) as f:
-        ops_per_pair = float(json.load(f)["ops_per_prim_pair"])
+        ops_rec = json.load(f)["workloads"]["1440" if args.cells else args.workload]
+    ops_per_pair = float(ops_rec["ops_per_prim_pair"])
     fp64_ms = stage_ms.get("fp64", 0.0)
     roof_fp64 = {"bound": "alu", "kernel": "fp64 (exact contact tests on the filter's survivors)",
                  "achieved": float(counts[S.C_FLOPS]) / (fp64_ms * 1e-3) / 1e9 if fp64_ms > 0 else None,
@@ -341,7 +342,7 @@ def run_ours(args, rank, world, local):
         roof = {"bound": "alu", "achieved": work / (narrow_ms * 1e-3) / 1e9, "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s", "kernel": "narrow phase (patch_pairs + narrow + pieces + fp64)",
                 "units": units, "unit_name": "primitive pairs of the exact swept-box test",
-                "ops_per_unit": ops_per_pair, "work_per_launch": work,
+                "ops_per_unit": ops_per_pair, "ops_per_unit_measured_on": ops_rec["scene"], "work_per_launch": work,
                 "peak_source": "FP64 1.25 TFLOP/s nominal (vector = tensor rate on GB300)"}
     elif dom == "synth":
         work = float(sum(2 * synth_flops(int(p)) for p in sc.p)) if prec == S.STIV_FP64 else 0.0
