@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--cells", default=None,
                     help="smaller piece of the 58%% lattice (e.g. 6,6,2) for profiling; default: the 1440 scene")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
@@ -257,8 +258,10 @@ def run_ours(args, rank, world, local):
     ds = S.DeviceScene.from_scene(sc, precision=prec, device=dev)
     stream = torch.cuda.current_stream(dev)
     st = int(stream.cuda_stream)
-    # size the buffers (grows on overflow), then profile inside the captured graph
+    # size the buffers (grows on overflow), pick launch shapes, then profile
+    # inside the captured graph
     eng.step(ds, grad=True)
+    shapes = None if args.no_autotune else eng.autotune(ds, stream=stream)
     S.stiv_profile(eng.h, True)
     gX = torch.zeros(ds.verts.numel(), dtype=torch.float64, device=dev)
     gcoef = torch.zeros_like(ds.coef)
@@ -398,6 +401,7 @@ def run_ours(args, rank, world, local):
                            "step": "upsample X0,X1 + boxes + Alg.1 pairs + VF/EE contact tests + V + dV/dX1 "
                                    "+ adjoint to SH coefficients",
                            "graph": "CUDA graph replay (upsample+detect+V+dV); adjoint launched after it",
+                           "launch_shapes": shapes,
                            "candidate_pairs": int(counts[S.C_PAIRS]),
                            "contact_pairs": int(counts[S.C_CPAIRS]),
                            "contacts_vf": int(counts[S.C_VF]), "contacts_ee": int(counts[S.C_EE]),

@@ -229,6 +229,27 @@ int stiv_profile_read(stiv_handle* h, int32_t max_names, char* names, int64_t* l
  * if an overflow flag is set, STIV_ERR_INPUT for an input flag, else STIV_OK. */
 int stiv_sync_counts(void* stream, const int64_t* counts_dev, int64_t* counts_host);
 
+/* Launch-shape autotuner (not a step of the method: it changes how the
+ * narrow phase's kernels are launched, never what they compute).  Runs
+ * stiv_detect on the given inputs (same arguments) under candidate launch
+ * shapes, coordinate descent over the STIV_TUNE_* parameters, timing each
+ * with CUDA events (the call synchronises the stream), and keeps the fastest
+ * in the handle for later stiv_detect / stiv_step calls (a captured
+ * stiv_step graph is re-captured).  choice_out (host, may be NULL) gets the
+ * STIV_NTUNE chosen values; best_ms_out (host, may be NULL) the best time.
+ * Outputs (cand, out, counts) hold the last run's results, identical for
+ * every launch shape. */
+enum stiv_tune_param {
+  STIV_TUNE_NARROW_CTAS = 0,   /* narrow-kernel CTAs per SM (<= occupancy limit)  */
+  STIV_TUNE_PIECES_CTAS = 1,   /* piece-test CTAs per SM                          */
+  STIV_TUNE_FP64_BLOCKS = 2,   /* FP64 contact-test blocks per SM                 */
+  STIV_TUNE_PATCH_BLOCKS = 3,  /* patch-pair blocks per SM                        */
+  STIV_NTUNE = 4
+};
+int stiv_autotune(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                  const int64_t* vert_off_dev, const void* verts_dev, const stiv_pairs* cand,
+                  const stiv_contacts* out, int64_t* counts_dev, int32_t* choice_out, double* best_ms_out);
+
 /* Stable LSD radix sort of (key, value) pairs on the low key_bits bits of the
  * 64-bit keys (Alg. 1's check-point sort, on one GPU).  scratch:
  * at least stiv_sort_scratch_bytes(n) bytes of device memory. */

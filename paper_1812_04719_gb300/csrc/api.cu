@@ -315,6 +315,62 @@ extern "C" int stiv_detect(stiv_handle* h, void* stream, int32_t n_ves, int32_t 
   return STIV_OK;
 }
 
+extern "C" int stiv_autotune(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                             const int64_t* vert_off_dev, const void* verts_dev, const stiv_pairs* cand,
+                             const stiv_contacts* out, int64_t* counts_dev, int32_t* choice_out,
+                             double* best_ms_out) {
+  if (!h || !counts_dev) return STIV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  static const int32_t cands[STIV_NTUNE][4] = {{2, 3, 4, 0}, {1, 2, 3, 4}, {4, 8, 16, 32}, {2, 4, 8, 0}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  STIV_CUDA(h, cudaEventCreate(&e0));
+  STIV_CUDA(h, cudaEventCreate(&e1));
+  int64_t host_counts[STIV_NCOUNTS];
+  // one timed run of the detection with the handle's current launch shapes
+  auto timed = [&](float& ms) -> int {
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      if (cudaEventRecord(e0, st) != cudaSuccess) return STIV_ERR_CUDA;
+      int rc = stiv_detect(h, stream, n_ves, p_max, p_dev, vert_off_dev, verts_dev, cand, out, counts_dev);
+      if (rc) return rc;
+      if (cudaEventRecord(e1, st) != cudaSuccess) return STIV_ERR_CUDA;
+      if (cudaEventSynchronize(e1) != cudaSuccess) return STIV_ERR_CUDA;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (t < best) best = t;
+    }
+    ms = best;
+    return stiv_sync_counts(stream, counts_dev, host_counts);
+  };
+  int32_t saved[STIV_NTUNE];
+  for (int k = 0; k < STIV_NTUNE; ++k) saved[k] = h->tune[k];
+  float best_ms = 0.f;
+  int rc = timed(best_ms);   // warm-up with the current shapes (sizes the workspace)
+  if (!rc) rc = timed(best_ms);
+  for (int k = 0; k < STIV_NTUNE && !rc; ++k) {
+    int32_t keep = h->tune[k];
+    for (int c = 0; c < 4 && !rc; ++c) {
+      if (cands[k][c] == 0 || cands[k][c] == keep) continue;
+      h->tune[k] = cands[k][c];
+      float ms = 0.f;
+      rc = timed(ms);
+      if (!rc && ms < best_ms) { best_ms = ms; keep = cands[k][c]; }
+    }
+    h->tune[k] = keep;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    for (int k = 0; k < STIV_NTUNE; ++k) h->tune[k] = saved[k];
+    return rc;
+  }
+  if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; h->graph_key = 0; }
+  stiv_prof_drop_graph(h);
+  if (choice_out) for (int k = 0; k < STIV_NTUNE; ++k) choice_out[k] = h->tune[k];
+  if (best_ms_out) *best_ms_out = best_ms;
+  return STIV_OK;
+}
+
 extern "C" int stiv_sync_counts(void* stream, const int64_t* counts_dev, int64_t* counts_host) {
   if (!counts_dev || !counts_host) return STIV_ERR_ARG;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return STIV_ERR_CUDA;

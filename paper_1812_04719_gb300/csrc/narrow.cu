@@ -1214,7 +1214,8 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
                       const stiv_pairs* cand, detect_ws& w, int num_sms, int p_max) {
   const double* L = h->prm.box_L;
   int blocks = (int)((cand->capacity + 3) / 4);
-  if (blocks > 4 * num_sms) blocks = 4 * num_sms;
+  int pp_mult = h->tune[STIV_TUNE_PATCH_BLOCKS] > 0 ? h->tune[STIV_TUNE_PATCH_BLOCKS] : 4;
+  if (blocks > pp_mult * num_sms) blocks = pp_mult * num_sms;
   if (blocks < 1) blocks = 1;
   int mp = stiv_npatches(2 * p_max);
   size_t psmem = (size_t)4 * 2 * mp * 6 * sizeof(float) + (size_t)4 * 2 * mp * sizeof(unsigned short);
@@ -1244,6 +1245,7 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   STIV_CUDA(h, cudaFuncSetAttribute(nk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   STIV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nk, NW * 32, smem));
+  if (h->tune[STIV_TUNE_NARROW_CTAS] > 0 && h->tune[STIV_TUNE_NARROW_CTAS] < per_sm) per_sm = h->tune[STIV_TUNE_NARROW_CTAS];
   if (per_sm < 1) per_sm = 1;
   {
     STIV_PROF(h, st, "narrow");
@@ -1255,6 +1257,8 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
     STIV_CUDA(h, cudaFuncSetAttribute(pieces_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm2));
     int per_sm2 = 0;
     STIV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, pieces_kernel, PW * 32, psm2));
+    if (h->tune[STIV_TUNE_PIECES_CTAS] > 0 && h->tune[STIV_TUNE_PIECES_CTAS] < per_sm2)
+      per_sm2 = h->tune[STIV_TUNE_PIECES_CTAS];
     if (per_sm2 < 1) per_sm2 = 1;
     STIV_PROF(h, st, "pieces");
     pieces_kernel<<<per_sm2 * num_sms, PW * 32, psm2, st>>>(a);
@@ -1263,7 +1267,8 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   {
     STIV_PROF(h, st, "fp64");
     auto fk = mixed ? fp64_kernel<true> : fp64_kernel<false>;
-    fk<<<num_sms * 16, 128, 0, st>>>(a);
+    int fm = h->tune[STIV_TUNE_FP64_BLOCKS] > 0 ? h->tune[STIV_TUNE_FP64_BLOCKS] : 16;
+    fk<<<num_sms * fm, 128, 0, st>>>(a);
   }
   STIV_LAUNCH(h);
   return STIV_OK;

@@ -38,6 +38,8 @@ struct stiv_handle {
   void* tc_ws;
   size_t tc_ws_bytes;
   int* tc_status;
+  // launch shapes of the narrow phase (0 = default), set by stiv_autotune
+  int32_t tune[STIV_NTUNE];
   void* ws;
   size_t ws_bytes;
   // CUDA graph of stiv_step

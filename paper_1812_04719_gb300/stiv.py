@@ -33,7 +33,8 @@ F_PAIRS_OVERFLOW, F_CONTACTS_OVERFLOW, F_BOX_TOO_SMALL, F_NONFINITE, F_WORK_OVER
 EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_error", "stiv_mesh_topology",
            "stiv_upsample", "stiv_detect", "stiv_stiv", "stiv_stiv_grad", "stiv_grad_scatter",
            "stiv_grad_to_coef", "stiv_step", "stiv_sync_counts", "stiv_sort_scratch_bytes", "stiv_sort_pairs",
-           "stiv_profile", "stiv_profile_read", "stiv_sort_pairs_static"]
+           "stiv_profile", "stiv_profile_read", "stiv_sort_pairs_static", "stiv_autotune"]
+TUNE_NAMES = ("narrow_ctas_per_sm", "pieces_ctas_per_sm", "fp64_blocks_per_sm", "patch_blocks_per_sm")
 SORT_STATIC_MAX = 1 << 20
 
 
@@ -92,6 +93,7 @@ def lib() -> ctypes.CDLL:
     L.stiv_sort_scratch_bytes.restype = ctypes.c_size_t
     L.stiv_sort_pairs.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp, ctypes.c_size_t]
     L.stiv_sort_pairs_static.argtypes = [vp, i64, i32, vp, vp, vp, vp]
+    L.stiv_autotune.argtypes = [vp, vp, i32, i32, vp, vp, vp, P(StivPairs), P(StivContacts), vp, vp, vp]
     L.stiv_profile.argtypes = [vp, i32]
     L.stiv_profile_read.argtypes = [vp, i32, vp, vp, vp, vp]
     _lib = L
@@ -363,6 +365,29 @@ class Stiv:
             _check(rc, "step")
             return self.result(counts, grad)
         raise StivError(STIV_ERR_CAPACITY, "step: capacities kept overflowing")
+
+    def autotune(self, ds: DeviceScene, stream=None, max_retries: int = 8) -> dict:
+        """Pick the narrow phase's launch shapes for this workload (the
+        library times its detection under candidates and keeps the fastest).
+        Returns {parameter: value, "best_ms": detection time}."""
+        st = _stream(stream)
+        self.step(ds, grad=False, stream=stream)      # upsampled vertices and sized buffers
+        choice = np.zeros(len(TUNE_NAMES), dtype=np.int32)
+        best = ctypes.c_double(0.0)
+        for _ in range(max_retries):
+            b = self._buffers(False)
+            cand, out = b.pairs_struct(), b.contacts_struct()
+            rc = lib().stiv_autotune(self.h, st, ds.n, ds.p_max, _ptr(ds.p), _ptr(ds.vert_off), _ptr(ds.verts),
+                                     ctypes.byref(cand), ctypes.byref(out), _ptr(b.counts), choice.ctypes.data,
+                                     ctypes.addressof(best))
+            if rc == STIV_ERR_CAPACITY:
+                self.step(ds, grad=False, stream=stream)   # grows the capacities
+                continue
+            _check(rc, "stiv_autotune")
+            res = {k: int(v) for k, v in zip(TUNE_NAMES, choice)}
+            res["best_ms"] = best.value
+            return res
+        raise StivError(STIV_ERR_CAPACITY, "autotune: capacities kept overflowing")
 
     def result(self, counts, grad: bool) -> dict:
         b = self.buf

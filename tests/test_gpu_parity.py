@@ -239,3 +239,23 @@ def test_contact_order_large_segments():
     assert n > 4096  # more than one shared-memory chunk (4096 entries)
     key = (g["pair"].astype(np.int64) << 32) | (g["type"].astype(np.int64) << 30) | (g["a"].astype(np.int64) << 15) | g["b"]
     assert np.all(np.diff(key) > 0)
+
+
+def test_autotune_keeps_results():
+    """The launch-shape autotuner changes timings only: contacts, times and
+    volumes after tuning equal those before, and the chosen shapes are among
+    the candidates."""
+    sc = G.scene_lattice58((6, 6, 2))
+    eng = S.Stiv.for_scene(sc, pair_cap=2048, contact_cap=1 << 17)
+    ds = S.DeviceScene.from_scene(sc)
+    r0 = {k: (v.cpu().numpy().copy() if torch.is_tensor(v) else v) for k, v in eng.step(ds, grad=True).items()}
+    choice = eng.autotune(ds)
+    assert choice["best_ms"] > 0
+    assert choice["narrow_ctas_per_sm"] in (0, 2, 3, 4) and choice["pieces_ctas_per_sm"] in (0, 1, 2, 3, 4)
+    assert choice["fp64_blocks_per_sm"] in (0, 4, 8, 16, 32) and choice["patch_blocks_per_sm"] in (0, 2, 4, 8)
+    for use_graph in (False, True, True):
+        r1 = eng.step(ds, grad=True, use_graph=use_graph)
+        for k in ("i", "j", "shift", "pair", "type", "a", "b"):
+            assert np.array_equal(r1[k].cpu().numpy(), r0[k]), k
+        assert np.array_equal(bits(r1["tau"].cpu().numpy()), bits(r0["tau"]))
+        assert np.array_equal(r1["V_pair"].cpu().numpy(), r0["V_pair"])
