@@ -230,7 +230,9 @@ int stiv_profile_read(stiv_handle* h, int32_t max_names, char* names, int64_t* l
 int stiv_sync_counts(void* stream, const int64_t* counts_dev, int64_t* counts_host);
 
 /* Launch-shape autotuner (not a step of the method: it changes how the
- * narrow phase's kernels are launched, never what they compute).  Runs
+ * narrow phase's kernels are launched and how deep the certified FP32 piece
+ * test refines before handing a pair to the FP64 test, never what the
+ * detection returns).  Runs
  * stiv_detect on the given inputs (same arguments) under candidate launch
  * shapes, coordinate descent over the STIV_TUNE_* parameters, timing each
  * with CUDA events (the call synchronises the stream), and keeps the fastest
@@ -244,11 +246,15 @@ enum stiv_tune_param {
   STIV_TUNE_PIECES_CTAS = 1,   /* piece-test CTAs per SM                          */
   STIV_TUNE_FP64_BLOCKS = 2,   /* FP64 contact-test blocks per SM                 */
   STIV_TUNE_PATCH_BLOCKS = 3,  /* patch-pair blocks per SM                        */
-  STIV_NTUNE = 4
+  STIV_TUNE_PIECE_LEVELS = 4,  /* refinement levels of the FP32 piece test (2-6)  */
+  STIV_NTUNE = 5
 };
 int stiv_autotune(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
                   const int64_t* vert_off_dev, const void* verts_dev, const stiv_pairs* cand,
                   const stiv_contacts* out, int64_t* counts_dev, int32_t* choice_out, double* best_ms_out);
+/* Set the STIV_NTUNE launch-shape values directly (host array; 0 = default;
+ * STIV_TUNE_PIECE_LEVELS in [1, 6]); STIV_ERR_ARG for a value out of range. */
+int stiv_set_tuning(stiv_handle* h, const int32_t* values);
 
 /* Stable LSD radix sort of (key, value) pairs on the low key_bits bits of the
  * 64-bit keys (Alg. 1's check-point sort, on one GPU).  scratch:

@@ -321,7 +321,7 @@ extern "C" int stiv_autotune(stiv_handle* h, void* stream, int32_t n_ves, int32_
                              double* best_ms_out) {
   if (!h || !counts_dev) return STIV_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  static const int32_t cands[STIV_NTUNE][4] = {{2, 3, 4, 0}, {1, 2, 3, 4}, {4, 8, 16, 32}, {2, 4, 8, 0}};
+  static const int32_t cands[STIV_NTUNE][4] = {{2, 3, 4, 0}, {1, 2, 3, 4}, {4, 8, 16, 32}, {2, 4, 8, 0}, {2, 3, 4, 0}};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   STIV_CUDA(h, cudaEventCreate(&e0));
   STIV_CUDA(h, cudaEventCreate(&e1));
@@ -368,6 +368,16 @@ extern "C" int stiv_autotune(stiv_handle* h, void* stream, int32_t n_ves, int32_
   stiv_prof_drop_graph(h);
   if (choice_out) for (int k = 0; k < STIV_NTUNE; ++k) choice_out[k] = h->tune[k];
   if (best_ms_out) *best_ms_out = best_ms;
+  return STIV_OK;
+}
+
+extern "C" int stiv_set_tuning(stiv_handle* h, const int32_t* values) {
+  if (!h || !values) return STIV_ERR_ARG;
+  for (int k = 0; k < STIV_NTUNE; ++k)
+    if (values[k] < 0 || values[k] > 64 || (k == STIV_TUNE_PIECE_LEVELS && values[k] > 6)) return STIV_ERR_ARG;
+  for (int k = 0; k < STIV_NTUNE; ++k) h->tune[k] = values[k];
+  if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; h->graph_key = 0; }
+  stiv_prof_drop_graph(h);
   return STIV_OK;
 }
 

@@ -83,6 +83,7 @@ struct narrow_args {
   int64_t W;
   int include_ee;
   int exact_only;
+  int nlevel;               // refinement levels of the piece test (<= NLEVEL)
   const float* vorg;
   const float* fprep;
   int64_t fstride;
@@ -917,11 +918,14 @@ __global__ void __launch_bounds__(NW * 32, 4) narrow_kernel(narrow_args a) {
 // stage 3b: the pieces of [0,1] that may hold a root, certified non-contact.
 // A warp takes 32 descriptors; the pieces that need the inside test become
 // (descriptor, piece) tasks spread over the lanes, so that every lane runs the
-// same test; an undecided piece is split once.
+// same test; an undecided piece is split in two, level by level (NLEVEL
+// levels), and a half whose cubic certainly keeps one sign is dropped.
 // ---------------------------------------------------------------------------
 constexpr int PW = 8;          // warps per CTA
-constexpr int NPIECE = 16;     // level-1 pieces of [0, 1]
+constexpr int NPIECE = 16;     // level-0 pieces of [0, 1]
+constexpr int NLEVEL = 6;      // most refinement levels (finest piece: 1 / (16 * 32))
 constexpr int MAXTASK = 512;
+static_assert(NPIECE << (NLEVEL - 1) <= 1024, "piece index fits 10 bits");
 
 struct PieceWarp {
   float x[32][4][3], d[32][4][3];
@@ -972,61 +976,72 @@ __global__ void __launch_bounds__(PW * 32) pieces_kernel(narrow_args a) {
         }
       }
     }
-    // task list of this batch
+    // task list of this batch: (owner lane, piece) of level 0
     int cnt = __popc(mask), off = cnt;
     for (int o = 1; o < 32; o <<= 1) { int v = __shfl_up_sync(0xffffffffu, off, o); if (lane >= o) off += v; }
     int total = __shfl_sync(0xffffffffu, off, 31);
     off -= cnt;
     for (unsigned m = mask; m; m &= m - 1) {
       int p = __ffs(m) - 1;
-      if (off < MAXTASK) W.task[off] = (unsigned short)((lane << 5) | p);
+      if (off < MAXTASK) W.task[off] = (unsigned short)((lane << 10) | p);
       else W.fail[lane] = 1;
       ++off;
     }
-    if (lane == 0) W.ntask2 = 0;
-    __syncwarp();
     if (total > MAXTASK) total = MAXTASK;
+    // adaptive refinement: a piece that may hold a root and whose inside test
+    // is undecided splits in two, down to NLEVEL levels; a half that
+    // certainly holds no root is dropped
+    unsigned short* cur = W.task;
+    unsigned short* nxt = W.task2;
 #pragma unroll 1
-    for (int t0 = 0; t0 < total; t0 += 32) {
-      int t = t0 + lane;
-      if (t < total) {
-        int owner = W.task[t] >> 5, p = W.task[t] & 31;
-        f3 xq[4], dq[4];
-        for (int q = 0; q < 4; ++q) {
-          xq[q] = {W.x[owner][q][0], W.x[owner][q][1], W.x[owner][q][2]};
-          dq[q] = {W.d[owner][q][0], W.d[owner][q][1], W.d[owner][q][2]};
-        }
-        int res = inside_cert(W.kind[owner], xq, dq, p * (1.0f / NPIECE), 1.0f / NPIECE, W.ep[owner], W.ed[owner]);
-        if (res == 2) W.fail[owner] = 1;
-        else if (res == 0) {
-          int k = atomicAdd(&W.ntask2, 2);
-          if (k + 1 < MAXTASK) { W.task2[k] = (unsigned short)((owner << 6) | (2 * p)); W.task2[k + 1] = (unsigned short)((owner << 6) | (2 * p + 1)); }
-          else W.fail[owner] = 1;
-        }
-      }
-    }
-    __syncwarp();
-    int total2 = min(W.ntask2, MAXTASK);
+    for (int level = 0; level < a.nlevel && total > 0; ++level) {
+      if (lane == 0) W.ntask2 = 0;
+      __syncwarp();
+      const float w = (1.0f / NPIECE) * __int_as_float((127 - level) << 23);   // 2^-level / NPIECE
 #pragma unroll 1
-    for (int t0 = 0; t0 < total2; t0 += 32) {
-      int t = t0 + lane;
-      if (t < total2) {
-        int owner = W.task2[t] >> 6, p = W.task2[t] & 63;
-        const float w = 0.5f / NPIECE;
-        float t0p = p * w;
-        float k0 = W.k[owner][0], k1 = W.k[owner][1], k2 = W.k[owner][2], k3 = W.k[owner][3], E = W.E[owner];
-        float f0 = fmaf(fmaf(fmaf(k3, t0p, k2), t0p, k1), t0p, k0);
-        float fp1 = fmaf(fmaf(3.f * k3, t0p, 2.f * k2), t0p, k1);
-        float g1 = w * fp1, g2 = w * w * fmaf(3.f * k3, t0p, k2), g3 = w * w * w * k3;
-        if (!certain_sign4(f0, f0 + g1 * (1.f / 3.f), f0 + (2.f * g1 + g2) * (1.f / 3.f), f0 + g1 + g2 + g3, E)) {
-          f3 xq[4], dq[4];
-          for (int q = 0; q < 4; ++q) {
-            xq[q] = {W.x[owner][q][0], W.x[owner][q][1], W.x[owner][q][2]};
-            dq[q] = {W.d[owner][q][0], W.d[owner][q][1], W.d[owner][q][2]};
+      for (int t0 = 0; t0 < total; t0 += 32) {
+        int t = t0 + lane;
+        if (t < total) {
+          int owner = cur[t] >> 10, idx = cur[t] & 1023;
+          float tl = idx * w;
+          bool may_root = true;
+          if (level > 0) {
+            float k0 = W.k[owner][0], k1 = W.k[owner][1], k2 = W.k[owner][2], k3 = W.k[owner][3], E = W.E[owner];
+            float f0 = fmaf(fmaf(fmaf(k3, tl, k2), tl, k1), tl, k0);
+            float fp1 = fmaf(fmaf(3.f * k3, tl, 2.f * k2), tl, k1);
+            float g1 = w * fp1, g2 = w * w * fmaf(3.f * k3, tl, k2), g3 = w * w * w * k3;
+            may_root = !certain_sign4(f0, f0 + g1 * (1.f / 3.f), f0 + (2.f * g1 + g2) * (1.f / 3.f),
+                                      f0 + g1 + g2 + g3, E);
           }
-          if (inside_cert(W.kind[owner], xq, dq, t0p, w, W.ep[owner], W.ed[owner]) != 1) W.fail[owner] = 1;
+          if (may_root) {
+            f3 xq[4], dq[4];
+            for (int q = 0; q < 4; ++q) {
+              xq[q] = {W.x[owner][q][0], W.x[owner][q][1], W.x[owner][q][2]};
+              dq[q] = {W.d[owner][q][0], W.d[owner][q][1], W.d[owner][q][2]};
+            }
+            int res = inside_cert(W.kind[owner], xq, dq, tl, w, W.ep[owner], W.ed[owner]);
+            if (res == 2) {
+              W.fail[owner] = 1;                       // a contact: the FP64 test decides its time
+            } else if (res == 0) {
+              if (level + 1 == a.nlevel) {
+                W.fail[owner] = 1;
+              } else {
+                int k = atomicAdd(&W.ntask2, 2);
+                if (k + 1 < MAXTASK) {
+                  nxt[k] = (unsigned short)((owner << 10) | (2 * idx));
+                  nxt[k + 1] = (unsigned short)((owner << 10) | (2 * idx + 1));
+                } else {
+                  W.fail[owner] = 1;
+                }
+              }
+            }
+          }
         }
       }
+      __syncwarp();
+      total = min(W.ntask2, MAXTASK);
+      unsigned short* tmp = cur; cur = nxt; nxt = tmp;
+      __syncwarp();
     }
     __syncwarp();
     push_global(a.q2, a.Q2, &a.ctr[15], &a.ctr[STIV_C_STATUS], valid && W.fail[lane], e, lane);
@@ -1234,6 +1249,9 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   a.L[0] = L[0]; a.L[1] = L[1]; a.L[2] = L[2];
   a.ci = cand->i; a.cj = cand->j; a.cs = cand->shift;
   a.work = w.work; a.W = w.W; a.include_ee = h->prm.include_ee; a.exact_only = w.exact_only;
+  a.nlevel = h->tune[STIV_TUNE_PIECE_LEVELS] > 0 ? h->tune[STIV_TUNE_PIECE_LEVELS] : 2;
+  if (a.nlevel > NLEVEL) a.nlevel = NLEVEL;
+  if (a.nlevel < 1) a.nlevel = 1;
   a.vorg = w.vorg; a.fprep = w.fprep; a.fstride = w.fstride;
   a.q3 = w.q3; a.q2 = w.q2; a.Q3 = w.Q3; a.Q2 = w.Q2;
   a.C = w.C;

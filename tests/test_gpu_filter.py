@@ -1,7 +1,8 @@
 """The certified FP32 rejection in the narrow phase changes no result: with
 and without it (stiv_params.exact_only) the contact lists, contact times and
 counts agree bit for bit, on a 144-vesicle piece of the 58% lattice workload
-(p = 16 -> 32) in both precision forms."""
+(p = 16 -> 32) in both precision forms and at the default and deepest
+refinement of the piece test."""
 import numpy as np
 import pytest
 import torch
@@ -13,11 +14,12 @@ from tests.gpu_run import run_gpu
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", [S.STIV_FP64, S.STIV_MIXED])
-def test_filter_is_exact(precision):
+@pytest.mark.parametrize("precision,levels", [(S.STIV_FP64, 2), (S.STIV_MIXED, 2), (S.STIV_FP64, 6)])
+def test_filter_is_exact(precision, levels):
     sc = G.scene_lattice58((6, 6, 2))
     kw = dict(precision=precision, pair_cap=2048, contact_cap=1 << 17)
     eng_f = S.Stiv.for_scene(sc, precision=precision, pair_cap=2048, contact_cap=1 << 17)
+    eng_f.set_tuning(piece_levels=levels)
     eng_x = S.Stiv.for_scene(sc, precision=precision, pair_cap=2048, contact_cap=1 << 17, exact_only=True)
     g_f = run_gpu(sc, eng=eng_f, **kw)
     g_x = run_gpu(sc, eng=eng_x, **kw)

@@ -253,6 +253,7 @@ def test_autotune_keeps_results():
     assert choice["best_ms"] > 0
     assert choice["narrow_ctas_per_sm"] in (0, 2, 3, 4) and choice["pieces_ctas_per_sm"] in (0, 1, 2, 3, 4)
     assert choice["fp64_blocks_per_sm"] in (0, 4, 8, 16, 32) and choice["patch_blocks_per_sm"] in (0, 2, 4, 8)
+    assert choice["piece_levels"] in (0, 2, 3, 4)
     for use_graph in (False, True, True):
         r1 = eng.step(ds, grad=True, use_graph=use_graph)
         for k in ("i", "j", "shift", "pair", "type", "a", "b"):
