@@ -58,6 +58,7 @@ struct PatchSm {
   int vid[NS];                     // global vertex id of each slot (-1: unused)
   const PatchTopo* tp;
   unsigned char vf[MAXV], tf[MAXT], ef[MAXE];
+  float4 vlo[MAXV], vhi[MAXV];     // boxes of the filtered vertices, in vf order
   int nv, nt, ne, nvf, ntf, nef;
   int P, I, J, ves;
   float box[6];
@@ -65,8 +66,8 @@ struct PatchSm {
 
 struct WarpSm {
   PatchSm A, B;
+  float4 elo[MAXE], ehi[MAXE];     // boxes of A's filtered edges, in ef order
   unsigned q1[QCAP];
-  int n1;
   float dx;                        // bound on the FP32 position error in this frame
 };
 
@@ -308,8 +309,10 @@ __device__ __forceinline__ bool fbox_hit(const float* a, const float* b) {
   return a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] && b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
 }
 
-// Compact the primitives of S whose FP32 boxes overlap box ob.
-__device__ void filter_patch(PatchSm& S, const float* ob, int lane) {
+// Compact the primitives of S whose FP32 boxes overlap box ob; the boxes of
+// the kept vertices (and of the kept edges, if elo is given) are stored in
+// the compacted order for the stage-1 loops.
+__device__ void filter_patch(PatchSm& S, const float* ob, int lane, float4* elo, float4* ehi) {
 #pragma unroll 1
   for (int kind = 0; kind < 3; ++kind) {
     int n = kind == 0 ? S.nv : kind == 1 ? S.nt : S.ne;
@@ -318,15 +321,20 @@ __device__ void filter_patch(PatchSm& S, const float* ob, int lane) {
     for (int k0 = 0; k0 < n; k0 += 32) {
       int k = k0 + lane;
       bool hit = false;
+      float b[6];
       if (k < n) {
-        float b[6];
         if (kind == 0) slot_box(S, S.tp->v_slot[k], b);
         else if (kind == 1) tri_box(S, k, b);
         else edge_box(S, k, b);
         hit = fbox_hit(b, ob);
       }
       unsigned m = __ballot_sync(0xffffffffu, hit);
-      if (hit) out[base + __popc(m & ((1u << lane) - 1u))] = (unsigned char)k;
+      if (hit) {
+        int pos = base + __popc(m & ((1u << lane) - 1u));
+        out[pos] = (unsigned char)k;
+        if (kind == 0) { S.vlo[pos] = make_float4(b[0], b[1], b[2], 0.f); S.vhi[pos] = make_float4(b[3], b[4], b[5], 0.f); }
+        if (kind == 2 && elo) { elo[pos] = make_float4(b[0], b[1], b[2], 0.f); ehi[pos] = make_float4(b[3], b[4], b[5], 0.f); }
+      }
       base += __popc(m);
     }
     if (lane == 0) { if (kind == 0) S.nvf = base; else if (kind == 1) S.ntf = base; else S.nef = base; }
@@ -813,7 +821,8 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
           unsigned long long p = (unsigned)SB->vid[sl[2]], q = (unsigned)SB->vid[sl[3]];
           v2 = p < q ? p : q; v3 = p < q ? q : p;
         }
-        desc.x = make_desc(r, kind, prim_gid(*SA, kind == 2 ? 2 : 0, x), prim_gid(*SB, kind == 2 ? 2 : 1, y));
+        // EE edge indices are formed by the FP64 stage for contacts only
+        desc.x = kind == 2 ? make_desc(r, kind, 0, 0) : make_desc(r, kind, (int)v0, prim_gid(*SB, 1, y));
         desc.y = v0 | (v1 << 16) | (v2 << 32) | (v3 << 48);
       }
     }
@@ -822,23 +831,23 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
   else push_global(a.q3, a.Q3, &a.ctr[14], &a.ctr[STIV_C_STATUS], keep, desc, lane);
 }
 
+// Queue the hits of one stage-1 test (n1: the queue length, the same in every
+// lane); 32 queued entries go through stages 2 and 3a.
 __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, int lane, int r, const narrow_args& a,
-                                        long long& nprim) {
+                                        long long& nprim, int& n1) {
   unsigned m = __ballot_sync(0xffffffffu, hit);
   if (!m) return;
-  int n1 = ws.n1;
   if (hit) ws.q1[n1 + __popc(m & ((1u << lane) - 1u))] = entry;
   n1 += __popc(m);
-  __syncwarp();
   if (n1 >= 32) {
+    __syncwarp();
     stage_filter(ws, 32, lane, r, a, nprim);
     unsigned rest = (lane + 32 < n1) ? ws.q1[lane + 32] : 0;
     __syncwarp();
     if (lane + 32 < n1) ws.q1[lane] = rest;
     n1 -= 32;
+    __syncwarp();
   }
-  if (lane == 0) ws.n1 = n1;
-  __syncwarp();
 }
 
 // Stages 1-3a: one warp per patch pair.
@@ -864,10 +873,9 @@ __global__ void __launch_bounds__(NW * 32, 4) narrow_kernel(narrow_args a) {
     int r = (int)(w >> 32), pa = (int)((w >> 16) & 0xFFFF), pb = (int)(w & 0xFFFF);
     stiv_pair_info pi = a.pinfo[r];
     stage_pair<MIXED>(ws, a, topo, pi, pa, pb, lane);
-    filter_patch(ws.A, ws.B.box, lane);
-    filter_patch(ws.B, ws.A.box, lane);
-    if (lane == 0) ws.n1 = 0;
-    __syncwarp();
+    filter_patch(ws.A, ws.B.box, lane, ws.elo, ws.ehi);
+    filter_patch(ws.B, ws.A.box, lane, nullptr, nullptr);
+    int n1 = 0;
     // stage 1: FP32 boxes.  VF: vertices of A vs triangles of B (0), vertices of B vs triangles of A (1)
 #pragma unroll 1
     for (int dir = 0; dir < 2; ++dir) {
@@ -881,11 +889,10 @@ __global__ void __launch_bounds__(NW * 32, 4) narrow_kernel(narrow_args a) {
         tri_box(T, y, tb);
 #pragma unroll 1
         for (int xk = 0; xk < V.nvf; ++xk) {
-          int x = V.vf[xk];
-          float vb[6];
-          slot_box(V, V.tp->v_slot[x], vb);
+          float4 lo = V.vlo[xk], hi = V.vhi[xk];
+          float vb[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
           bool hit = valid && fbox_hit(vb, tb);
-          enqueue(ws, hit, ((unsigned)dir << 16) | ((unsigned)x << 8) | (unsigned)y, lane, r, a, nprim);
+          enqueue(ws, hit, ((unsigned)dir << 16) | ((unsigned)V.vf[xk] << 8) | (unsigned)y, lane, r, a, nprim, n1);
         }
       }
     }
@@ -898,15 +905,14 @@ __global__ void __launch_bounds__(NW * 32, 4) narrow_kernel(narrow_args a) {
         edge_box(ws.B, y, eb);
 #pragma unroll 1
         for (int xk = 0; xk < ws.A.nef; ++xk) {
-          int x = ws.A.ef[xk];
-          float ab[6];
-          edge_box(ws.A, x, ab);
+          float4 lo = ws.elo[xk], hi = ws.ehi[xk];
+          float ab[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
           bool hit = valid && fbox_hit(ab, eb);
-          enqueue(ws, hit, (2u << 16) | ((unsigned)x << 8) | (unsigned)y, lane, r, a, nprim);
+          enqueue(ws, hit, (2u << 16) | ((unsigned)ws.A.ef[xk] << 8) | (unsigned)y, lane, r, a, nprim, n1);
         }
       }
     }
-    int n1 = ws.n1;
+    __syncwarp();
     if (n1 > 0) stage_filter(ws, n1, lane, r, a, nprim);
     item = __shfl_sync(0xffffffffu, next, 0);
   }
@@ -1090,7 +1096,13 @@ __global__ void __launch_bounds__(128) fp64_kernel(narrow_args a) {
       }
       flops += 12;  // displacements
       int st = ccd64(ty == 2 ? KIND_EE : KIND_VF, X0, D, tau, w1, w2, flops);
-      if (st == 1) type = ty;
+      if (st == 1) {
+        type = ty;
+        if (ty == 2) {   // edge indices of the two edges (their vertex ids are ordered)
+          ga = stiv_edge_index(Pij & 0xFFFF, vid[0], vid[1]);
+          gb = stiv_edge_index(Pij >> 16, vid[2], vid[3]);
+        }
+      }
       else if (st == 2) ++ndeg;
     }
     unsigned m = __ballot_sync(0xffffffffu, type >= 0);
