@@ -46,7 +46,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
+                    help="mixed: the precision form (tensor-core 3xTF32 synthesis, FP32 vertices, FP64 detection "
+                         "and V/dV); fp64: the FP64 form")
+    ap.add_argument("--no-fp64-form", action="store_true", help="skip timing the FP64 form beside the mixed one")
     ap.add_argument("--seed", type=int, default=None, help="scene seed (default: the workload's own)")
     ap.add_argument("--workload", default="1440", choices=["1440", "4096", "256", "64"],
                     help="1440: 58%% lattice, p=16->32 (default); 4096: 40%%, p in {8,12,16}, batched uneven "
@@ -240,83 +243,149 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def compare_forms(S, sc, ra, rb, verts_a, verts_b):
+    """Errors of form a (the precision form) against form b (the FP64 form,
+    which the parity tests tie to the FP64 oracle bit for bit)."""
+    import torch
+    out = {}
+    xa = verts_a.double().cpu().numpy(); xb = verts_b.double().cpu().numpy()
+    out["max_abs_dX"] = float(np.abs(xa - xb).max())
+    out["max_abs_X"] = float(np.abs(xb).max())
+
+    def pair_keys(r):
+        i = r["i"].cpu().numpy().astype(np.uint64); j = r["j"].cpu().numpy().astype(np.uint64)
+        s_ = r["shift"].cpu().numpy().astype(np.uint64)
+        return (i << np.uint64(18)) | (j << np.uint64(5)) | s_
+
+    pa, pb = pair_keys(ra), pair_keys(rb)
+    va, vb = ra["V_pair"].cpu().numpy(), rb["V_pair"].cpu().numpy()
+    common, ia, ib = np.intersect1d(pa, pb, return_indices=True)
+    hit = vb[ib] > 0
+    rel = np.abs(va[ia][hit] - vb[ib][hit]) / vb[ib][hit]
+    out["V_pair_max_rel"] = float(rel.max()) if rel.size else 0.0
+    out["V_pair_median_rel"] = float(np.median(rel)) if rel.size else 0.0
+    out["V_pairs_rel_above_1e-3"] = int((rel > 1e-3).sum())
+    # volume-weighted: sum |dV| over all pairs relative to the total volume
+    out["V_sum_abs_dV_over_sum_V"] = float(np.abs(va[ia] - vb[ib]).sum() / max(vb.sum(), 1e-300))
+    out["candidate_pairs_only_in_one_form"] = int(len(pa) + len(pb) - 2 * len(common))
+
+    def contact_keys(r, pk):
+        pr = r["pair"].cpu().numpy()
+        t = r["type"].cpu().numpy().astype(np.uint64)
+        a = r["a"].cpu().numpy().astype(np.uint64); b = r["b"].cpu().numpy().astype(np.uint64)
+        return (pk[pr] << np.uint64(32)) | (t << np.uint64(30)) | (a << np.uint64(15)) | b
+
+    ca, cb = contact_keys(ra, pa), contact_keys(rb, pb)
+    cc, ja, jb = np.intersect1d(ca, cb, return_indices=True)
+    out["contacts_fp64_form"] = int(len(cb))
+    out["contacts_symmetric_difference"] = int(len(ca) + len(cb) - 2 * len(cc))
+    ga = ra["grad"].cpu().numpy().reshape(len(ca), -1)[ja]
+    gb = rb["grad"].cpu().numpy().reshape(len(cb), -1)[jb]
+    nb = np.linalg.norm(gb, axis=1)
+    ok = nb > 0
+    g_rel = np.linalg.norm(ga - gb, axis=1)[ok] / nb[ok]
+    out["grad_row_max_rel"] = float(g_rel.max()) if g_rel.size else 0.0
+    out["grad_row_median_rel"] = float(np.median(g_rel)) if g_rel.size else 0.0
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
     import torch.distributed as dist
     from paper_1812_04719_gb300 import build as B
     B.build()
-    from paper_1812_04719_gb300 import scenegen as G
     from paper_1812_04719_gb300 import stiv as S
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-    prec = S.STIV_MIXED if args.precision == "mixed" else S.STIV_FP64
     sc = make_scene(args, default_seed(args) + rank)
-    eng = S.Stiv.for_scene(sc, precision=prec, pair_cap=8192, contact_cap=1 << 20, device=dev)
-    ds = S.DeviceScene.from_scene(sc, precision=prec, device=dev)
     stream = torch.cuda.current_stream(dev)
     st = int(stream.cuda_stream)
-    # size the buffers (grows on overflow), pick launch shapes, then profile
-    # inside the captured graph
-    eng.step(ds, grad=True)
-    shapes = None if args.no_autotune else eng.autotune(ds, stream=stream)
-    S.stiv_profile(eng.h, True)
-    gX = torch.zeros(ds.verts.numel(), dtype=torch.float64, device=dev)
-    gcoef = torch.zeros_like(ds.coef)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
 
-    def step(r_holder):
-        r = eng.step(ds, grad=True, use_graph=True, stream=stream)
-        b = eng.buf
-        cst = b.contacts_struct()
-        gX.zero_()
-        S.stiv_grad_scatter(eng.h, st, ds.p.data_ptr(), cst, b.counts.data_ptr(), 0, b.grad.data_ptr(),
-                            b.gves.data_ptr(), b.gvid.data_ptr(), ds.vert_off.data_ptr(), gX.data_ptr())
-        S.stiv_grad_to_coef(eng.h, st, ds.n, ds.p_max, ds.p.data_ptr(), ds.coef_off.data_ptr(),
-                            ds.vert_off.data_ptr(), gX.data_ptr(), gcoef.data_ptr())
-        r_holder[0] = r
+    def setup(prec):
+        eng = S.Stiv.for_scene(sc, precision=prec, pair_cap=8192, contact_cap=1 << 20, device=dev)
+        ds = S.DeviceScene.from_scene(sc, precision=prec, device=dev)
+        # size the buffers (grows on overflow), pick launch shapes, then profile
+        # inside the captured graph
+        eng.step(ds, grad=True)
+        shapes = None if args.no_autotune else eng.autotune(ds, stream=stream)
+        S.stiv_profile(eng.h, True)
+        gX = torch.zeros(ds.verts.numel(), dtype=torch.float64, device=dev)
+        gcoef = torch.zeros_like(ds.coef)
 
-    holder = [None]
-    for _ in range(max(args.warmup, 3)):
-        flush.zero_()
-        step(holder)
+        def step(r_holder):
+            r = eng.step(ds, grad=True, use_graph=True, stream=stream)
+            b = eng.buf
+            cst = b.contacts_struct()
+            gX.zero_()
+            S.stiv_grad_scatter(eng.h, st, ds.p.data_ptr(), cst, b.counts.data_ptr(), 0, b.grad.data_ptr(),
+                                b.gves.data_ptr(), b.gvid.data_ptr(), ds.vert_off.data_ptr(), gX.data_ptr())
+            S.stiv_grad_to_coef(eng.h, st, ds.n, ds.p_max, ds.p.data_ptr(), ds.coef_off.data_ptr(),
+                                ds.vert_off.data_ptr(), gX.data_ptr(), gcoef.data_ptr())
+            r_holder[0] = r
+        return eng, ds, step, shapes
+
+    def timed(eng, step, nsteps, clocks=None):
+        holder = [None]
+        for _ in range(max(args.warmup, 3)):
+            flush.zero_()
+            step(holder)
+            torch.cuda.synchronize(dev)
+            S.stiv_profile_read(eng.h)
+        prof_tot = {}
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize(dev)
-        S.stiv_profile_read(eng.h)
-    prof_tot = {}
-    clocks = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    t_wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        step(holder)
-        ev[k][1].record(stream)
+        if clocks:
+            clocks.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        t_wall0 = time.perf_counter()
+        for k in range(nsteps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step(holder)
+            ev[k][1].record(stream)
+            torch.cuda.synchronize(dev)
+            for name, (n, ms) in S.stiv_profile_read(eng.h).items():
+                a = prof_tot.setdefault(name, [0, 0.0])
+                a[0] += n; a[1] += ms
         torch.cuda.synchronize(dev)
-        for name, (n, ms) in S.stiv_profile_read(eng.h).items():
-            a = prof_tot.setdefault(name, [0, 0.0])
-            a[0] += n; a[1] += ms
-    torch.cuda.synchronize(dev)
-    t_wall = time.perf_counter() - t_wall0
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    ms_mean = float(np.mean(step_ms))
-    counts = holder[0]["counts"]
-    # max over ranks of the per-step time
-    if world > 1:
-        t = torch.tensor([ms_mean], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    else:
-        ms_max = ms_mean
+        t_wall = time.perf_counter() - t_wall0
+        if world > 1:
+            dist.barrier()
+        clk = clocks.stop() if clocks else None
+        ms_mean = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
+        # max over ranks of the per-step time
+        if world > 1:
+            t = torch.tensor([ms_mean], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_mean = float(t.item())
+        return ms_mean, prof_tot, holder[0], t_wall, clk
+
+    prec = S.STIV_MIXED if args.precision == "mixed" else S.STIV_FP64
+    eng, ds, step, shapes = setup(prec)
+    ms_max, prof_tot, last, t_wall, clk = timed(eng, step, args.steps, ClockSampler(local))
+    counts = last["counts"]
     value = sc.n * world / (ms_max * 1e-3)
+
+    # the FP64 form on the same workload, and the precision form's errors against it
+    fp64_form = None
+    if prec == S.STIV_MIXED and not args.no_fp64_form:
+        eng64, ds64, step64, shapes64 = setup(S.STIV_FP64)
+        ms64, prof64, last64, _, _ = timed(eng64, step64, args.steps)
+        fp64_form = {"value": sc.n * world / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                     "launch_shapes": shapes64,
+                     "stage_ms": {k: round(v[1] / args.steps, 4) for k, v in
+                                  sorted(prof64.items(), key=lambda x: -x[1][1])}}
+        if rank == 0:
+            ra = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in eng.step(ds, grad=True).items()}
+            rb = eng64.step(ds64, grad=True)
+            torch.cuda.synchronize(dev)
+            fp64_form["precision_form_errors"] = compare_forms(S, sc, ra, rb, ds.verts, ds64.verts)
+        eng64.close()
 
     # roofline of the dominant stage: the narrow phase (four kernels), whose
     # algorithmic work is the FP64 contact test on every primitive pair of the
@@ -407,7 +476,8 @@ def run_ours(args, rank, world, local):
                            "contacts_vf": int(counts[S.C_VF]), "contacts_ee": int(counts[S.C_EE]),
                            "prim_pairs_tested": int(counts[S.C_PRIM]), "patch_pairs": int(counts[S.C_PATCH]),
                            "prim_pairs_fp64": int(counts[S.C_EXACT])},
-                "roofline": roof, "roofline_fp64_kernel": roof_fp64, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "roofline_fp64_kernel": roof_fp64, "fp64_form": fp64_form,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches,
                 "clocks": clk, "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda x: -x[1])},
                 "wall_s": t_wall}
