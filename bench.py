@@ -243,6 +243,22 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest per-step time over all ranks (each rank one GPU running its
+    own replica of the workload); every rank gets the same value."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job vesicle-steps/s: every rank advances its own n_per_rank
+    vesicles per step; the job's step takes the slowest rank's time."""
+    return n_per_rank * world / (ms_max * 1e-3)
+
+
 def compare_forms(S, sc, ra, rb, verts_a, verts_b):
     """Errors of form a (the precision form) against form b (the FP64 form,
     which the parity tests tie to the FP64 oracle bit for bit)."""
@@ -358,18 +374,15 @@ def run_ours(args, rank, world, local):
             dist.barrier()
         clk = clocks.stop() if clocks else None
         ms_mean = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
-        # max over ranks of the per-step time
         if world > 1:
-            t = torch.tensor([ms_mean], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_mean = float(t.item())
+            ms_mean = max_over_ranks(ms_mean, dev)
         return ms_mean, prof_tot, holder[0], t_wall, clk
 
     prec = S.STIV_MIXED if args.precision == "mixed" else S.STIV_FP64
     eng, ds, step, shapes = setup(prec)
     ms_max, prof_tot, last, t_wall, clk = timed(eng, step, args.steps, ClockSampler(local))
     counts = last["counts"]
-    value = sc.n * world / (ms_max * 1e-3)
+    value = job_throughput(sc.n, world, ms_max)
 
     # the FP64 form on the same workload, and the precision form's errors against it
     fp64_form = None
