@@ -9,7 +9,8 @@
 //   3. each box lists the cells it overlaps (an exact cell-range enumeration
 //      standing in for the check points of Alg. 1), keyed by the
 //      Morton id of the (wrapped) cell;
-//   4. stable radix sort by Morton id (Alg. 1, check-point sort);
+//   4. stable radix sort by Morton id (Alg. 1, check-point sort; 24-bit keys:
+//      at most 256 wrapped cells per axis);
 //   5. all box pairs within a cell: the image shift follows from the unwrapped
 //      cell coordinates, then bbiCheck in FP64 (Alg. 1, per-cell loop);
 //   6. sort + unique (Alg. 1, final step) -> pairs (i < j, shift), ascending.
@@ -32,21 +33,25 @@ __device__ __forceinline__ double vload(const void* X, int mixed, size_t i) {
 __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, const int64_t* voff, const void* X,
                                                     int mixed, double dm, double Lx, double Ly, double Lz,
                                                     double* vbox, float* pbox, int pstride, float* vorg,
-                                                    float* fprep, int64_t fstride, int64_t* ctr) {
+                                                    float* fprep, int64_t fstride, int64_t* ctr, size_t vb_cap) {
+  extern __shared__ float vbs[];   // [6][nv]: swept FP32 box of each vertex (rounded outward), if it fits
   int v = blockIdx.x;
   int P = 2 * pv[v], nv = stiv_nverts(P);
+  bool use_sm = (size_t)6 * nv <= vb_cap;
   const size_t base = voff[v];
   __shared__ double red[6][256];
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   bool bad = false;
   for (int k = threadIdx.x; k < nv; k += blockDim.x)
-    for (int t = 0; t < 2; ++t)
-      for (int c = 0; c < 3; ++c) {
-        double x = vload(X, mixed, base + (size_t)(t * 3 + c) * nv + k);
-        if (!finite_d(x)) bad = true;
-        lo[c] = fmin(lo[c], x);
-        hi[c] = fmax(hi[c], x);
-      }
+    for (int c = 0; c < 3; ++c) {
+      double x0 = vload(X, mixed, base + (size_t)c * nv + k);
+      double x1 = vload(X, mixed, base + (size_t)(3 + c) * nv + k);
+      if (!finite_d(x0) || !finite_d(x1)) bad = true;
+      double a = fmin(x0, x1), b = fmax(x0, x1);
+      lo[c] = fmin(lo[c], a);
+      hi[c] = fmax(hi[c], b);
+      if (use_sm) { vbs[c * nv + k] = __double2float_rd(a); vbs[(3 + c) * nv + k] = __double2float_ru(b); }
+    }
   for (int c = 0; c < 3; ++c) { red[c][threadIdx.x] = lo[c]; red[3 + c][threadIdx.x] = hi[c]; }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_NONFINITE);
   for (int s = 128; s > 0; s >>= 1) {
@@ -91,8 +96,39 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
     f4[2 * k] = make_float4(xo[0], xo[1], xo[2], 0.f);
     f4[2 * k + 1] = make_float4(dd[0], dd[1], dd[2], 0.f);
   }
-  // patch boxes: vertex rows [I*BR, min(I*BR+BR, P)], columns [J*BC, J*BC+ncol] (wrapping), poles
+  // patch boxes: vertex rows [I*BR, min(I*BR+BR, P)], columns [J*BC, J*BC+ncol] (wrapping), poles.
+  // From the per-vertex FP32 boxes in shared memory when they fit: rounding
+  // outward is monotone, so the result equals rounding the FP64 min / max.
   int nbr = stiv_nband_blocks(P), nbc = stiv_ncol_blocks(P), W = 2 * P;
+  __syncthreads();
+  if (use_sm) {
+    for (int patch = threadIdx.x; patch < nbr * nbc; patch += blockDim.x) {
+      int I = patch / nbc, J = patch % nbc;
+      int r0 = I * STIV_BR, r1 = min(r0 + STIV_BR, P);
+      int c0 = J * STIV_BC, nc = min(STIV_BC, W - c0);
+      float plo[3] = {INFINITY, INFINITY, INFINITY}, phi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int r = r0; r <= r1; ++r)
+        for (int cc = 0; cc <= nc; ++cc) {
+          int col = c0 + cc; if (col >= W) col -= W;
+          int vid = r * W + col;
+          for (int c = 0; c < 3; ++c) {
+            plo[c] = fminf(plo[c], vbs[c * nv + vid]);
+            phi[c] = fmaxf(phi[c], vbs[(3 + c) * nv + vid]);
+          }
+        }
+      for (int pole = 0; pole < 2; ++pole) {
+        if ((pole == 0 && I != 0) || (pole == 1 && I != nbr - 1)) continue;
+        int vid = W * (P + 1) + pole;
+        for (int c = 0; c < 3; ++c) {
+          plo[c] = fminf(plo[c], vbs[c * nv + vid]);
+          phi[c] = fmaxf(phi[c], vbs[(3 + c) * nv + vid]);
+        }
+      }
+      float* B = pbox + ((size_t)v * pstride + patch) * 6;
+      for (int c = 0; c < 3; ++c) { B[c] = plo[c]; B[3 + c] = phi[c]; }
+    }
+    return;
+  }
   for (int patch = threadIdx.x; patch < nbr * nbc; patch += blockDim.x) {
     int I = patch / nbc, J = patch % nbc;
     int r0 = I * STIV_BR, r1 = min(r0 + STIV_BR, P);
@@ -245,7 +281,7 @@ __device__ __forceinline__ bool bbi(const double* a, const double* b) {
 __global__ void cell_pairs_kernel(const int64_t* nrec_dev, int64_t R, const uint64_t* key, const int32_t* val,
                                   const int32_t* rbox, const int32_t* rcell, const double* vbox,
                                   const double* grid, double Lx, double Ly, double Lz, int64_t Q,
-                                  uint64_t* pkey, int32_t* pval, int64_t* ctr) {
+                                  uint64_t* pkey, int32_t* pval, int64_t* ctr, int nb) {
   int64_t nrec = *nrec_dev; if (nrec > R) nrec = R;
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nrec) return;
@@ -281,7 +317,7 @@ __global__ void cell_pairs_kernel(const int64_t* nrec_dev, int64_t R, const uint
     int code = 9 * (s[0] + 1) + 3 * (s[1] + 1) + (s[2] + 1);
     unsigned long long slot = atomicAdd((unsigned long long*)&ctr[9], 1ull);
     if ((int64_t)slot < Q) {
-      pkey[slot] = ((uint64_t)i << 29) | ((uint64_t)j << 5) | (uint64_t)code;
+      pkey[slot] = ((uint64_t)i << (nb + 5)) | ((uint64_t)j << 5) | (uint64_t)code;
       pval[slot] = 0;
     } else {
       atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_WORK_OVERFLOW);
@@ -292,7 +328,7 @@ __global__ void cell_pairs_kernel(const int64_t* nrec_dev, int64_t R, const uint
 // Alg. 1, final step: unique sorted keys -> output pair list; one CTA.
 __global__ void __launch_bounds__(1024) unique_pairs_kernel(const int64_t* nkey_dev, int64_t Q, const uint64_t* key,
                                                             int64_t cap, int32_t* oi, int32_t* oj, int32_t* os,
-                                                            int64_t* ctr) {
+                                                            int64_t* ctr, int nb) {
   __shared__ int32_t part[1024];
   int64_t n = *nkey_dev; if (n > Q) n = Q;
   int64_t per = (n + 1023) / 1024;
@@ -312,8 +348,8 @@ __global__ void __launch_bounds__(1024) unique_pairs_kernel(const int64_t* nkey_
     if (k == 0 || key[k] != key[k - 1]) {
       if (run < cap) {
         uint64_t x = key[k];
-        oi[run] = (int32_t)(x >> 29);
-        oj[run] = (int32_t)((x >> 5) & 0xFFFFFF);
+        oi[run] = (int32_t)(x >> (nb + 5));
+        oj[run] = (int32_t)((x >> 5) & ((1ull << nb) - 1));
         os[run] = (int32_t)(x & 31);
       }
       ++run;
@@ -335,8 +371,13 @@ int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, const int32_t* p_de
   const double* L = h->prm.box_L;
   {
   STIV_PROF(h, st, "boxes");
-  boxes_kernel<<<n, 256, 0, st>>>(n, p_dev, voff, X, mixed, h->prm.d_m, L[0], L[1], L[2], w.vbox, w.pbox,
-                                  w.pstride, w.vorg, w.fprep, w.fstride, ctr);
+  // per-vertex boxes in shared memory up to 96 KB (orders up to P = 44)
+  size_t nv_max = (size_t)(w.fstride / 8);
+  size_t vb_cap = 6 * nv_max * sizeof(float) <= 96 * 1024 ? 6 * nv_max : 0;
+  size_t bsmem = vb_cap * sizeof(float);
+  STIV_CUDA(h, cudaFuncSetAttribute(boxes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+  boxes_kernel<<<n, 256, bsmem, st>>>(n, p_dev, voff, X, mixed, h->prm.d_m, L[0], L[1], L[2], w.vbox, w.pbox,
+                                      w.pstride, w.vorg, w.fprep, w.fstride, ctr, vb_cap);
   }
   {
   STIV_PROF_N(h, st, "cells", 4);
@@ -347,31 +388,35 @@ int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, const int32_t* p_de
                                                     w.rec_box, w.rec_cell, ctr);
   }
   STIV_LAUNCH(h);
-  // records: ctr[8] = count; sort by Morton id (30 bits)
+  // records: ctr[8] = count; sort by Morton id (wrapped cells < 256 per axis: 24 bits)
   int rc;
   {
-  STIV_PROF_N(h, st, "sort_cells", stiv_sort_kernels(30));
-  rc = stiv_sort_pairs_impl(st, w.R, 30, w.rec_key, w.rec_val, w.rec_key2, w.rec_val2, w.sort_scratch,
+  STIV_PROF_N(h, st, "sort_cells", stiv_sort_kernels(24));
+  rc = stiv_sort_pairs_impl(st, w.R, 24, w.rec_key, w.rec_val, w.rec_key2, w.rec_val2, w.sort_scratch,
                                 w.sort_scratch_bytes, &ctr[8]);
   }
+  // candidate keys i << (nb + 5) | j << 5 | shift code: nb bits per vesicle index
+  int nb = 1;
+  while ((1 << nb) < n) ++nb;
+  int pair_bits = 2 * nb + 5;
   if (rc) return rc;
   {
   STIV_PROF(h, st, "cell_pairs");
   cell_pairs_kernel<<<(unsigned)((w.R + 127) / 128), 128, 0, st>>>(&ctr[8], w.R, w.rec_key2, w.rec_val2, w.rec_box,
                                                                    w.rec_cell, w.vbox, w.grid, L[0], L[1], L[2],
-                                                                   w.Q, w.pkey, w.pval, ctr);
+                                                                   w.Q, w.pkey, w.pval, ctr, nb);
   }
   STIV_LAUNCH(h);
   {
-    STIV_PROF_N(h, st, "sort_pairs", stiv_sort_kernels(53));
-    rc = stiv_sort_pairs_impl(st, w.Q, 53, w.pkey, w.pval, w.pkey2, w.pval2, w.sort_scratch, w.sort_scratch_bytes,
-                              &ctr[9]);
+    STIV_PROF_N(h, st, "sort_pairs", stiv_sort_kernels(pair_bits));
+    rc = stiv_sort_pairs_impl(st, w.Q, pair_bits, w.pkey, w.pval, w.pkey2, w.pval2, w.sort_scratch,
+                              w.sort_scratch_bytes, &ctr[9]);
   }
   if (rc) return rc;
   {
     STIV_PROF(h, st, "unique_pairs");
     unique_pairs_kernel<<<1, 1024, 0, st>>>(&ctr[9], w.Q, w.pkey2, cand->capacity, cand->i, cand->j, cand->shift,
-                                            ctr);
+                                            ctr, nb);
   }
   STIV_LAUNCH(h);
   return STIV_OK;
