@@ -197,7 +197,10 @@ int stiv_grad_scatter(stiv_handle* h, void* stream, const int32_t* p_dev, const 
 /* Adjoint of the upsampling: gcoef = S^T gX for the X1 block of every vesicle
  * (S the synthesis matrix of stiv_upsample, grid and poles).  gX_dev in the
  * FP64 vertex layout; gcoef_dev in the coefficient layout (the X0 block is
- * set to zero). */
+ * set to zero).  STIV_FP64: FP64.  STIV_MIXED: on the tensor cores like the
+ * mixed synthesis (3xTF32 split products, FP32 accumulation, FP64 output);
+ * the first call with a given n_ves and p_max allocates scratch in the
+ * handle. */
 int stiv_grad_to_coef(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
                       const int64_t* coef_off_dev, const int64_t* vert_off_dev,
                       const double* gX_dev, double* gcoef_dev);

@@ -185,8 +185,11 @@ extern "C" int stiv_destroy(stiv_handle* h) {
   for (int p = 0; p <= STIV_MAX_P; ++p) {
     if (h->tab_ready[p]) { cudaFree(h->tab[p].leg); cudaFree(h->tab[p].trig); cudaFree(h->tab[p].theta); }
     if (h->ytab[p]) cudaFree(h->ytab[p]);
+    if (h->ytabT[p]) cudaFree(h->ytabT[p]);
   }
   if (h->tc_ws) cudaFree(h->tc_ws);
+  if (h->tc_ws2) cudaFree(h->tc_ws2);
+  if (h->tc_status) cudaFree(h->tc_status);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->ws) cudaFree(h->ws);
   stiv_profile(h, 0);

@@ -518,6 +518,8 @@ extern "C" int stiv_grad_to_coef(stiv_handle* h, void* stream, int32_t n_ves, in
   if (n_ves == 0) return STIV_OK;
   if (!p_dev || !coef_off_dev || !vert_off_dev || !gX_dev || !gcoef_dev) return STIV_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  if (h->prm.precision == STIV_MIXED)
+    return stiv_grad_to_coef_tc(h, st, n_ves, p_max, p_dev, coef_off_dev, vert_off_dev, gX_dev, gcoef_dev);
   adj_args a;
   a.p = p_dev; a.coef_off = coef_off_dev; a.vert_off = vert_off_dev; a.gX = gX_dev; a.gcoef = gcoef_dev;
   for (int p = 0; p <= STIV_MAX_P; ++p) { a.leg[p] = nullptr; a.trig[p] = nullptr; }

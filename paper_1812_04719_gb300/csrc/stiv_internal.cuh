@@ -35,8 +35,11 @@ struct stiv_handle {
   // tensor-core synthesis (STIV_MIXED): synthesis-matrix blocks per order,
   // per-call scratch, and the device status word of its bounded waits
   float* ytab[STIV_MAX_P + 1];
-  void* tc_ws;
+  float* ytabT[STIV_MAX_P + 1];   // transposed blocks for the adjoint
+  void* tc_ws;                    // synthesis scratch (referenced by captured graphs: never reused)
   size_t tc_ws_bytes;
+  void* tc_ws2;                   // adjoint scratch
+  size_t tc_ws2_bytes;
   int* tc_status;
   // launch shapes of the narrow phase (0 = default), set by stiv_autotune
   int32_t tune[STIV_NTUNE];
@@ -145,6 +148,10 @@ int stiv_ensure_tables(stiv_handle* h, cudaStream_t st, int p);
 int stiv_upsample_tc(stiv_handle* h, cudaStream_t st, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
                      const int64_t* coef_off_dev, const double* coef_dev, const int64_t* vert_off_dev,
                      float* verts_dev);
+// Its adjoint (STIV_MIXED): gcoef = S^T gX on the tensor cores.
+int stiv_grad_to_coef_tc(stiv_handle* h, cudaStream_t st, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                         const int64_t* coef_off_dev, const int64_t* vert_off_dev, const double* gX_dev,
+                         double* gcoef_dev);
 int stiv_ws_reserve(stiv_handle* h, size_t bytes);
 int stiv_sort_pairs_impl(cudaStream_t st, int64_t n, int key_bits, const uint64_t* kin, const int32_t* vin,
                          uint64_t* kout, int32_t* vout, void* scratch, size_t scratch_bytes,

@@ -68,10 +68,35 @@ __device__ __forceinline__ float tf32_rn(float x) {
 __device__ __forceinline__ int blk_index(int row, int k) { return (k >> 2) * (TM * 4) + row * 4 + (k & 3); }
 
 // ---------------------------------------------------------------------------
-// Y blocks of order p: [mtile][kblock][hi | lo][8][128][4]
+// Synthesis matrix entry Y(row, q) of order p (grid vertex i * 2P + j or a
+// pole; coefficient n^2 + n + m), from the FP64 Legendre table.
 // ---------------------------------------------------------------------------
+__device__ double ymat(int p, const double* leg, int row, int q) {
+  int P = 2 * p, W = 2 * P, nl = (p + 1) * (p + 2) / 2;
+  int n = (int)sqrt((double)q);
+  while (n * n > q) --n;
+  while ((n + 1) * (n + 1) <= q) ++n;
+  int m = q - n * n - n, am = m < 0 ? -m : m;
+  if (row < W * (P + 1)) {
+    int i = row / W, j = row % W;
+    double L = leg[(size_t)i * nl + n * (n + 1) / 2 + am];
+    double tr = 1.0;
+    if (m != 0) {
+      double sv, cv;
+      sincospi((double)((am * j) % W) / P, &sv, &cv);
+      tr = m > 0 ? cv : sv;
+    }
+    return L * tr;
+  }
+  if (m != 0) return 0.0;
+  int pole = row - W * (P + 1);
+  return leg[(size_t)(P + 1 + pole) * nl + n * (n + 1) / 2];
+}
+
+// Y blocks of order p for the synthesis: rows = vertices, k = q - 1 (the
+// degree-0 column is added in the epilogue): [mtile][kblock][hi | lo][8][128][4]
 __global__ void ytab_kernel(int p, const double* leg, float* ytab) {
-  int P = 2 * p, W = 2 * P, nv = stiv_nverts(P), nc = (p + 1) * (p + 1), nl = (p + 1) * (p + 2) / 2;
+  int nv = stiv_nverts(2 * p), nc = (p + 1) * (p + 1);
   int MT = tc_mtiles(p), KB = tc_kblocks(p);
   int64_t total = (int64_t)MT * KB * TM * TK;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -81,27 +106,31 @@ __global__ void ytab_kernel(int p, const double* leg, float* ytab) {
     rest /= TM;
     int kb = (int)(rest % KB), mt = (int)(rest / KB);
     int row = mt * TM + r, q = kb * TK + k + 1;
-    double y = 0.0;
-    if (row < nv && q < nc) {
-      int n = (int)sqrt((double)q);
-      while (n * n > q) --n;
-      while ((n + 1) * (n + 1) <= q) ++n;
-      int m = q - n * n - n, am = m < 0 ? -m : m;
-      if (row < W * (P + 1)) {
-        int i = row / W, j = row % W;
-        double L = leg[(size_t)i * nl + n * (n + 1) / 2 + am];
-        double tr = 1.0;
-        if (m != 0) {
-          double sv, cv;
-          sincospi((double)((am * j) % W) / P, &sv, &cv);
-          tr = m > 0 ? cv : sv;
-        }
-        y = L * tr;
-      } else if (m == 0) {
-        int pole = row - W * (P + 1);
-        y = leg[(size_t)(P + 1 + pole) * nl + n * (n + 1) / 2];
-      }
-    }
+    double y = (row < nv && q < nc) ? ymat(p, leg, row, q) : 0.0;
+    float yf = (float)y, hi = tf32_rn(yf), lo = tf32_rn(yf - hi);
+    float* blk = ytab + ((size_t)mt * KB + kb) * (2 * BLK_FLOATS);
+    blk[blk_index(r, k)] = hi;
+    blk[BLK_FLOATS + blk_index(r, k)] = lo;
+  }
+}
+
+// Transposed blocks for the adjoint: rows = coefficients q (all, degree 0
+// included), k = vertices: [mtile over q][kblock over vertices][hi | lo][8][128][4]
+__host__ __device__ inline int tcA_mtiles(int p) { return ((p + 1) * (p + 1) + TM - 1) / TM; }
+__host__ __device__ inline int tcA_kblocks(int p) { return (stiv_nverts(2 * p) + TK - 1) / TK; }
+
+__global__ void ytabT_kernel(int p, const double* leg, float* ytab) {
+  int nv = stiv_nverts(2 * p), nc = (p + 1) * (p + 1);
+  int MT = tcA_mtiles(p), KB = tcA_kblocks(p);
+  int64_t total = (int64_t)MT * KB * TM * TK;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int k = (int)(t % TK);
+    int64_t rest = t / TK;
+    int r = (int)(rest % TM);
+    rest /= TM;
+    int kb = (int)(rest % KB), mt = (int)(rest / KB);
+    int q = mt * TM + r, row = kb * TK + k;
+    double y = (row < nv && q < nc) ? ymat(p, leg, row, q) : 0.0;
     float yf = (float)y, hi = tf32_rn(yf), lo = tf32_rn(yf - hi);
     float* blk = ytab + ((size_t)mt * KB + kb) * (2 * BLK_FLOATS);
     blk[blk_index(r, k)] = hi;
@@ -114,6 +143,8 @@ __global__ void ytab_kernel(int p, const double* leg, float* ytab) {
 // ---------------------------------------------------------------------------
 struct tc_group {
   int cnt, list_off, ntn, mt, kb, tile_off;  // vesicles, list offset, column tiles, row tiles, k blocks, first tile
+  int nrows;                                 // rows of the output (vertices, or coefficients for the adjoint)
+  int pad;
   long long boff;                            // first B block of the group
   long long coff;                            // first column (of all groups' padded columns)
 };
@@ -125,7 +156,10 @@ struct tc_colinfo {
   float pad;
 };
 
-__global__ void group_kernel(int n, int p_max, const int32_t* pv, tc_group* g, int* ntiles, int* list) {
+// adjoint = 0: synthesis (6 fields per vesicle, rows = vertices, k = q - 1);
+// adjoint = 1: transposed synthesis of the X1 gradient (3 fields per vesicle,
+// rows = coefficients, k = vertices)
+__global__ void group_kernel(int n, int p_max, const int32_t* pv, tc_group* g, int* ntiles, int* list, int adjoint) {
   __shared__ int cnt[STIV_MAX_P + 1], fill[STIV_MAX_P + 1], off[STIV_MAX_P + 1];
   for (int p = threadIdx.x; p <= STIV_MAX_P; p += blockDim.x) { cnt[p] = 0; fill[p] = 0; }
   __syncthreads();
@@ -141,9 +175,11 @@ __global__ void group_kernel(int n, int p_max, const int32_t* pv, tc_group* g, i
       tc_group G;
       G.cnt = (p >= 1 && p <= p_max) ? cnt[p] : 0;
       G.list_off = lo;
-      G.ntn = (6 * G.cnt + TN - 1) / TN;
-      G.mt = p >= 1 ? tc_mtiles(p) : 0;
-      G.kb = p >= 1 ? tc_kblocks(p) : 0;
+      G.ntn = ((adjoint ? 3 : 6) * G.cnt + TN - 1) / TN;
+      G.mt = p < 1 ? 0 : adjoint ? tcA_mtiles(p) : tc_mtiles(p);
+      G.kb = p < 1 ? 0 : adjoint ? tcA_kblocks(p) : tc_kblocks(p);
+      G.nrows = p < 1 ? 0 : adjoint ? (p + 1) * (p + 1) : stiv_nverts(2 * p);
+      G.pad = 0;
       G.tile_off = to;
       G.boff = bo;
       G.coff = co;
@@ -202,6 +238,56 @@ __global__ void bprep_kernel(int p_max, const tc_group* g, const int* list, cons
       }
     }
   }
+}
+
+// B blocks of the adjoint: column c of order group p is coordinate (c % 3) of
+// the X1 block of vesicle list[c / 3] of the gradient gX (FP64, vertex
+// layout); k = vertex.  Thread per (group, column, k block, 4 vertices).
+__global__ void gprep_kernel(int p_max, const tc_group* g, const int* list, const int64_t* coef_off,
+                             const int64_t* vert_off, const double* gX, float* bblk, tc_colinfo* ci) {
+  for (int p = 1; p <= p_max; ++p) {
+    tc_group G = g[p];
+    if (G.cnt == 0) continue;
+    int nc = (p + 1) * (p + 1), nv = stiv_nverts(2 * p);
+    long long ncols = (long long)G.ntn * TN;
+    long long items = ncols * G.kb * (TK / 4);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < items;
+         t += (long long)gridDim.x * blockDim.x) {
+      int kg = (int)(t % (TK / 4));
+      long long rest = t / (TK / 4);
+      long long c = rest % ncols;
+      int kb = (int)(rest / ncols);
+      int v = c / 3 < G.cnt ? list[G.list_off + c / 3] : -1;
+      int f = (int)(c % 3);
+      float hi[4], lo[4];
+      for (int e = 0; e < 4; ++e) {
+        int row = kb * TK + kg * 4 + e;
+        float x = 0.f;
+        if (v >= 0 && row < nv) x = __double2float_rn(gX[vert_off[v] + (size_t)(3 + f) * nv + row]);
+        hi[e] = tf32_rn(x);
+        lo[e] = tf32_rn(x - hi[e]);
+      }
+      int nt = (int)(c / TN), r = (int)(c % TN);
+      float* blk = bblk + ((size_t)G.boff + (size_t)nt * G.kb + kb) * (2 * BLK_FLOATS);
+      *(float4*)(blk + blk_index(r, kg * 4)) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      *(float4*)(blk + BLK_FLOATS + blk_index(r, kg * 4)) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      if (kb == 0 && kg == 0) {
+        tc_colinfo info;
+        info.dst = v >= 0 ? (long long)coef_off[v] + (long long)(3 + f) * nc : -1;
+        info.bias = 0.f;
+        info.pad = 0.f;
+        ci[(size_t)G.coff + c] = info;
+      }
+    }
+  }
+}
+
+// X0 blocks of the coefficient gradient are zero (X0 is a constant of the step).
+__global__ void zero_x0_kernel(int n, const int32_t* pv, const int64_t* coef_off, double* gcoef) {
+  int v = blockIdx.x;
+  if (v >= n) return;
+  int nc = (pv[v] + 1) * (pv[v] + 1);
+  for (int k = threadIdx.x; k < 3 * nc; k += blockDim.x) gcoef[coef_off[v] + k] = 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -280,7 +366,7 @@ struct gemm_args {
   const float* ytab[STIV_MAX_P + 1];
   const float* bblk;
   const tc_colinfo* ci;
-  float* X;
+  void* X;              // float (synthesis) or double (adjoint) output
   int* status;
   int p_max;
 };
@@ -300,6 +386,7 @@ __device__ __forceinline__ bool tile_of(const tc_group* G, int p_max, int tile, 
   return true;
 }
 
+template <typename OUT>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(gemm_args a) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ tc_group G[STIV_MAX_P + 1];
@@ -400,7 +487,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(gemm_args a) {
       if (!mbar_wait(acc_full(b), (tc / NACC) & 1)) { ok = false; break; }
       tc_fence_after();
       int row = mt * TM + q * 32 + lane;
-      int nv = stiv_nverts(2 * p);
+      int nrows = G[p].nrows;
+      OUT* X = (OUT*)a.X;
       const tc_colinfo* cinfo = a.ci + (size_t)G[p].coff + (size_t)nt * TN;
 #pragma unroll 1
       for (int c0 = 0; c0 < TN; c0 += 16) {
@@ -411,7 +499,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(gemm_args a) {
         for (int i = 0; i < 16; ++i) {
           long long dst = __shfl_sync(0xffffffffu, mine.dst, i);
           float bias = __shfl_sync(0xffffffffu, mine.bias, i);
-          if (dst >= 0 && row < nv) a.X[dst + row] = v[i] + bias;
+          if (dst >= 0 && row < nrows) X[dst + row] = (OUT)(v[i] + bias);
         }
       }
       tc_fence_before();
@@ -444,6 +532,27 @@ static int ensure_ytab(stiv_handle* h, cudaStream_t st, int p) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Device status word of the bounded waits (word 0) and the tile count of the
+// synthesis (word 1) and of the adjoint (word 2); allocated once per handle.
+static int ensure_status(stiv_handle* h, cudaStream_t st) {
+  if (h->tc_status) return STIV_OK;
+  STIV_CUDA(h, cudaMalloc(&h->tc_status, 256));
+  STIV_CUDA(h, cudaMemsetAsync(h->tc_status, 0, 256, st));
+  return STIV_OK;
+}
+
+// Transposed Y blocks of order p for the adjoint (built once).
+static int ensure_ytabT(stiv_handle* h, cudaStream_t st, int p) {
+  if (h->ytabT[p]) return STIV_OK;
+  int rc = stiv_ensure_tables(h, st, p);
+  if (rc) return rc;
+  size_t bytes = (size_t)tcA_mtiles(p) * tcA_kblocks(p) * BLK_BYTES;
+  STIV_CUDA(h, cudaMalloc(&h->ytabT[p], bytes));
+  ytabT_kernel<<<1024, 256, 0, st>>>(p, h->tab[p].leg, h->ytabT[p]);
+  STIV_LAUNCH(h);
+  return STIV_OK;
+}
+
 int stiv_upsample_tc(stiv_handle* h, cudaStream_t st, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
                      const int64_t* coef_off_dev, const double* coef_dev, const int64_t* vert_off_dev,
                      float* verts_dev) {
@@ -454,8 +563,9 @@ int stiv_upsample_tc(stiv_handle* h, cudaStream_t st, int32_t n_ves, int32_t p_m
   // scratch bounds from n_ves and p_max only (sizes must not depend on device data)
   long long max_ntn = (6LL * n_ves + TN - 1) / TN + p_max;
   long long max_blocks = max_ntn * tc_kblocks(p_max);
-  size_t o_status = 0;
-  size_t o_g = 256;
+  int rc0 = ensure_status(h, st);
+  if (rc0) return rc0;
+  size_t o_g = 0;
   size_t o_list = align256(o_g + sizeof(tc_group) * (STIV_MAX_P + 1));
   size_t o_ci = align256(o_list + sizeof(int) * (size_t)n_ves);
   size_t o_b = align256(o_ci + sizeof(tc_colinfo) * (size_t)max_ntn * TN);
@@ -463,30 +573,76 @@ int stiv_upsample_tc(stiv_handle* h, cudaStream_t st, int32_t n_ves, int32_t p_m
   if (total > h->tc_ws_bytes) {
     if (h->tc_ws) { STIV_CUDA(h, cudaFree(h->tc_ws)); h->tc_ws = nullptr; h->tc_ws_bytes = 0; }
     STIV_CUDA(h, cudaMalloc(&h->tc_ws, total));
-    STIV_CUDA(h, cudaMemsetAsync(h->tc_ws, 0, 256, st));
     h->tc_ws_bytes = total;
   }
   char* w = (char*)h->tc_ws;
-  int* status = (int*)(w + o_status);
+  int* status = h->tc_status;
   int* ntiles = status + 1;
   tc_group* g = (tc_group*)(w + o_g);
   int* list = (int*)(w + o_list);
   tc_colinfo* ci = (tc_colinfo*)(w + o_ci);
   float* bblk = (float*)(w + o_b);
-  h->tc_status = status;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   STIV_PROF_N(h, st, "synth", 3);
-  group_kernel<<<1, 1024, 0, st>>>(n_ves, p_max, p_dev, g, ntiles, list);
+  group_kernel<<<1, 1024, 0, st>>>(n_ves, p_max, p_dev, g, ntiles, list, 0);
   bprep_kernel<<<sms * 8, 256, 0, st>>>(p_max, g, list, coef_off_dev, coef_dev, vert_off_dev, bblk, ci);
   gemm_args A;
   A.g = g; A.ntiles = ntiles; A.bblk = bblk; A.ci = ci; A.X = verts_dev; A.status = status; A.p_max = p_max;
   for (int p = 0; p <= STIV_MAX_P; ++p) A.ytab[p] = p >= 1 && p <= p_max ? h->ytab[p] : nullptr;
   size_t smem = (size_t)NSTAGE * STAGE_BYTES + 1024;
-  STIV_CUDA(h, cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  STIV_CUDA(h, cudaFuncSetAttribute(gemm_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   long long tiles_bound = max_ntn * tc_mtiles(p_max);
   int grid = (int)(tiles_bound < sms ? tiles_bound : sms);
-  gemm_kernel<<<grid, GEMM_THREADS, smem, st>>>(A);
+  gemm_kernel<float><<<grid, GEMM_THREADS, smem, st>>>(A);
+  STIV_LAUNCH(h);
+  return STIV_OK;
+}
+
+// Adjoint of the mixed-form synthesis on the tensor cores: gcoef (X1 block) =
+// Y^T gX (X1 block), 3xTF32 products accumulated in FP32; X0 block zero.
+int stiv_grad_to_coef_tc(stiv_handle* h, cudaStream_t st, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                         const int64_t* coef_off_dev, const int64_t* vert_off_dev, const double* gX_dev,
+                         double* gcoef_dev) {
+  for (int p = 1; p <= p_max; ++p) {
+    int rc = ensure_ytabT(h, st, p);
+    if (rc) return rc;
+  }
+  int rc0 = ensure_status(h, st);
+  if (rc0) return rc0;
+  long long max_ntn = (3LL * n_ves + TN - 1) / TN + p_max;
+  long long max_blocks = max_ntn * tcA_kblocks(p_max);
+  size_t o_g = 0;
+  size_t o_list = align256(o_g + sizeof(tc_group) * (STIV_MAX_P + 1));
+  size_t o_ci = align256(o_list + sizeof(int) * (size_t)n_ves);
+  size_t o_b = align256(o_ci + sizeof(tc_colinfo) * (size_t)max_ntn * TN);
+  size_t total = o_b + (size_t)max_blocks * BLK_BYTES;
+  if (total > h->tc_ws2_bytes) {
+    if (h->tc_ws2) { STIV_CUDA(h, cudaFree(h->tc_ws2)); h->tc_ws2 = nullptr; h->tc_ws2_bytes = 0; }
+    STIV_CUDA(h, cudaMalloc(&h->tc_ws2, total));
+    h->tc_ws2_bytes = total;
+  }
+  char* w = (char*)h->tc_ws2;
+  int* status = h->tc_status;
+  int* ntiles = status + 2;
+  tc_group* g = (tc_group*)(w + o_g);
+  int* list = (int*)(w + o_list);
+  tc_colinfo* ci = (tc_colinfo*)(w + o_ci);
+  float* bblk = (float*)(w + o_b);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  STIV_PROF_N(h, st, "grad_to_coef", 4);
+  zero_x0_kernel<<<n_ves, 256, 0, st>>>(n_ves, p_dev, coef_off_dev, gcoef_dev);
+  group_kernel<<<1, 1024, 0, st>>>(n_ves, p_max, p_dev, g, ntiles, list, 1);
+  gprep_kernel<<<sms * 8, 256, 0, st>>>(p_max, g, list, coef_off_dev, vert_off_dev, gX_dev, bblk, ci);
+  gemm_args A;
+  A.g = g; A.ntiles = ntiles; A.bblk = bblk; A.ci = ci; A.X = gcoef_dev; A.status = status; A.p_max = p_max;
+  for (int p = 0; p <= STIV_MAX_P; ++p) A.ytab[p] = p >= 1 && p <= p_max ? h->ytabT[p] : nullptr;
+  size_t smem = (size_t)NSTAGE * STAGE_BYTES + 1024;
+  STIV_CUDA(h, cudaFuncSetAttribute(gemm_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  long long tiles_bound = max_ntn * tcA_mtiles(p_max);
+  int grid = (int)(tiles_bound < sms ? tiles_bound : sms);
+  gemm_kernel<double><<<grid, GEMM_THREADS, smem, st>>>(A);
   STIV_LAUNCH(h);
   return STIV_OK;
 }

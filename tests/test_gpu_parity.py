@@ -212,6 +212,42 @@ def test_adjoint_matches_oracle(orc, name):
             assert np.abs(got[1, d] - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
 
 
+@pytest.mark.parametrize("name", ["cluster_p4", "uneven_p234", "lattice_144_p16"])
+def test_adjoint_mixed_tensor_cores(orc, name):
+    """STIV_MIXED adjoint (tensor cores, 3xTF32 products, FP32 accumulation over
+    the vertices) against the FP64 oracle adjoint.  Bound per coefficient:
+    2^-12 sum_rows |Y| |gX| <= 2^-12 Ymax sum_rows |gX| (accumulation of n_v
+    terms in FP32 at worst n_v 2^-24 of their absolute sum, plus the split
+    products' 2^-22 each); the measured ratio is printed."""
+    sc = G.scene_lattice58((6, 6, 2)) if name == "lattice_144_p16" else SCENES[name]()
+    g = run_gpu(sc, precision=S.STIV_MIXED, pair_cap=2048, contact_cap=1 << 17)
+    eng = g["eng"]
+    ds = g["ds"]
+    rng = np.random.default_rng(4)
+    gX = torch.tensor(rng.normal(size=ds.verts.numel()), dtype=torch.float64, device="cuda")
+    gc = torch.full_like(ds.coef, 7.0)
+    S.stiv_grad_to_coef(eng.h, torch.cuda.current_stream().cuda_stream, ds.n, ds.p_max, ds.p.data_ptr(),
+                        ds.coef_off.data_ptr(), ds.vert_off.data_ptr(), gX.data_ptr(), gc.data_ptr())
+    torch.cuda.synchronize()
+    gXh, gch = gX.cpu().numpy(), gc.cpu().numpy()
+    vo = sc.vert_off()
+    worst = 0.0
+    for v in range(sc.n):
+        p, P = int(sc.p[v]), int(sc.P[v])
+        nv = G.nverts(P)
+        blk = gXh[vo[v]:vo[v] + 6 * nv].reshape(2, 3, nv)
+        got = gch[sc.coef_off[v]:sc.coef_off[v] + 6 * (p + 1) ** 2].reshape(2, 3, -1)
+        assert np.all(got[0] == 0)
+        ymax = np.sqrt((2 * p + 1) / (2 * np.pi))
+        for d in range(3):
+            ref = orc.synth_adjoint(p, P, blk[1, d])
+            scale = ymax * np.abs(blk[1, d]).sum()
+            err = np.abs(got[1, d] - ref).max()
+            assert err <= 2.0 ** -12 * scale, (v, d, err, scale)
+            worst = max(worst, err / scale)
+    print(f"mixed adjoint: max error / (Ymax sum|gX|) = {worst:.3g}")
+
+
 def test_mixed_precision_lists(orc):
     """MIXED: FP32 vertices; the FP64 contact arithmetic on those vertices is
     bit-identical to the oracle run on the same (widened) vertices."""
