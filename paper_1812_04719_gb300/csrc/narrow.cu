@@ -597,16 +597,35 @@ __device__ double bisect64(double k0, double k1, double k2, double k3, double lo
   return lo;
 }
 
+// n / den < 0 for den > 0, decided from the sign of n when the quotient
+// cannot underflow to -0: |n| >= 2^-899 and den < 2^171 give |n / den| >
+// 2^-1070.
+__device__ __forceinline__ bool quot_neg(double n, double den) {
+  long long b = __double_as_longlong(n);
+  return b < 0 && ((b >> 52) & 0x7FF) >= 124 && (__double_as_longlong(den) >> 52) <= 1193;
+}
+// n / den rounds above 1 for positive n, den: n exceeds den by more than 8
+// units in the last place (then n / den > 1 + 2^-50).
+__device__ __forceinline__ bool quot_above1(double n, double den) {
+  long long bn = __double_as_longlong(n), bd = __double_as_longlong(den);
+  return bn > 0 && bn > bd + 8;
+}
+
 // Inside test at the positions Y (VF: xp, x0, x1, x2; EE: p0, p1, q0, q1).
-// 1 inside, 0 outside, -1 degenerate.
+// 1 inside, 0 outside, -1 degenerate.  A quotient whose sign (or excess
+// over 1) is decided by its numerator is not formed when that already
+// decides "outside": the decision equals that of the rounded quotient.
 __device__ int inside64(int kind, const d3* Y, double& w1, double& w2) {
   if (kind == KIND_VF) {
     d3 a = d3_sub(Y[2], Y[1]), b = d3_sub(Y[3], Y[1]), c = d3_sub(Y[0], Y[1]);
     double d00 = d3_dot(a, a), d01 = d3_dot(a, b), d11 = d3_dot(b, b), d20 = d3_dot(c, a), d21 = d3_dot(c, b);
     double den = __fma_rn(d00, d11, -__dmul_rn(d01, d01));
     if (!is_pos(den)) return -1;
-    double b1 = __ddiv_rn(__fma_rn(d11, d20, -__dmul_rn(d01, d21)), den);
-    double b2 = __ddiv_rn(__fma_rn(d00, d21, -__dmul_rn(d01, d20)), den);
+    double n1 = __fma_rn(d11, d20, -__dmul_rn(d01, d21));
+    double n2 = __fma_rn(d00, d21, -__dmul_rn(d01, d20));
+    if (quot_neg(n1, den) || quot_neg(n2, den)) return 0;
+    double b1 = __ddiv_rn(n1, den);
+    double b2 = __ddiv_rn(n2, den);
     double b0 = __dsub_rn(__dsub_rn(1.0, b1), b2);
     w1 = b1; w2 = b2;
     return (!is_neg(b0) && !is_neg(b1) && !is_neg(b2)) ? 1 : 0;
@@ -615,8 +634,11 @@ __device__ int inside64(int kind, const d3* Y, double& w1, double& w2) {
     double A = d3_dot(d1, d1), B = d3_dot(d1, d2), E = d3_dot(d2, d2), C = d3_dot(d1, r), F = d3_dot(d2, r);
     double den = __fma_rn(A, E, -__dmul_rn(B, B));
     if (!is_pos(den)) return -1;
-    double s = __ddiv_rn(__fma_rn(B, F, -__dmul_rn(C, E)), den);
-    double u = __ddiv_rn(__fma_rn(A, F, -__dmul_rn(B, C)), den);
+    double ns = __fma_rn(B, F, -__dmul_rn(C, E));
+    double nu = __fma_rn(A, F, -__dmul_rn(B, C));
+    if (quot_neg(ns, den) || quot_neg(nu, den) || quot_above1(ns, den) || quot_above1(nu, den)) return 0;
+    double s = __ddiv_rn(ns, den);
+    double u = __ddiv_rn(nu, den);
     w1 = s; w2 = u;
     const long long one = 0x3FF0000000000000ll;
     bool s_le1 = is_neg(s) || __double_as_longlong(s) <= one;
