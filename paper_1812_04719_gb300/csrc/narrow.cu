@@ -548,6 +548,40 @@ __device__ __forceinline__ float trunc_f32(double t) {
   return __uint_as_float(((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7FFFFF));
 }
 
+// Double-float (unevaluated sum of two floats) arithmetic for the second
+// sign tier of the bisection.  two_prod is exact with an FMA; two_sum is
+// exact (the library is built without FMA contraction).
+struct dflt { float h, l; };
+__device__ __forceinline__ dflt two_sum(float a, float b) {
+  float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dflt fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dflt df_mul(dflt x, dflt y) {
+  float p = x.h * y.h, e = fmaf(x.h, y.h, -p);
+  e = e + (x.h * y.l + x.l * y.h);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dflt df_add(dflt x, dflt y) {
+  dflt s = two_sum(x.h, y.h);
+  return fast_two_sum(s.h, s.l + (x.l + y.l));
+}
+// m in [2^-74, 1] as a double-float from its bits: the high part keeps 24
+// significant bits, the low part the remaining 29 rounded to 24 (|m - h - l|
+// <= 2^-47 m); returns false below that range.
+__device__ __forceinline__ bool df_of_unit(double m, dflt& r) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(m);
+  int E = (int)(b >> 52);
+  if (E < 949) return false;
+  r.h = __uint_as_float(((unsigned)(E - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFF));
+  unsigned rem = (unsigned)(b & ((1ull << 29) - 1));
+  r.l = __uint2float_rn(rem) * __uint_as_float((unsigned)(E - 1075 + 127) << 23);
+  return true;
+}
+
 // FP64 operations of the procedure, counted as executed (+ - * / sqrt = 1,
 // fma = 2, negations and comparisons 0): the algorithmic work of the exact
 // contact test, reported for the roofline.
@@ -562,6 +596,11 @@ __device__ __forceinline__ float trunc_f32(double t) {
 // |f32| > E the FP64 value has the same sign and is not zero; otherwise the
 // FP64 Horner value is computed.  Coefficients outside [1e-25, 1e25] keep
 // every FP32 term far from underflow and overflow, else only FP64 is used.
+// Between the two, a double-float Horner evaluation decides the sign when
+// |f_df| > 2^-40 (S + S1): its own error (3 multiply-add steps at <= 2^-44
+// relative each), the coefficients' and the midpoint's representation
+// (2^-48 |k_i|, 2^-47 m times max |f'|) and the FP64 Horner error (< 2^-50 S)
+// together stay below that bound.
 __device__ double bisect64(double k0, double k1, double k2, double k3, double lo, double hi, double flo,
                            long long& flops) {
   bool neg_lo = is_neg(flo);
@@ -570,7 +609,11 @@ __device__ double bisect64(double k0, double k1, double k2, double k3, double lo
   float a0 = fabsf(f0), a1 = fabsf(f1), a2 = fabsf(f2), a3 = fabsf(f3);
   float mk = fmaxf(fmaxf(a0, a1), fmaxf(a2, a3));
   float E = 1.01f * (4.5e-7f * (((a0 + a1) + a2) + a3) + 1.25e-7f * ((a1 + 2.0f * a2) + 3.0f * a3));
+  float Edf = 1.01f * 9.094947e-13f * ((((a0 + a1) + a2) + a3) + ((a1 + 2.0f * a2) + 3.0f * a3));  // 2^-40
+  bool use_df = mk > 1e-20f && mk < 1e25f;
   if (!(mk > 1e-25f && mk < 1e25f)) E = INFINITY;
+  dflt c0 = {f0, __double2float_rn(__dsub_rn(k0, (double)f0))}, c1 = {f1, __double2float_rn(__dsub_rn(k1, (double)f1))},
+       c2 = {f2, __double2float_rn(__dsub_rn(k2, (double)f2))}, c3 = {f3, __double2float_rn(__dsub_rn(k3, (double)f3))};
 #pragma unroll 1
   for (int it = 0; it < 64; ++it) {
     bool ok;
@@ -584,8 +627,17 @@ __device__ double bisect64(double k0, double k1, double k2, double k3, double lo
     float m = trunc_f32(mid);
     float fs = fmaf(fmaf(fmaf(f3, m, f2), m, f1), m, f0);
     bool neg;
+    dflt md;
     if (fabsf(fs) > E) {
       neg = fs < 0.0f;
+    } else if (use_df && df_of_unit(mid, md) &&
+               [&] {
+                 dflt v = df_add(df_mul(df_add(df_mul(df_add(df_mul(c3, md), c2), md), c1), md), c0);
+                 float vv = v.h + v.l;
+                 neg = vv < 0.0f;
+                 return fabsf(vv) > Edf;
+               }()) {
+      // sign certified by the double-float tier
     } else {
       double fm = horner3(k0, k1, k2, k3, mid);
       if (is_zero(fm)) return mid;
