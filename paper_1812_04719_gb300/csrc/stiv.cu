@@ -36,6 +36,7 @@ struct contact_in {
   int type;       // 0, 1: VF (point 0 = vertex, 1..3 triangle); 2: EE (0,1 = edge of i; 2,3 = edge of j)
   d3 X0[4], X1[4];
   double tau;
+  double w1, w2;  // inside-test weights of the detection at tau (VF: b1, b2; EE: s, u)
 };
 
 // V and (optionally) dV/dX1 [4] of one contact.
@@ -49,8 +50,9 @@ __device__ double stiv_one(const contact_in& c, double e2, d3* g) {
   if (c.type < 2) {
     d3 a = Y[2] - Y[1], b = Y[3] - Y[1], cc = Y[0] - Y[1];
     double d00 = dot(a, a), d01 = dot(a, b), d11 = dot(b, b), d20 = dot(cc, a), d21 = dot(cc, b);
-    double den = d00 * d11 - d01 * d01;
-    double b1 = (d11 * d20 - d01 * d21) / den, b2 = (d00 * d21 - d01 * d20) / den, b0 = 1.0 - b1 - b2;
+    double den = d00 * d11 - d01 * d01, iden = 1.0 / den;
+    (void)d20; (void)d21;
+    double b1 = c.w1, b2 = c.w2, b0 = 1.0 - b1 - b2;
     d3 m = cross(a, b);
     d3 Dr = D[0] - (b0 * D[1] + b1 * D[2] + b2 * D[3]);
     double dm = dot(Dr, m);
@@ -67,7 +69,7 @@ __device__ double stiv_one(const contact_in& c, double e2, d3* g) {
     double g1 = bb1 - bb0, g2 = bb2 - bb0;
     d3 ab = cross(b, mb), bbv = cross(mb, a), cb = mk(0, 0, 0);
     // least squares beta = M^-1 G^T c, G = [a b]
-    double z1 = (d11 * g1 - d01 * g2) / den, z2 = (d00 * g2 - d01 * g1) / den;
+    double z1 = (d11 * g1 - d01 * g2) * iden, z2 = (d00 * g2 - d01 * g1) * iden;
     d3 w = z1 * a + z2 * b;
     d3 res = cc - (b1 * a + b2 * b);
     cb = cb + w;
@@ -79,8 +81,9 @@ __device__ double stiv_one(const contact_in& c, double e2, d3* g) {
   } else {
     d3 d1 = Y[1] - Y[0], d2 = Y[3] - Y[2], r = Y[0] - Y[2];
     double A = dot(d1, d1), B = dot(d1, d2), E = dot(d2, d2), C = dot(d1, r), F = dot(d2, r);
-    double den = A * E - B * B;
-    double s = (B * F - C * E) / den, u = (A * F - B * C) / den;
+    double den = A * E - B * B, iden = 1.0 / den;
+    (void)C; (void)F;
+    double s = c.w1, u = c.w2;
     d3 m = cross(d1, d2);
     d3 Dr = ((1.0 - u) * D[2] + u * D[3]) - ((1.0 - s) * D[0] + s * D[1]);
     double dm = dot(Dr, m);
@@ -96,7 +99,7 @@ __device__ double stiv_one(const contact_in& c, double e2, d3* g) {
     double sb = -dot(Drb, D[1] - D[0]), ub = dot(Drb, D[3] - D[2]);
     d3 d1b = cross(d2, mb), d2b = cross(mb, d1);
     // least squares (s, u) = M^-1 G^T c, G = [d1, -d2], c = -r; M = [[A, -B], [-B, E]]
-    double z1 = (E * sb + B * ub) / den, z2 = (B * sb + A * ub) / den;
+    double z1 = (E * sb + B * ub) * iden, z2 = (B * sb + A * ub) * iden;
     d3 w = z1 * d1 - z2 * d2;
     d3 res = (-r) - (s * d1 - u * d2);
     d3 rb = -w;
@@ -121,7 +124,7 @@ struct stiv_args {
   int mixed;
   double L[3];
   const int32_t* ci; const int32_t* cj; const int32_t* cs;
-  const int32_t* pair; const int32_t* type; const int32_t* a; const int32_t* b; const double* tau;
+  const int32_t* pair; const int32_t* type; const int32_t* a; const int32_t* b; const double* tau; const double* w;
   const int64_t* counts;
   int64_t cap;
   double e2;
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(128) stiv_kernel(stiv_args A) {
       stiv_edge_verts(2 * A.pv[vj], pb, &u, &v); ves[2] = vj; vid[2] = u; ves[3] = vj; vid[3] = v;
     }
     contact_in c;
-    c.type = ty; c.tau = A.tau[k];
+    c.type = ty; c.tau = A.tau[k]; c.w1 = A.w[2 * k]; c.w2 = A.w[2 * k + 1];
     for (int q = 0; q < 4; ++q) {
       sh[q] = ves[q] == vj ? s1 : nullptr;
       c.X0[q] = vpos(A, ves[q], 0, vid[q], sh[q]);
@@ -456,7 +459,7 @@ static int run_stiv(stiv_handle* h, void* stream, const int32_t* p_dev, const in
   A.pv = p_dev; A.voff = vert_off_dev; A.X = verts_dev; A.mixed = h->prm.precision == STIV_MIXED;
   for (int c = 0; c < 3; ++c) A.L[c] = h->prm.box_L[c];
   A.ci = cand->i; A.cj = cand->j; A.cs = cand->shift;
-  A.pair = ct->pair; A.type = ct->type; A.a = ct->a; A.b = ct->b; A.tau = ct->tau;
+  A.pair = ct->pair; A.type = ct->type; A.a = ct->a; A.b = ct->b; A.tau = ct->tau; A.w = ct->w;
   A.counts = counts_dev; A.cap = ct->capacity;
   double edt = h->prm.eps * h->prm.dt;
   A.e2 = edt * edt;
