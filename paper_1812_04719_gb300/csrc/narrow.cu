@@ -369,13 +369,12 @@ constexpr float U32 = 5.9604645e-8f;   // 2^-24, unit roundoff of float
 // gv.  |(g1 x g2) . (g3 x g4)| <= |g1||g2||g3||g4|, so the change over the
 // interval is at most sum_i h|gd_i| prod_{j != i} max|g_j|.  Returns +1
 // (certainly > 0), -1 (certainly < 0) or 0.
-__device__ int form_sign(const f3* gv, const f3* gd, float h, float eg) {
-  float val = fdot(fcross(gv[0], gv[1]), fcross(gv[2], gv[3]));
-  float M[4], R[4];
-  for (int i = 0; i < 4; ++i) {
-    R[i] = h * fnorm(gd[i]);
-    M[i] = fnorm(gv[i]) + R[i] + 2.0f * eg;
-  }
+// The same test with the bound's ingredients given: M_i >= max |g_i| over the
+// interval (plus the input error 2 eg), R_i = h |gd_i| (half width times the
+// rate); the norms of the vectors an inside test shares between its forms
+// are taken once.
+__device__ __forceinline__ int form_sign_m(f3 g0, f3 g1, f3 g2, f3 g3, const float* M, const float* R, float eg) {
+  float val = fdot(fcross(g0, g1), fcross(g2, g3));
   float p01 = M[0] * M[1], p23 = M[2] * M[3];
   float prod = p01 * p23;
   float var = R[0] * M[1] * p23 + M[0] * R[1] * p23 + p01 * R[2] * M[3] + p01 * M[2] * R[3];
@@ -390,6 +389,10 @@ __device__ int form_sign(const f3* gv, const f3* gd, float h, float eg) {
 // triangle / are the edges certainly apart (1), certainly inside (2), or
 // undecided (0)?  Points: VF xp, x0, x1, x2; EE p0, p1, q0, q1.
 // ep, ed: error bounds of the FP32 positions / displacements per component.
+// Each barycentric (VF) or closest-point (EE) numerator is a form
+// (g1 x g2) . (g3 x g4) of linear g: |(g1 x g2) . (g3 x g4)| <= prod |g_i|,
+// so its change over the interval is at most sum_i h |gd_i| prod_{j != i}
+// max |g_j|; form_sign_m certifies its sign.
 __device__ int inside_cert(int kind, const f3* x, const f3* d, float t0, float w, float ep, float ed) {
   float h = 0.5f * w + 1e-6f;           // half width, widened past the FP64 root's last ulp
   float tm = t0 + 0.5f * w;
@@ -397,41 +400,59 @@ __device__ int inside_cert(int kind, const f3* x, const f3* d, float t0, float w
   for (int q = 0; q < 4; ++q) P[q] = fat(x[q], tm, d[q]);
   float pm = fmaxf(fmaxf(amax3(P[0]), amax3(P[1])), fmaxf(amax3(P[2]), amax3(P[3])));
   float eg = 2.0f * (ep + ed) + 4.0f * U32 * pm;  // per component, differences of positions at tm
-  f3 gv[4], gd[4];
+  // vector (position difference at tm, rate) -> M, R of form_sign_m
+  auto mr = [&](f3 gv, f3 gd, float& M, float& R) {
+    R = h * fnorm(gd);
+    M = fnorm(gv) + R + 2.0f * eg;
+  };
   if (kind == 0) {
     // barycentric weight of T_k ~ ((T_{k+2} - T_{k+1}) x (p - T_{k+1})) . n,  n = (T1 - T0) x (T2 - T0)
-    gv[2] = fsub(P[2], P[1]); gd[2] = fsub(d[2], d[1]);
-    gv[3] = fsub(P[3], P[1]); gd[3] = fsub(d[3], d[1]);
-    bool all_in = true;
-#pragma unroll 1
-    for (int k = 0; k < 3; ++k) {
-      int a1 = 1 + (k + 1) % 3, a2 = 1 + (k + 2) % 3;
-      gv[0] = fsub(P[a2], P[a1]); gd[0] = fsub(d[a2], d[a1]);
-      gv[1] = fsub(P[0], P[a1]); gd[1] = fsub(d[0], d[a1]);
-      int sg = form_sign(gv, gd, h, eg);
-      if (sg < 0) return 1;
-      if (sg <= 0) all_in = false;
-    }
-    return all_in ? 2 : 0;
+    f3 t01 = fsub(P[2], P[1]), t02 = fsub(P[3], P[1]), t12 = fsub(P[3], P[2]);
+    f3 q0 = fsub(P[0], P[1]), q1 = fsub(P[0], P[2]), q2 = fsub(P[0], P[3]);
+    float Mt01, Rt01, Mt02, Rt02, Mt12, Rt12, Mq0, Rq0, Mq1, Rq1, Mq2, Rq2;
+    mr(t01, fsub(d[2], d[1]), Mt01, Rt01);
+    mr(t02, fsub(d[3], d[1]), Mt02, Rt02);
+    mr(t12, fsub(d[3], d[2]), Mt12, Rt12);
+    mr(q0, fsub(d[0], d[1]), Mq0, Rq0);
+    mr(q1, fsub(d[0], d[2]), Mq1, Rq1);
+    mr(q2, fsub(d[0], d[3]), Mq2, Rq2);
+    f3 nt02 = {-t02.x, -t02.y, -t02.z};
+    // k = 0: (T2 - T1) x (p - T1); k = 1: (T0 - T2) x (p - T2); k = 2: (T1 - T0) x (p - T0)
+    float M0[4] = {Mt12, Mq1, Mt01, Mt02}, R0[4] = {Rt12, Rq1, Rt01, Rt02};
+    int sg0 = form_sign_m(t12, q1, t01, t02, M0, R0, eg);
+    if (sg0 < 0) return 1;
+    float M1[4] = {Mt02, Mq2, Mt01, Mt02}, R1[4] = {Rt02, Rq2, Rt01, Rt02};
+    int sg1 = form_sign_m(nt02, q2, t01, t02, M1, R1, eg);
+    if (sg1 < 0) return 1;
+    float M2[4] = {Mt01, Mq0, Mt01, Mt02}, R2[4] = {Rt01, Rq0, Rt01, Rt02};
+    int sg2 = form_sign_m(t01, q0, t01, t02, M2, R2, eg);
+    if (sg2 < 0) return 1;
+    return (sg0 > 0 && sg1 > 0 && sg2 > 0) ? 2 : 0;
   }
   // EE with m = (p1 - p0) x (q1 - q0):  s ~ ((q0 - p0) x (q1 - q0)) . m,
   // s - 1 ~ ((q0 - p1) x (q1 - q0)) . m,  u ~ ((q0 - p0) x (p1 - p0)) . m,
   // u - 1 ~ ((q1 - p0) x (p1 - p0)) . m   (each divided by |m|^2)
-  f3 e1v = fsub(P[1], P[0]), e1d = fsub(d[1], d[0]);
-  f3 e2v = fsub(P[3], P[2]), e2d = fsub(d[3], d[2]);
-  const int va[4] = {2, 2, 2, 3}, vb[4] = {0, 1, 0, 0};
-  int sgn[4];
-#pragma unroll 1
-  for (int k = 0; k < 4; ++k) {
-    gv[0] = fsub(P[va[k]], P[vb[k]]); gd[0] = fsub(d[va[k]], d[vb[k]]);
-    gv[1] = k < 2 ? e2v : e1v; gd[1] = k < 2 ? e2d : e1d;
-    gv[2] = e1v; gd[2] = e1d;
-    gv[3] = e2v; gd[3] = e2d;
-    sgn[k] = form_sign(gv, gd, h, eg);
-  }
-  if (sgn[0] < 0 || sgn[1] > 0 || sgn[2] < 0 || sgn[3] > 0) return 1;
-  if (sgn[0] > 0 && sgn[1] < 0 && sgn[2] > 0 && sgn[3] < 0) return 2;
-  return 0;
+  f3 e1v = fsub(P[1], P[0]), e2v = fsub(P[3], P[2]);
+  f3 a0 = fsub(P[2], P[0]), a1 = fsub(P[2], P[1]), a3 = fsub(P[3], P[0]);
+  float Me1, Re1, Me2, Re2, Ma0, Ra0, Ma1, Ra1, Ma3, Ra3;
+  mr(e1v, fsub(d[1], d[0]), Me1, Re1);
+  mr(e2v, fsub(d[3], d[2]), Me2, Re2);
+  mr(a0, fsub(d[2], d[0]), Ma0, Ra0);
+  mr(a1, fsub(d[2], d[1]), Ma1, Ra1);
+  mr(a3, fsub(d[3], d[0]), Ma3, Ra3);
+  float Ms[4] = {Ma0, Me2, Me1, Me2}, Rs[4] = {Ra0, Re2, Re1, Re2};
+  int s0 = form_sign_m(a0, e2v, e1v, e2v, Ms, Rs, eg);
+  if (s0 < 0) return 1;
+  float Ms1[4] = {Ma1, Me2, Me1, Me2}, Rs1[4] = {Ra1, Re2, Re1, Re2};
+  int s1 = form_sign_m(a1, e2v, e1v, e2v, Ms1, Rs1, eg);
+  if (s1 > 0) return 1;
+  float Mu[4] = {Ma0, Me1, Me1, Me2}, Ru[4] = {Ra0, Re1, Re1, Re2};
+  int u0 = form_sign_m(a0, e1v, e1v, e2v, Mu, Ru, eg);
+  if (u0 < 0) return 1;
+  float Mu1[4] = {Ma3, Me1, Me1, Me2}, Ru1[4] = {Ra3, Re1, Re1, Re2};
+  int u1 = form_sign_m(a3, e1v, e1v, e2v, Mu1, Ru1, eg);
+  if (u1 > 0) return 1;
+  return (s0 > 0 && s1 < 0 && u0 > 0 && u1 < 0) ? 2 : 0;
 }
 
 // Coefficients of the coplanarity cubic in FP32 and a bound E on the error of
@@ -1015,7 +1036,7 @@ struct PieceWarp {
   int ntask2;
 };
 
-__global__ void __launch_bounds__(PW * 32) pieces_kernel(narrow_args a) {
+__global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
   extern __shared__ unsigned char psraw[];
   PieceWarp& W = ((PieceWarp*)psraw)[threadIdx.x >> 5];
   int lane = threadIdx.x & 31;
