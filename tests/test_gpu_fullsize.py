@@ -72,3 +72,31 @@ def test_sampled_pairs_contacts_volumes_gradients(orc, full):
             assert np.array_equal(g["gves"][gm], c["gves"][cm])
         n_checked += int(gm.sum())
     assert n_checked > 1000
+
+
+@pytest.mark.parametrize("name,prec", [("64", S.STIV_FP64), ("64", S.STIV_MIXED), ("256", S.STIV_FP64),
+                                       ("256", S.STIV_MIXED)])
+def test_whole_scene_lists(orc, name, prec):
+    """The 64-vesicle 30% workload (random orientations, p = 16 -> 32) and the
+    256-vesicle 50% workload (p = 12 -> 24): every candidate pair and every
+    contact (keys, contact times and weights bit for bit), V per pair within
+    1e-10, against the oracle run on the same vertices."""
+    sc = G.scene_64() if name == "64" else G.scene_256()
+    eng = S.Stiv.for_scene(sc, precision=prec, pair_cap=4096, contact_cap=1 << 18)
+    ds = S.DeviceScene.from_scene(sc, precision=prec)
+    for _ in range(2):
+        r = eng.step(ds, grad=False, use_graph=True)
+    torch.cuda.synchronize()
+    g = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
+    Xs = verts_list(sc, ds.verts.double().cpu().numpy())
+    boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
+    pairs = orc.candidate_pairs(boxes, sc.L)
+    assert np.array_equal(gpu_pairs_rows(g), pairs)
+    c = orc.contacts(sc.P, Xs, pairs, sc.L, sc.eps * sc.dt, grad=False)
+    assert len(c["pair"]) > 0
+    for k in ("pair", "type", "a", "b"):
+        assert np.array_equal(g[k], c[k]), k
+    assert np.array_equal(bits(g["tau"]), bits(c["tau"]))
+    assert np.array_equal(bits(g["w"]), bits(c["w"]))
+    assert np.all(np.abs(g["V_pair"] - c["V_pair"]) <= 1e-10 * np.abs(c["V_pair"]))
+    assert g["counts"][S.C_PRIM] == c["counts"][1]
