@@ -259,6 +259,14 @@ int stiv_autotune(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, co
  * STIV_TUNE_PIECE_LEVELS in [1, 6]); STIV_ERR_ARG for a value out of range. */
 int stiv_set_tuning(stiv_handle* h, const int32_t* values);
 
+/* Check of the bounded device waits (not a step of the method): one thread
+ * waits on a shared-memory barrier that nothing completes, giving up after
+ * limit_cycles SM clocks (0 <= limit_cycles <= the bound the tensor-core
+ * synthesis uses, about a second at 2 GHz), and writes *status_dev = 1 when
+ * it gave up, 0 otherwise.  The wait returns by itself; the context stays
+ * usable.  STIV_ERR_ARG for a limit out of range. */
+int stiv_wait_selftest(void* stream, int64_t limit_cycles, int32_t* status_dev);
+
 /* Stable LSD radix sort of (key, value) pairs on the low key_bits bits of the
  * 64-bit keys (Alg. 1's check-point sort, on one GPU).  scratch:
  * at least stiv_sort_scratch_bytes(n) bytes of device memory. */

@@ -302,9 +302,9 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 // true once the phase with the given parity has completed; gives up after
-// WAIT_CYCLES SM clocks (about a second), however long each try_wait
+// limit SM clocks (WAIT_CYCLES: about a second), however long each try_wait
 // suspends the thread
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long limit = WAIT_CYCLES) {
   long long t0 = clock64();
   while (true) {
     unsigned ok;
@@ -316,7 +316,20 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+
+// One thread waits on an mbarrier that nothing arrives on, with the bound the
+// synthesis kernels use (or a shorter one): status = 1 when the wait gave up,
+// 0 if it completed.
+__global__ void wait_selftest_kernel(long long limit, int32_t* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bool ok = mbar_wait(smem_u32(&bar), 0, limit);
+    *status = ok ? 0 : 1;
   }
 }
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
@@ -645,4 +658,10 @@ int stiv_grad_to_coef_tc(stiv_handle* h, cudaStream_t st, int32_t n_ves, int32_t
   gemm_kernel<double><<<grid, GEMM_THREADS, smem, st>>>(A);
   STIV_LAUNCH(h);
   return STIV_OK;
+}
+
+extern "C" int stiv_wait_selftest(void* stream, int64_t limit_cycles, int32_t* status_dev) {
+  if (!status_dev || limit_cycles < 0 || limit_cycles > WAIT_CYCLES) return STIV_ERR_ARG;
+  wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((long long)limit_cycles, status_dev);
+  return cudaGetLastError() == cudaSuccess ? STIV_OK : STIV_ERR_CUDA;
 }

@@ -33,7 +33,8 @@ F_PAIRS_OVERFLOW, F_CONTACTS_OVERFLOW, F_BOX_TOO_SMALL, F_NONFINITE, F_WORK_OVER
 EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_error", "stiv_mesh_topology",
            "stiv_upsample", "stiv_detect", "stiv_stiv", "stiv_stiv_grad", "stiv_grad_scatter",
            "stiv_grad_to_coef", "stiv_step", "stiv_sync_counts", "stiv_sort_scratch_bytes", "stiv_sort_pairs",
-           "stiv_profile", "stiv_profile_read", "stiv_sort_pairs_static", "stiv_autotune", "stiv_set_tuning"]
+           "stiv_profile", "stiv_profile_read", "stiv_sort_pairs_static", "stiv_autotune", "stiv_set_tuning",
+           "stiv_wait_selftest"]
 TUNE_NAMES = ("narrow_ctas_per_sm", "pieces_ctas_per_sm", "fp64_blocks_per_sm", "patch_blocks_per_sm",
               "piece_levels")
 SORT_STATIC_MAX = 1 << 20
@@ -96,6 +97,7 @@ def lib() -> ctypes.CDLL:
     L.stiv_sort_pairs_static.argtypes = [vp, i64, i32, vp, vp, vp, vp]
     L.stiv_autotune.argtypes = [vp, vp, i32, i32, vp, vp, vp, P(StivPairs), P(StivContacts), vp, vp, vp]
     L.stiv_set_tuning.argtypes = [vp, vp]
+    L.stiv_wait_selftest.argtypes = [vp, i64, vp]
     L.stiv_profile.argtypes = [vp, i32]
     L.stiv_profile_read.argtypes = [vp, i32, vp, vp, vp, vp]
     _lib = L
