@@ -207,7 +207,9 @@ int stiv_grad_to_coef(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max
 
 /* The whole per-step path: upsample + detect + stiv_grad.  With use_graph = 1
  * the launches are captured into a CUDA graph on the first call and replayed
- * on later calls with the same arguments. */
+ * on later calls with the same arguments.  coef_dev = NULL skips the
+ * upsampling: verts_dev then holds the input vertices (in the layout
+ * stiv_upsample writes) and coef_off_dev is not read. */
 int stiv_step(stiv_handle* h, void* stream, int32_t use_graph, int32_t n_ves, int32_t p_max,
               const int32_t* p_dev, const int64_t* coef_off_dev, const double* coef_dev,
               const int64_t* vert_off_dev, void* verts_dev, const stiv_pairs* cand,
@@ -231,6 +233,55 @@ int stiv_profile_read(stiv_handle* h, int32_t max_names, char* names, int64_t* l
 /* Wait for the stream, copy the counts to the host and return STIV_ERR_CAPACITY
  * if an overflow flag is set, STIV_ERR_INPUT for an input flag, else STIV_OK. */
 int stiv_sync_counts(void* stream, const int64_t* counts_dev, int64_t* counts_host);
+
+/* Contact LCP (Sec. 3.2, Eq. 3.7; Sec. 3.3.3, Alg. 3):
+ *     0 <= q + B lambda  perp  lambda >= 0,   q = -V,  B = J M J^T,
+ * one row per contact volume: each candidate pair (i, j, shift) with
+ * contacts, in candidate-pair order; V its volume (V_pair of stiv_stiv_grad,
+ * >= 0 for interference; the paper's constraint volume has the opposite sign,
+ * which B does not see); J = dV/dX1, the gradient rows of stiv_stiv_grad
+ * summed per vertex; M block-diagonal, a stand-in for the locally implicit
+ * scheme's A^-1 G with its block structure: per vesicle i,
+ * M_ii = m_i I + t_i (1 1^T (x) I_3), a local part plus a rigid translation
+ * of the whole vesicle (m_ves_dev NULL: m_i = 1; t_ves_dev NULL: t_i = 0), so
+ * B(j, k) = sum over vesicles i common to volumes j and k of
+ * m_i g_j|i . g_k|i + t_i (sum g_j|i) . (sum g_k|i).  Entries are stored for
+ * every pair of volumes that share a vesicle (a value may be 0), CSR with
+ * columns ascending; B is symmetric bit for bit and positive semidefinite.
+ * Caller-owned device arrays: */
+typedef struct {
+  int64_t row_capacity;   /* rows (contact volumes) the arrays hold              */
+  int64_t nnz_capacity;   /* nonzeros of B the arrays hold                       */
+  int32_t* row_pair;      /* [row_capacity] candidate-pair index of each row      */
+  double* q;              /* [row_capacity] -V of each row                        */
+  int64_t* row_ptr;       /* [row_capacity + 1]                                   */
+  int32_t* col;           /* [nnz_capacity]                                       */
+  double* val;            /* [nnz_capacity]                                       */
+  int64_t* dims;          /* [8]: rows, nonzeros, status (1 rows over capacity, 2
+                             nonzeros over capacity), internal counts             */
+} stiv_lcp;
+/* Forms B (Alg. 3) and q from the outputs of stiv_detect (cand, contacts,
+ * counts) and stiv_stiv_grad (V_pair, grad, g_ves, g_vid) of the same step,
+ * all on the device (m_ves_dev, t_ves_dev: [n_ves] or NULL).  Entries are
+ * deterministic (every sum in a fixed order).  Scratch is handle-owned,
+ * allocated on the first call with given capacities.  Returns STIV_ERR_ARG
+ * for a NULL array or a capacity outside [1, 2^30); rows or nonzeros beyond
+ * the capacities are not an error of the call: dims[2] reports them (after
+ * the stream reaches the call), the arrays then hold the first row_capacity
+ * rows and nnz_capacity nonzeros, and stiv_lcp_solve refuses the matrix. */
+int stiv_lcp_matrix(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const stiv_pairs* cand,
+                    const stiv_contacts* contacts, const int64_t* counts_dev, const double* V_pair_dev,
+                    const double* grad_dev, const int32_t* g_ves_dev, const int32_t* g_vid_dev,
+                    const double* m_ves_dev, const double* t_ves_dev, const stiv_lcp* lcp);
+/* Minimum-map Newton method (Sec. 3.3.3) for the LCP above: Phi(lambda) =
+ * min(lambda, q + B lambda); the Newton system on the active set (q + B
+ * lambda < lambda) solved by conjugate gradients (at most max_cg steps),
+ * Armijo line search on |Phi|^2 / 2, at most max_newton steps, stop when
+ * max |Phi| <= tol.  lambda_dev [row_capacity] gets the multipliers;
+ * info_dev [4]: Newton steps, max |Phi|, CG steps, status (0 converged, 1
+ * matrix over capacity, 2 not converged).  One CTA; asynchronous. */
+int stiv_lcp_solve(stiv_handle* h, void* stream, const stiv_lcp* lcp, double tol, int32_t max_newton,
+                   int32_t max_cg, double* lambda_dev, double* info_dev);
 
 /* Launch-shape autotuner (not a step of the method: it changes how the
  * narrow phase's kernels are launched and how deep the certified FP32 piece

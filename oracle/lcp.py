@@ -13,7 +13,10 @@ locally implicit scheme (one block per vesicle).  The paper writes the
 interference volume as negative (V >= 0 is the constraint); the volumes of
 this code are non-negative for interference, so its LCP reads
 0 <= -V + B lambda perp lambda >= 0 with the same B (the sign of J cancels).
-M here is a stand-in: one scalar m_i per vesicle (M_ii = m_i I).
+M here is a stand-in with the block structure of A^-1 G: per vesicle i,
+M_ii = m_i I + t_i (1 1^T (x) I_3), a local part plus a rigid translation of
+the whole vesicle (a force at one point moves every point), so that B(j, k)
+is nonzero whenever volumes j and k involve a common vesicle.
 """
 from __future__ import annotations
 
@@ -39,10 +42,11 @@ def jacobian_rows(n_rows, row_of_contact, grad, gves, gvid, nverts):
     return rows
 
 
-def lcp_matrix_alg3(rows, m_ves):
+def lcp_matrix_alg3(rows, m_ves, t_ves=None):
     """Alg. 3: for each vesicle i, for each pair (j, k) of contact volumes that
     involve i, B(j, k) += g_j . M_ii g_k with g the Jacobian rows restricted to
-    the sample points of vesicle i."""
+    the sample points of vesicle i; with M_ii = m_i I + t_i (1 1^T (x) I_3)
+    that is m_i sum_points g_j . g_k + t_i (sum_points g_j) . (sum_points g_k)."""
     n = len(rows)
     B = np.zeros((n, n))
     involved = {}
@@ -55,6 +59,8 @@ def lcp_matrix_alg3(rows, m_ves):
             for k in involved[i]:
                 gk = rows[k][i]
                 B[j, k] += m_ves[i] * float(np.sum(gj * gk))
+                if t_ves is not None:
+                    B[j, k] += t_ves[i] * float(gj.sum(axis=0) @ gk.sum(axis=0))
     return B
 
 

@@ -190,6 +190,8 @@ extern "C" int stiv_destroy(stiv_handle* h) {
   if (h->tc_ws) cudaFree(h->tc_ws);
   if (h->tc_ws2) cudaFree(h->tc_ws2);
   if (h->tc_status) cudaFree(h->tc_status);
+  if (h->lcp_ws) cudaFree(h->lcp_ws);
+  if (h->lcp_ws2) cudaFree(h->lcp_ws2);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->ws) cudaFree(h->ws);
   stiv_profile(h, 0);
@@ -400,8 +402,11 @@ static int step_eager(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max
                       const int64_t* coef_off_dev, const double* coef_dev, const int64_t* vert_off_dev,
                       void* verts_dev, const stiv_pairs* cand, const stiv_contacts* out, int64_t* counts_dev,
                       double* Vc, double* Vp, double* grad, int32_t* gves, int32_t* gvid) {
-  int rc = stiv_upsample(h, stream, n_ves, p_max, p_dev, coef_off_dev, coef_dev, vert_off_dev, verts_dev);
-  if (rc) return rc;
+  int rc = STIV_OK;
+  if (coef_dev) {   // NULL: the vertices are the input
+    rc = stiv_upsample(h, stream, n_ves, p_max, p_dev, coef_off_dev, coef_dev, vert_off_dev, verts_dev);
+    if (rc) return rc;
+  }
   rc = stiv_detect(h, stream, n_ves, p_max, p_dev, vert_off_dev, verts_dev, cand, out, counts_dev);
   if (rc) return rc;
   if (grad)

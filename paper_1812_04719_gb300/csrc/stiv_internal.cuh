@@ -41,6 +41,11 @@ struct stiv_handle {
   void* tc_ws2;                   // adjoint scratch
   size_t tc_ws2_bytes;
   int* tc_status;
+  // contact LCP scratch (assembly, solve)
+  void* lcp_ws;
+  size_t lcp_ws_bytes;
+  void* lcp_ws2;
+  size_t lcp_ws2_bytes;
   // launch shapes of the narrow phase (0 = default), set by stiv_autotune
   int32_t tune[STIV_NTUNE];
   void* ws;

@@ -34,7 +34,7 @@ EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_
            "stiv_upsample", "stiv_detect", "stiv_stiv", "stiv_stiv_grad", "stiv_grad_scatter",
            "stiv_grad_to_coef", "stiv_step", "stiv_sync_counts", "stiv_sort_scratch_bytes", "stiv_sort_pairs",
            "stiv_profile", "stiv_profile_read", "stiv_sort_pairs_static", "stiv_autotune", "stiv_set_tuning",
-           "stiv_wait_selftest"]
+           "stiv_wait_selftest", "stiv_lcp_matrix", "stiv_lcp_solve"]
 TUNE_NAMES = ("narrow_ctas_per_sm", "pieces_ctas_per_sm", "fp64_blocks_per_sm", "patch_blocks_per_sm",
               "piece_levels")
 SORT_STATIC_MAX = 1 << 20
@@ -44,6 +44,12 @@ class StivError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
         super().__init__(f"{what}: {status_string(status)} ({status})" if what else status_string(status))
+
+
+class StivLcp(ctypes.Structure):
+    _fields_ = [("row_capacity", ctypes.c_int64), ("nnz_capacity", ctypes.c_int64), ("row_pair", ctypes.c_void_p),
+                ("q", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("dims", ctypes.c_void_p)]
 
 
 class StivParams(ctypes.Structure):
@@ -98,6 +104,9 @@ def lib() -> ctypes.CDLL:
     L.stiv_autotune.argtypes = [vp, vp, i32, i32, vp, vp, vp, P(StivPairs), P(StivContacts), vp, vp, vp]
     L.stiv_set_tuning.argtypes = [vp, vp]
     L.stiv_wait_selftest.argtypes = [vp, i64, vp]
+    L.stiv_lcp_matrix.argtypes = [vp, vp, i32, i32, P(StivPairs), P(StivContacts), vp, vp, vp, vp, vp, vp, vp,
+                                  P(StivLcp)]
+    L.stiv_lcp_solve.argtypes = [vp, vp, P(StivLcp), ctypes.c_double, i32, i32, vp, vp]
     L.stiv_profile.argtypes = [vp, i32]
     L.stiv_profile_read.argtypes = [vp, i32, vp, vp, vp, vp]
     _lib = L
@@ -345,19 +354,11 @@ class Stiv:
         for _ in range(max_retries):
             b = self._buffers(grad)
             cand, out = b.pairs_struct(), b.contacts_struct()
-            if upsample:
-                stiv_step(self.h, st, use_graph, ds.n, ds.p_max, _ptr(ds.p), _ptr(ds.coef_off), _ptr(ds.coef),
-                          _ptr(ds.vert_off), _ptr(ds.verts), cand, out, _ptr(b.counts), _ptr(b.Vc), _ptr(b.Vp),
-                          _ptr(b.grad) if grad else 0, _ptr(b.gves) if grad else 0, _ptr(b.gvid) if grad else 0)
-            else:
-                stiv_detect(self.h, st, ds.n, ds.p_max, _ptr(ds.p), _ptr(ds.vert_off), _ptr(ds.verts), cand, out,
-                            _ptr(b.counts))
-                if grad:
-                    stiv_stiv_grad(self.h, st, ds.n, _ptr(ds.p), _ptr(ds.vert_off), _ptr(ds.verts), cand, out,
-                                   _ptr(b.counts), _ptr(b.Vc), _ptr(b.Vp), _ptr(b.grad), _ptr(b.gves), _ptr(b.gvid))
-                else:
-                    stiv_stiv(self.h, st, ds.n, _ptr(ds.p), _ptr(ds.vert_off), _ptr(ds.verts), cand, out,
-                              _ptr(b.counts), _ptr(b.Vc), _ptr(b.Vp))
+            # coef NULL: ds.verts is the input, the upsampling is skipped
+            stiv_step(self.h, st, use_graph, ds.n, ds.p_max, _ptr(ds.p), _ptr(ds.coef_off),
+                      _ptr(ds.coef) if upsample else 0, _ptr(ds.vert_off), _ptr(ds.verts), cand, out, _ptr(b.counts),
+                      _ptr(b.Vc), _ptr(b.Vp), _ptr(b.grad) if grad else 0, _ptr(b.gves) if grad else 0,
+                      _ptr(b.gvid) if grad else 0)
             rc, counts = stiv_sync_counts(st, _ptr(b.counts))
             if rc == STIV_ERR_CAPACITY:
                 f = int(counts[C_STATUS])
@@ -414,3 +415,74 @@ def shift_vec(code):
     """shift code 9(sx+1) + 3(sy+1) + (sz+1) -> (sx, sy, sz) (numpy, vectorised)."""
     code = np.asarray(code)
     return np.stack([code // 9 - 1, (code // 3) % 3 - 1, code % 3 - 1], axis=-1)
+
+
+class ContactLCP:
+    """The contact LCP of a step (Eq. 3.7): 0 <= -V + B lambda perp lambda >= 0,
+    B = J M J^T with M_ii = m_i I + t_i (1 1^T (x) I_3) per vesicle (m_i = 1
+    when m_ves is None, t_i = 0 when t_ves is None).  Buffers grow when the
+    library reports a capacity overflow."""
+
+    def __init__(self, device="cuda", row_cap: int = 1024, nnz_cap: int = 1 << 15):
+        self.device = torch.device(device)
+        self._alloc(row_cap, nnz_cap)
+
+    def _alloc(self, row_cap, nnz_cap):
+        d = self.device
+        self.row_cap, self.nnz_cap = int(row_cap), int(nnz_cap)
+        self.row_pair = torch.zeros(self.row_cap, dtype=torch.int32, device=d)
+        self.q = torch.zeros(self.row_cap, dtype=torch.float64, device=d)
+        self.row_ptr = torch.zeros(self.row_cap + 1, dtype=torch.int64, device=d)
+        self.col = torch.zeros(self.nnz_cap, dtype=torch.int32, device=d)
+        self.val = torch.zeros(self.nnz_cap, dtype=torch.float64, device=d)
+        self.dims = torch.zeros(8, dtype=torch.int64, device=d)
+        self.lam = torch.zeros(self.row_cap, dtype=torch.float64, device=d)
+        self.info = torch.zeros(4, dtype=torch.float64, device=d)
+
+    def struct(self) -> StivLcp:
+        return StivLcp(self.row_cap, self.nnz_cap, _ptr(self.row_pair), _ptr(self.q), _ptr(self.row_ptr),
+                       _ptr(self.col), _ptr(self.val), _ptr(self.dims))
+
+    def assemble(self, eng: "Stiv", ds: "DeviceScene", m_ves=None, t_ves=None, stream=None,
+                 max_retries: int = 6) -> dict:
+        """B and q from the engine's last step with grad=True (m_ves, t_ves:
+        float64 device tensors [n] or None)."""
+        b = eng.buf
+        st = _stream(stream)
+        mv = 0 if m_ves is None else _ptr(m_ves)
+        tv = 0 if t_ves is None else _ptr(t_ves)
+        for _ in range(max_retries):
+            lcp = self.struct()
+            _check(lib().stiv_lcp_matrix(eng.h, st, ds.n, ds.p_max, ctypes.byref(b.pairs_struct()),
+                                         ctypes.byref(b.contacts_struct()), _ptr(b.counts), _ptr(b.Vp),
+                                         _ptr(b.grad), _ptr(b.gves), _ptr(b.gvid), mv, tv, ctypes.byref(lcp)),
+                   "stiv_lcp_matrix")
+            dims = self.dims.cpu().numpy()
+            if dims[2] == 0:
+                n, nnz = int(dims[0]), int(dims[1])
+                return dict(n=n, nnz=nnz, row_pair=self.row_pair[:n], q=self.q[:n], row_ptr=self.row_ptr[:n + 1],
+                            col=self.col[:nnz], val=self.val[:nnz])
+            self._alloc(max(self.row_cap, 2 * int(dims[0]) + 16) if dims[2] & 1 else self.row_cap,
+                        max(self.nnz_cap, 2 * int(dims[1]) + 16) if dims[2] & 2 else self.nnz_cap)
+        raise StivError(STIV_ERR_CAPACITY, "lcp: capacities kept overflowing")
+
+    def load_csr(self, row_ptr, col, val, q):
+        """A given matrix (CSR, host arrays) and q, for stiv_lcp_solve."""
+        n, nnz = len(q), len(val)
+        if n > self.row_cap or nnz > self.nnz_cap:
+            self._alloc(max(self.row_cap, n), max(self.nnz_cap, nnz))
+        d = self.device
+        self.row_ptr[:n + 1].copy_(torch.as_tensor(np.asarray(row_ptr, dtype=np.int64), device=d))
+        self.col[:nnz].copy_(torch.as_tensor(np.asarray(col, dtype=np.int32), device=d))
+        self.val[:nnz].copy_(torch.as_tensor(np.asarray(val, dtype=np.float64), device=d))
+        self.q[:n].copy_(torch.as_tensor(np.asarray(q, dtype=np.float64), device=d))
+        self.dims.copy_(torch.tensor([n, nnz, 0, 0, 0, 0, 0, 0], dtype=torch.int64, device=d))
+
+    def solve(self, eng: "Stiv", tol: float = 1e-12, max_newton: int = 100, max_cg: int = 2000,
+              stream=None) -> dict:
+        _check(lib().stiv_lcp_solve(eng.h, _stream(stream), ctypes.byref(self.struct()), float(tol), int(max_newton),
+                                    int(max_cg), _ptr(self.lam), _ptr(self.info)), "stiv_lcp_solve")
+        n = int(self.dims[0].item())
+        info = self.info.cpu().numpy()
+        return dict(lam=self.lam[:n], newton=int(info[0]), residual=float(info[1]), cg=int(info[2]),
+                    status=int(info[3]))

@@ -20,6 +20,27 @@ def run_gpu(sc, precision=S.STIV_FP64, grad=True, use_graph=False, include_ee=Tr
     return out
 
 
+def run_gpu_on(sc, X, precision=S.STIV_FP64, grad=True, use_graph=False, replays=1, include_ee=True, pair_cap=256,
+               contact_cap=4096, eng=None):
+    """Detection, volumes (and gradient rows) on given FP64 vertices X (the
+    oracle's synthesis): uploaded in the form's vertex type, the step run
+    without the GPU upsampling.  out["verts"] holds the values the device
+    used, widened to FP64 (the oracle's input)."""
+    eng = eng or S.Stiv.for_scene(sc, precision=precision, include_ee=include_ee, pair_cap=pair_cap,
+                                  contact_cap=contact_cap)
+    ds = S.DeviceScene.from_scene(sc, precision=precision)
+    Xd = np.ascontiguousarray(X, dtype=np.float32 if precision == S.STIV_MIXED else np.float64)
+    ds.verts.copy_(torch.from_numpy(Xd))
+    for _ in range(replays):
+        r = eng.step(ds, grad=grad, upsample=False, use_graph=use_graph)
+    torch.cuda.synchronize()
+    out = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
+    out["verts"] = Xd.astype(np.float64)
+    out["eng"] = eng
+    out["ds"] = ds
+    return out
+
+
 def verts_list(sc, flat):
     """Flat vertex array -> list of [2][3][n_v] arrays (FP64)."""
     offs = sc.vert_off()

@@ -11,6 +11,7 @@ from paper_1812_04719_gb300 import autograd as A
 from paper_1812_04719_gb300 import scenegen as G
 from paper_1812_04719_gb300 import stiv as S
 from tests.gpu_run import verts_list
+from tests.oracle_pool import oracle_vertices
 
 pytestmark = pytest.mark.gpu
 
@@ -37,11 +38,11 @@ def test_scene_has_contacts(c5):
 
 def test_gradient_matches_oracle(orc, c5):
     sc, g = c5["sc"], c5["grad"]
-    Xs = verts_list(sc, c5["verts"])
-    pairs = np.concatenate([c5["eng"].buf.ci[:c5["counts"][S.C_PAIRS]].cpu().numpy()[:, None],
-                            c5["eng"].buf.cj[:c5["counts"][S.C_PAIRS]].cpu().numpy()[:, None],
-                            S.shift_vec(c5["eng"].buf.cs[:c5["counts"][S.C_PAIRS]].cpu().numpy())], axis=1)
-    c = orc.contacts(sc.P, Xs, pairs.astype(np.int32), sc.L, sc.eps * sc.dt, grad=True)
+    Xs = verts_list(sc, oracle_vertices(sc))      # the oracle's own synthesis
+    boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
+    pairs = orc.candidate_pairs(boxes, sc.L)
+    c = orc.contacts(sc.P, Xs, pairs, sc.L, sc.eps * sc.dt, grad=True)
+    assert len(c["pair"]) == len(c5["keys"]["pair"])
     assert abs(c["V_pair"].sum() - c5["total"]) <= 1e-10 * c5["total"]
     # dense dSum/dX1 per vesicle, then the transpose of the oracle's synthesis
     gX = [np.zeros((3, G.nverts(int(P)))) for P in sc.P]

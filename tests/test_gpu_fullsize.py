@@ -1,16 +1,19 @@
 """Parity at the benchmark's full sizes: the 1440-vesicle 58% lattice workload
 (p = 16 -> 32) and the 4096-vesicle 40% workload of uneven orders (p in
 {8, 12, 16}), run as the benchmark runs them (graph replay of the whole
-step).  The whole candidate-pair list is compared with the oracle's all-pairs
-box test bit for bit; contacts, volumes and gradient rows are compared on a
-sample of vesicle pairs that the oracle recomputes one by one."""
+step).  The upsampled vertices are compared with the oracle's synthesis; the
+detection is then replayed on the oracle's vertices, and its whole
+candidate-pair list is compared with the oracle's all-pairs box test bit for
+bit; contacts, volumes and gradient rows are compared on a sample of vesicle
+pairs that the oracle recomputes one by one."""
 import numpy as np
 import pytest
 import torch
 
 from paper_1812_04719_gb300 import scenegen as G
 from paper_1812_04719_gb300 import stiv as S
-from tests.gpu_run import gpu_pairs_rows, verts_list
+from tests.gpu_run import gpu_pairs_rows, run_gpu_on, verts_list
+from tests.oracle_pool import oracle_vertices
 
 pytestmark = pytest.mark.gpu
 
@@ -24,18 +27,29 @@ def bits(x):
 def full(request):
     name, prec = request.param
     sc = G.scene_1440() if name == "1440" else G.scene_4096()
+    Xo = oracle_vertices(sc)
     eng = S.Stiv.for_scene(sc, precision=prec, pair_cap=8192, contact_cap=1 << 20)
     ds = S.DeviceScene.from_scene(sc, precision=prec)
     for _ in range(3):   # capture, then replays
-        r = eng.step(ds, grad=True, use_graph=True)
+        eng.step(ds, grad=True, use_graph=True)
     torch.cuda.synchronize()
-    g = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
-    g["verts"] = ds.verts.double().cpu().numpy()
-    return sc, g
+    up = ds.verts.double().cpu().numpy()
+    g = run_gpu_on(sc, Xo, precision=prec, grad=True, use_graph=True, replays=3, eng=eng)
+    return sc, g, up, Xo, prec
+
+
+def test_upsample_full(full):
+    """Synthesis at p -> 2p of every vesicle: FP64 within 1e-13 of the
+    oracle's, MIXED (tensor cores, FP32 output) within 4e-7, relative to the
+    largest coordinate."""
+    sc, g, up, Xo, prec = full
+    scale = np.abs(Xo).max()
+    tol = 1e-13 if prec == S.STIV_FP64 else 4e-7
+    assert np.abs(up - Xo).max() <= tol * scale
 
 
 def test_candidate_pairs_full(orc, full):
-    sc, g = full
+    sc, g = full[:2]
     Xs = verts_list(sc, g["verts"])
     boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
     pairs = orc.candidate_pairs(boxes, sc.L)
@@ -45,7 +59,7 @@ def test_candidate_pairs_full(orc, full):
 
 
 def test_sampled_pairs_contacts_volumes_gradients(orc, full):
-    sc, g = full
+    sc, g = full[:2]
     Xs = verts_list(sc, g["verts"])
     rows = gpu_pairs_rows(g)
     rng = np.random.default_rng(11)
@@ -80,15 +94,12 @@ def test_whole_scene_lists(orc, name, prec):
     """The 64-vesicle 30% workload (random orientations, p = 16 -> 32) and the
     256-vesicle 50% workload (p = 12 -> 24): every candidate pair and every
     contact (keys, contact times and weights bit for bit), V per pair within
-    1e-10, against the oracle run on the same vertices."""
+    1e-10, against the oracle run on the same vertices (its own synthesis, in
+    the form's vertex type)."""
     sc = G.scene_64() if name == "64" else G.scene_256()
-    eng = S.Stiv.for_scene(sc, precision=prec, pair_cap=4096, contact_cap=1 << 18)
-    ds = S.DeviceScene.from_scene(sc, precision=prec)
-    for _ in range(2):
-        r = eng.step(ds, grad=False, use_graph=True)
-    torch.cuda.synchronize()
-    g = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
-    Xs = verts_list(sc, ds.verts.double().cpu().numpy())
+    g = run_gpu_on(sc, oracle_vertices(sc), precision=prec, grad=False, use_graph=True, replays=2, pair_cap=4096,
+                   contact_cap=1 << 18)
+    Xs = verts_list(sc, g["verts"])
     boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
     pairs = orc.candidate_pairs(boxes, sc.L)
     assert np.array_equal(gpu_pairs_rows(g), pairs)

@@ -7,7 +7,8 @@ import oracle as O
 from paper_1812_04719_gb300 import scenegen as G
 from paper_1812_04719_gb300 import stiv as S
 from tests.golden_table3 import load as load_table3
-from tests.gpu_run import gpu_pairs_rows, run_gpu, verts_list
+from tests.gpu_run import gpu_pairs_rows, run_gpu, run_gpu_on, verts_list
+from tests.oracle_pool import oracle_vertices
 
 pytestmark = pytest.mark.gpu
 
@@ -125,9 +126,10 @@ def test_upsample_mixed_tensor_cores(orc, name):
 @pytest.mark.parametrize("name", list(SCENES))
 def test_detect_bit_exact(orc, name):
     """Candidate pairs and contacts (keys, tau and weights bit for bit) equal
-    the oracle's on the same vertices; the counted primitive pairs too."""
+    the oracle's on the same vertices (the oracle's synthesis); the counted
+    primitive pairs too."""
     sc = SCENES[name]()
-    g = run_gpu(sc)
+    g = run_gpu_on(sc, oracle_vertices(sc))
     Xs = verts_list(sc, g["verts"])
     boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
     pairs = orc.candidate_pairs(boxes, sc.L)
@@ -151,9 +153,12 @@ def test_operation_count_exact_mode(orc, name):
     work), operation for operation."""
     sc = SCENES[name]()
     eng = S.Stiv.for_scene(sc, pair_cap=256, contact_cap=4096, exact_only=True)
-    g = run_gpu(sc, eng=eng)
+    g = run_gpu_on(sc, oracle_vertices(sc), eng=eng)
     Xs = verts_list(sc, g["verts"])
-    c = orc.contacts(sc.P, Xs, gpu_pairs_rows(g), sc.L, sc.eps * sc.dt)
+    boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
+    pairs = orc.candidate_pairs(boxes, sc.L)
+    assert np.array_equal(gpu_pairs_rows(g), pairs)
+    c = orc.contacts(sc.P, Xs, pairs, sc.L, sc.eps * sc.dt)
     assert g["counts"][S.C_PRIM] == c["counts"][1]
     assert g["counts"][S.C_EXACT] == c["counts"][1]
     assert g["counts"][S.C_FLOPS] == c["counts"][3]
@@ -162,10 +167,13 @@ def test_operation_count_exact_mode(orc, name):
 @pytest.mark.parametrize("name", list(SCENES))
 def test_stiv_and_gradient(orc, name):
     sc = SCENES[name]()
-    g = run_gpu(sc)
+    g = run_gpu_on(sc, oracle_vertices(sc))
     Xs = verts_list(sc, g["verts"])
-    pairs = gpu_pairs_rows(g)
-    c = orc.contacts(sc.P, Xs, pairs, sc.L, sc.eps * sc.dt)
+    boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
+    pairs = orc.candidate_pairs(boxes, sc.L)
+    assert np.array_equal(gpu_pairs_rows(g), pairs)
+    c = orc.contacts(sc.P, Xs, pairs, sc.L, sc.eps * sc.dt, grad=True)
+    assert np.array_equal(g["pair"], c["pair"])
     assert np.all(np.abs(g["V"] - c["V"]) <= 1e-10 * np.abs(c["V"]) + 1e-300)
     assert np.all(np.abs(g["V_pair"] - c["V_pair"]) <= 1e-10 * np.abs(c["V_pair"]) + 1e-300)
     assert np.array_equal(g["gves"], c["gves"]) and np.array_equal(g["gvid"], c["gvid"])
@@ -249,12 +257,15 @@ def test_adjoint_mixed_tensor_cores(orc, name):
 
 
 def test_mixed_precision_lists(orc):
-    """MIXED: FP32 vertices; the FP64 contact arithmetic on those vertices is
-    bit-identical to the oracle run on the same (widened) vertices."""
+    """MIXED: FP32 vertices (the tensor-core synthesis within 4e-7 of the
+    oracle's); the FP64 contact arithmetic on FP32 vertices is bit-identical
+    to the oracle run on the same (widened) vertices, here the oracle's
+    synthesis rounded to FP32."""
     sc = SCENES["periodic_p3"]()
-    g = run_gpu(sc, precision=S.STIV_MIXED)
-    Xo = np.concatenate([orc.synth_vesicle(int(sc.p[v]), int(sc.P[v]), sc.coef_of(v)).ravel() for v in range(sc.n)])
-    assert np.abs(g["verts"] - Xo).max() < 4e-7 * np.abs(Xo).max()
+    g_up = run_gpu(sc, precision=S.STIV_MIXED)
+    Xo = oracle_vertices(sc)
+    assert np.abs(g_up["verts"] - Xo).max() < 4e-7 * np.abs(Xo).max()
+    g = run_gpu_on(sc, Xo, precision=S.STIV_MIXED)
     Xs = verts_list(sc, g["verts"])
     boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
     pairs = orc.candidate_pairs(boxes, sc.L)

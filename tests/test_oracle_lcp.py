@@ -40,18 +40,43 @@ def _scene_lcp(orc, sc):
     return rows, -c["V_pair"][hit], nverts
 
 
-def test_alg3_equals_j_m_jt(orc):
-    """Alg. 3's per-vesicle accumulation equals the matrix product J M J^T."""
+def _dense_M(m, t, nverts):
+    """The block-diagonal M written out: per vesicle m_i I + t_i (1 1^T (x) I_3)
+    over its 3 n_v coordinates (point-major, x y z)."""
+    blocks = []
+    for v, nv in enumerate(nverts):
+        blk = m[v] * np.eye(3 * nv)
+        if t is not None:
+            blk += t[v] * np.kron(np.ones((nv, nv)), np.eye(3))
+        blocks.append(blk)
+    n = sum(b.shape[0] for b in blocks)
+    M = np.zeros((n, n))
+    o = 0
+    for b in blocks:
+        M[o:o + b.shape[0], o:o + b.shape[0]] = b
+        o += b.shape[0]
+    return M
+
+
+@pytest.mark.parametrize("with_t", [False, True])
+def test_alg3_equals_j_m_jt(orc, with_t):
+    """Alg. 3's per-vesicle accumulation equals the matrix product J M J^T
+    with M written out densely."""
     sc = G.scene_small((4, 4, 2), p=3, seed=6, periodic=True)
     rows, q, nverts = _scene_lcp(orc, sc)
     assert len(rows) >= 30
     m = np.linspace(0.5, 2.0, sc.n)
-    B = L.lcp_matrix_alg3(rows, m)
+    t = np.linspace(0.05, 0.01, sc.n) if with_t else None
+    B = L.lcp_matrix_alg3(rows, m, t)
     J, offs = L.dense_jacobian(rows, nverts)
-    Mdiag = np.concatenate([np.full(3 * nv, m[v]) for v, nv in enumerate(nverts)])
-    ref = (J * Mdiag) @ J.T
+    ref = J @ _dense_M(m, t, nverts) @ J.T
     assert np.allclose(B, ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
     assert np.allclose(B, B.T, rtol=1e-12)
+    # every pair of volumes sharing a vesicle couples through the translation term
+    share = np.array([[bool(set(a) & set(b)) for b in rows] for a in rows])
+    if with_t:
+        assert np.array_equal(B != 0, share)
+    assert np.all(np.linalg.eigvalsh(B) > -1e-12 * np.abs(B).max())
 
 
 def test_scene_lcp_kkt(orc):
