@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--cells", default=None,
                     help="smaller piece of the 58%% lattice (e.g. 6,6,2) for profiling; default: the 1440 scene")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-lcp", action="store_true", help="skip timing the contact LCP (assembly + solve)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -470,6 +471,42 @@ def run_ours(args, rank, world, local):
         e2e = {"value": sc.n * world / (float(np.mean(e_ms)) * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(bi),
                "d2h_bytes_per_step": int(bo)}
 
+    # the contact LCP of the step (Eq. 3.7): B = J M J^T by Alg. 3 and the
+    # min-map Newton solve, on the last step's contacts and gradient rows;
+    # timed beside the step (the metric's step ends at dV/dX1)
+    lcp_rec = None
+    if not args.no_lcp:
+        eng.step(ds, grad=True, use_graph=True, stream=stream)
+        m_v = torch.ones(sc.n, dtype=torch.float64, device=dev)
+        t_v = torch.as_tensor(1.0 / np.array([S.nverts(int(P)) for P in sc.P]), dtype=torch.float64, device=dev)
+        lcp = S.ContactLCP(device=dev)
+        A = lcp.assemble(eng, ds, m_v, t_v, stream=stream)
+        b = eng.buf
+        ms_a, ms_s = [], []
+        for k in range(max(3, args.steps // 2) + 1):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            rc = S.lib().stiv_lcp_matrix(eng.h, st, ds.n, ds.p_max, b.pairs_struct(), b.contacts_struct(),
+                                         b.counts.data_ptr(), b.Vp.data_ptr(), b.grad.data_ptr(),
+                                         b.gves.data_ptr(), b.gvid.data_ptr(), m_v.data_ptr(), t_v.data_ptr(),
+                                         lcp.struct())
+            assert rc == S.STIV_OK, rc
+            ev[1].record(stream)
+            rc = S.lib().stiv_lcp_solve(eng.h, st, lcp.struct(), 1e-12, 100, 2000, lcp.lam.data_ptr(),
+                                        lcp.info.data_ptr())
+            assert rc == S.STIV_OK, rc
+            ev[2].record(stream)
+            torch.cuda.synchronize(dev)
+            S.stiv_profile_read(eng.h)
+            if k >= 1:
+                ms_a.append(ev[0].elapsed_time(ev[1])); ms_s.append(ev[1].elapsed_time(ev[2]))
+        info = lcp.info.cpu().numpy()
+        lcp_rec = {"rows": A["n"], "nnz": A["nnz"], "assemble_ms": float(np.mean(ms_a)),
+                   "solve_ms": float(np.mean(ms_s)), "newton_steps": int(info[0]), "cg_steps": int(info[2]),
+                   "max_abs_phi": float(info[1]), "status": int(info[3]),
+                   "M": "per vesicle I + (1/n_v) 1 1^T (x) I_3"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         nv, secs, threads, desc = oracle_sample(sc, args.cpu_seconds)
@@ -493,7 +530,7 @@ def run_ours(args, rank, world, local):
                            "prim_pairs_tested": int(counts[S.C_PRIM]), "patch_pairs": int(counts[S.C_PATCH]),
                            "prim_pairs_fp64": int(counts[S.C_EXACT])},
                 "roofline": roof, "roofline_fp64_kernel": roof_fp64, "fp64_form": fp64_form,
-                "cpu_baseline": cpu, "e2e": e2e,
+                "cpu_baseline": cpu, "e2e": e2e, "lcp": lcp_rec,
                 "gpu_launches": launches,
                 "clocks": clk, "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda x: -x[1])},
                 "wall_s": t_wall}

@@ -274,12 +274,17 @@ int stiv_lcp_matrix(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, 
                     const double* grad_dev, const int32_t* g_ves_dev, const int32_t* g_vid_dev,
                     const double* m_ves_dev, const double* t_ves_dev, const stiv_lcp* lcp);
 /* Minimum-map Newton method (Sec. 3.3.3) for the LCP above: Phi(lambda) =
- * min(lambda, q + B lambda); the Newton system on the active set (q + B
- * lambda < lambda) solved by conjugate gradients (at most max_cg steps),
- * Armijo line search on |Phi|^2 / 2, at most max_newton steps, stop when
- * max |Phi| <= tol.  lambda_dev [row_capacity] gets the multipliers;
- * info_dev [4]: Newton steps, max |Phi|, CG steps, status (0 converged, 1
- * matrix over capacity, 2 not converged).  One CTA; asynchronous. */
+ * min(lambda, q + B lambda); per Newton step the active set is
+ * {q + B lambda < lambda}, the direction is -lambda off it and on it solves
+ * the Newton system by a Jacobi-preconditioned conjugate gradient in FP32 to
+ * a relative residual of 1e-6 (at most max_cg steps; an inexact Newton
+ * method); Phi, the merit |Phi|^2 / 2 and its Armijo line search are FP64;
+ * at most max_newton steps, stop when max |Phi| <= tol (FP64).  lambda_dev
+ * [row_capacity] gets the multipliers; info_dev [4]: Newton steps, max |Phi|,
+ * CG steps, status (0 converged, 1 matrix over capacity, 2 not converged).
+ * One CTA (B and the vectors in its shared memory when they fit);
+ * asynchronous.  Returns STIV_ERR_ARG for a NULL array, tol <= 0 or a
+ * non-positive limit or capacity. */
 int stiv_lcp_solve(stiv_handle* h, void* stream, const stiv_lcp* lcp, double tol, int32_t max_newton,
                    int32_t max_cg, double* lambda_dev, double* info_dev);
 

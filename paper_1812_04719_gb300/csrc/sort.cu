@@ -5,9 +5,11 @@
 // "scattered" exactly as in Table 3.  The item count may live on the device
 // (n_dev); the host passes an upper bound for the launch shapes.
 //
-// Per digit pass: (1) per-tile digit histograms, (2) one exclusive scan over
-// [digit][tile], (3) a stable scatter: each tile ranks its items warp by warp
-// with __match_any_sync and writes them at tile offset + rank.
+// Per digit pass: (1) per-tile digit histograms [digit][tile], (2) one CTA per
+// digit scans its row over the tiles (exclusive, coalesced) and writes the
+// digit's total, (3) a stable scatter: each tile scans the 256 digit totals,
+// ranks its items warp by warp with __match_any_sync and writes them at
+// digit base + tile offset + rank.
 #include "stiv_internal.cuh"
 
 namespace {
@@ -17,6 +19,29 @@ constexpr int kItems = 8;                    // items per thread per tile
 constexpr int kTile = kThreads * kItems;     // 2048 items per tile
 constexpr int kRadix = 256;
 constexpr int kWarps = kThreads / 32;
+static_assert(kThreads == kRadix, "the scatter scans the digit totals one per thread");
+
+// Exclusive scan of one value per thread over the CTA (kThreads), in a fixed
+// order; *total gets the sum.  wsum: kWarps ints of shared memory.
+__device__ __forceinline__ int32_t cta_exclusive_scan(int32_t v, int32_t* wsum, int32_t* total) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t x = v;
+  for (int off = 1; off < 32; off <<= 1) {
+    int32_t y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  int32_t pre = 0, tot = 0;
+  for (int q = 0; q < kWarps; ++q) {
+    int32_t s = wsum[q];
+    pre += q < w ? s : 0;
+    tot += s;
+  }
+  __syncthreads();
+  *total = tot;
+  return pre + x - v;
+}
 
 __device__ __forceinline__ int64_t load_n(const int64_t* n_dev, int64_t n_max) {
   if (!n_dev) return n_max;
@@ -39,34 +64,37 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const uint64_t* keys, co
   for (int d = threadIdx.x; d < kRadix; d += kThreads) hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
-// Exclusive scan of m = kRadix * ntiles ints in one CTA (m <= a few million).
-__global__ void __launch_bounds__(1024) scan_kernel(int32_t* data, int64_t m) {
-  __shared__ int32_t part[1024];
-  int64_t per = (m + 1023) / 1024;
-  int64_t lo = threadIdx.x * per, hi = lo + per < m ? lo + per : m;
-  int32_t s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += data[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+// CTA d: exclusive scan of hist[d][0 .. ntiles) in place; totals[d] = the sum.
+__global__ void __launch_bounds__(kThreads) scan_kernel(int32_t* hist, int ntiles, int32_t* totals) {
+  __shared__ int32_t wsum[kWarps];
+  int32_t* row = hist + (int64_t)blockIdx.x * ntiles;
+  int32_t carry = 0;
+  for (int base = 0; base < ntiles; base += kThreads) {
+    int i = base + threadIdx.x;
+    int32_t v = i < ntiles ? row[i] : 0, tot;
+    int32_t ex = cta_exclusive_scan(v, wsum, &tot);
+    if (i < ntiles) row[i] = carry + ex;
+    carry += tot;
   }
-  int32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-  for (int64_t i = lo; i < hi; ++i) { int32_t v = data[i]; data[i] = run; run += v; }
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
 __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint64_t* kin, const int32_t* vin, uint64_t* kout,
                                                             int32_t* vout, const int64_t* n_dev, int64_t n_max,
-                                                            int shift, int ntiles, const int32_t* hist) {
+                                                            int shift, int ntiles, const int32_t* hist,
+                                                            const int32_t* totals) {
   __shared__ int32_t tile_off[kRadix];
+  __shared__ int32_t wsum[kWarps];
   __shared__ int32_t round_tot[kRadix];
   __shared__ int32_t warp_cnt[kWarps][kRadix];
   int64_t n = load_n(n_dev, n_max);
+  if ((int64_t)blockIdx.x * kTile >= n) return;   // an empty tile scatters nothing
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int d = threadIdx.x; d < kRadix; d += kThreads) tile_off[d] = hist[(int64_t)d * ntiles + blockIdx.x];
+  {
+    int32_t tot;
+    int32_t dbase = cta_exclusive_scan(totals[threadIdx.x], wsum, &tot);   // digit d = threadIdx.x
+    tile_off[threadIdx.x] = dbase + hist[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  }
   int64_t base = (int64_t)blockIdx.x * kTile;
   // a tile is processed in kItems rounds of kThreads consecutive items; within
   // a round items are ranked warp by warp, lanes in order: the scatter is stable
@@ -104,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint64_t* kin, 
 size_t stiv_sort_scratch_impl(int64_t n) {
   int64_t ntiles = (n + kTile - 1) / kTile;
   if (ntiles < 1) ntiles = 1;
-  return sizeof(int32_t) * (size_t)(kRadix * ntiles) + 256;
+  return sizeof(int32_t) * (size_t)(kRadix * ntiles + kRadix) + 256;
 }
 
 // Sorts n (or *n_dev if given, <= n) pairs.  Result lands in kout/vout; kin/vin
@@ -117,6 +145,7 @@ int stiv_sort_pairs_impl(cudaStream_t st, int64_t n, int key_bits, const uint64_
   if (ntiles < 1) ntiles = 1;
   if (scratch_bytes < stiv_sort_scratch_impl(n)) return STIV_ERR_ARG;
   int32_t* hist = (int32_t*)scratch;
+  int32_t* totals = hist + (size_t)kRadix * ntiles;
   int passes = (key_bits + 7) / 8;
   if (passes == 0) {
     if (n > 0) {
@@ -139,8 +168,9 @@ int stiv_sort_pairs_impl(cudaStream_t st, int64_t n, int key_bits, const uint64_
   for (int ps = 0; ps < passes; ++ps) {
     int shift = 8 * ps;
     hist_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(ka, n_dev, n, shift, (int)ntiles, hist);
-    scan_kernel<<<1, 1024, 0, st>>>(hist, (int64_t)kRadix * ntiles);
-    scatter_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(ka, va, kb, vb, n_dev, n, shift, (int)ntiles, hist);
+    scan_kernel<<<kRadix, kThreads, 0, st>>>(hist, (int)ntiles, totals);
+    scatter_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(ka, va, kb, vb, n_dev, n, shift, (int)ntiles, hist,
+                                                          totals);
     if (cudaGetLastError() != cudaSuccess) return STIV_ERR_CUDA;
     uint64_t* tk = ka; ka = kb; kb = tk;
     int32_t* tv = va; va = vb; vb = tv;

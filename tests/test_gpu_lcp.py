@@ -169,6 +169,34 @@ def test_lcp_solve_brute_force(orc, n):
         assert np.allclose(x, sols[0], rtol=1e-9, atol=1e-12)
 
 
+def test_lcp_solve_large_sparse(orc):
+    """A 4000-row sparse, diagonally dominant LCP (too large for the solve's
+    shared-memory staging: the vectors stay in global scratch): the oracle's
+    minimum-map Newton solution."""
+    rng = np.random.default_rng(7)
+    n = 4000
+    B = np.zeros((n, n))
+    for i in range(n):
+        for j in rng.choice(n, 3, replace=False):
+            if j != i:
+                v = rng.uniform(-0.3, 0.3)
+                B[i, j] += v
+                B[j, i] += v
+    B += np.diag(np.abs(B).sum(axis=1) + rng.uniform(0.5, 2.0, n))
+    q = rng.normal(size=n)
+    x_o, _, res_o = L.minmap_newton(B, q)
+    assert res_o <= 1e-12
+    nz = B != 0
+    rp = np.concatenate([[0], np.cumsum(nz.sum(axis=1))])
+    cols = np.nonzero(nz)[1]
+    lcp = S.ContactLCP()
+    lcp.load_csr(rp, cols, B[nz], q)
+    res = lcp.solve(S.Stiv(), tol=1e-12)
+    x = res["lam"].cpu().numpy()
+    assert res["status"] == 0, res
+    assert np.all(np.abs(x - x_o) <= 1e-10 * np.abs(x_o).max())
+
+
 def test_lcp_degenerate_cases(orc):
     """No contact volumes: an empty matrix and a solve that returns at once;
     q >= 0: lambda = 0 without a Newton step."""

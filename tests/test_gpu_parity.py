@@ -46,7 +46,7 @@ def test_sort_table3_fixture():
     assert icb.tolist() == t["scatter_Icb"]
 
 
-@pytest.mark.parametrize("n,bits_", [(1, 8), (1000, 12), (70000, 40), (300000, 64)])
+@pytest.mark.parametrize("n,bits_", [(1, 8), (1000, 12), (70000, 40), (300000, 64), (3000001, 35)])
 def test_sort_random_stable(n, bits_):
     rng = np.random.default_rng(n)
     k = rng.integers(0, 2 ** min(bits_, 62), size=n, dtype=np.int64)
