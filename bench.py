@@ -36,6 +36,17 @@ FP64_PEAK_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor), nominal
 # of the FP64 contact test), counted by tests/golden/make_narrow_ops.py
 NARROW_OPS = os.path.join(ROOT, "tests", "golden", "narrow_ops_per_pair.json")
 NARROW_STAGES = ("patch_pairs", "narrow", "pieces", "fp64")
+
+# DRAM traffic of the narrow phase (patch_pairs + narrow + pieces + fp64
+# kernels), dram__bytes_read.sum + dram__bytes_write.sum from one ncu --set full
+# capture of one launch each on the 144-vesicle piece of the 58% lattice
+# (MIXED), per primitive pair of the exact box test there (1877492 pairs); it
+# is scaled to a launch by the pairs the launch processes.  The figure belongs
+# to the kernels as captured: if csrc/narrow.cu differs from the captured
+# source (its SHA-256 prefix below), the traffic is reported as null.
+NARROW_TRAFFIC_BYTES_144 = 62169088.0
+NARROW_TRAFFIC_PAIRS_144 = 1877492.0
+NARROW_TRAFFIC_SRC_SHA256 = "071f992ab93ef5b6"
 METRIC = "vesicle-steps/s of detect+V+∇V at p=16→32, 58% vf; % of roofline vs FP64 form"
 UNIT = "vesicle-steps/s"
 
@@ -443,6 +454,14 @@ def run_ours(args, rank, world, local):
     if roof.get("achieved") is not None:
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
+    if dom == "narrow_phase":
+        import hashlib
+        src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1812_04719_gb300", "csrc", "narrow.cu")
+        with open(src, "rb") as fsrc:
+            same = hashlib.sha256(fsrc.read()).hexdigest()[:16] == NARROW_TRAFFIC_SRC_SHA256
+        if same:
+            roof["traffic"] = NARROW_TRAFFIC_BYTES_144 * float(counts[S.C_PRIM]) / NARROW_TRAFFIC_PAIRS_144
+            roof["traffic_unit"] = "bytes per launch (ncu on the 144-vesicle piece, scaled by primitive pairs)"
     roof["avg_launch_ms"] = stage_group[dom]
     launches = int(sum(v[0] for v in prof_tot.values()))
 
