@@ -69,6 +69,7 @@ def parse():
                     help="smaller piece of the 58%% lattice (e.g. 6,6,2) for profiling; default: the 1440 scene")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lcp", action="store_true", help="skip timing the contact LCP (assembly + solve)")
+    ap.add_argument("--no-fidelity", action="store_true", help="skip the mesh-fidelity diagnostic")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -526,6 +527,32 @@ def run_ours(args, rank, world, local):
                    "max_abs_phi": float(info[1]), "status": int(info[3]),
                    "M": "per vesicle I + (1/n_v) 1 1^T (x) I_3"}
 
+    # mesh fidelity of the step's meshes (Sec. 3.1.2, Fig. 6): the distance
+    # between each order-2p triangle mesh and its smooth order-p surface on
+    # the 4x upsampled grid; a diagnostic beside the step
+    fid_rec = None
+    if not args.no_fidelity:
+        eng.step(ds, grad=True, use_graph=True, stream=stream)
+        err = torch.zeros(ds.n, 2, dtype=torch.float64, device=dev)
+        ms_f = []
+        for k in range(4):
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = S.lib().stiv_mesh_fidelity(eng.h, st, ds.n, ds.p_max, ds.p.data_ptr(), ds.coef_off.data_ptr(),
+                                            ds.coef.data_ptr(), ds.vert_off.data_ptr(), ds.verts.data_ptr(), 4,
+                                            err.data_ptr())
+            assert rc == S.STIV_OK, rc
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            S.stiv_profile_read(eng.h)
+            if k >= 1:
+                ms_f.append(e0.elapsed_time(e1))
+        from paper_1812_04719_gb300 import scenegen as G
+        e = err.cpu().numpy()
+        fid_rec = {"factor": 4, "ms": float(np.mean(ms_f)), "max_err": float(e.max()),
+                   "median_err": float(np.median(e)), "max_err_over_R0": float(e.max() / G.R0_PAPER),
+                   "points_per_launch": int(sum(2 * (4 * int(P) + 1) * 8 * int(P) for P in sc.P))}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         nv, secs, threads, desc = oracle_sample(sc, args.cpu_seconds)
@@ -549,7 +576,7 @@ def run_ours(args, rank, world, local):
                            "prim_pairs_tested": int(counts[S.C_PRIM]), "patch_pairs": int(counts[S.C_PATCH]),
                            "prim_pairs_fp64": int(counts[S.C_EXACT])},
                 "roofline": roof, "roofline_fp64_kernel": roof_fp64, "fp64_form": fp64_form,
-                "cpu_baseline": cpu, "e2e": e2e, "lcp": lcp_rec,
+                "cpu_baseline": cpu, "e2e": e2e, "lcp": lcp_rec, "mesh_fidelity": fid_rec,
                 "gpu_launches": launches,
                 "clocks": clk, "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda x: -x[1])},
                 "wall_s": t_wall}

@@ -205,6 +205,24 @@ int stiv_grad_to_coef(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max
                       const int64_t* coef_off_dev, const int64_t* vert_off_dev,
                       const double* gX_dev, double* gcoef_dev);
 
+/* Mesh fidelity (Sec. 3.1.2; Fig. 6): how far each vesicle's order-2p
+ * triangle mesh (verts_dev as written by stiv_upsample, FP64 or FP32 per the
+ * handle's precision) lies from its smooth order-p surface (coef_dev),
+ * ||X^{q^up} - X(phi, theta)||_inf, estimated on the order-(factor 2p)
+ * grid: its Gauss-Legendre rings and factor x 2 x 2p longitudes, poles
+ * excluded.  The mesh is read as a map from parameter space: on the cell
+ * [theta_i, theta_{i+1}] x [phi_j, phi_{j+1}] with fractions a (theta), b
+ * (phi) it is the triangle (i,j), (i+1,j), (i+1,j+1) for a >= b and (i,j),
+ * (i+1,j+1), (i,j+1) for a < b; beyond the first and last rings, the pole
+ * fans.  err_dev [n_ves][2] (device, caller-owned) gets, per vesicle and time
+ * level (X0, X1), the largest Euclidean distance between mesh and series at
+ * those points; the paper asks for err < alpha d_m.  factor in [1, 8] (the
+ * paper's estimate uses 4).  FP64 evaluation.  Returns STIV_ERR_ARG for a
+ * NULL array or a parameter out of range. */
+int stiv_mesh_fidelity(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                       const int64_t* coef_off_dev, const double* coef_dev, const int64_t* vert_off_dev,
+                       const void* verts_dev, int32_t factor, double* err_dev);
+
 /* The whole per-step path: upsample + detect + stiv_grad.  With use_graph = 1
  * the launches are captured into a CUDA graph on the first call and replayed
  * on later calls with the same arguments.  coef_dev = NULL skips the

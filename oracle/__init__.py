@@ -54,6 +54,10 @@ def lib() -> ctypes.CDLL:
             L.orc_synth.restype = None
             L.orc_synth_vesicle.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
             L.orc_synth_vesicle.restype = None
+            L.orc_mesh_fidelity.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
+            L.orc_mesh_fidelity.restype = ctypes.c_double
+            L.orc_mesh_point.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp]
+            L.orc_mesh_point.restype = None
             L.orc_synth_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
             L.orc_synth_adjoint.restype = None
             L.orc_triangles.argtypes = [ctypes.c_int, ip]
@@ -118,6 +122,24 @@ def synth(p: int, P: int, coef: np.ndarray) -> np.ndarray:
     assert coef.shape == ((p + 1) ** 2,)
     out = np.zeros(nverts(P))
     lib().orc_synth(p, P, _d(coef), _d(out))
+    return out
+
+
+def mesh_fidelity(p: int, P: int, coef: np.ndarray, X: np.ndarray, factor: int = 4) -> float:
+    """Sec. 3.1.2 / Fig. 6: max over the order-(factor P) grid of the distance
+    between the order-P triangle mesh (read in parameter space) and the smooth
+    order-p surface.  coef [3][(p+1)^2] and X [3][n_v(P)] of one time level."""
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    assert coef.shape == (3, (p + 1) ** 2) and X.shape == (3, nverts(P))
+    return float(lib().orc_mesh_fidelity(p, P, factor, _d(coef), _d(X)))
+
+
+def mesh_point(P: int, X: np.ndarray, theta: float, phi: float) -> np.ndarray:
+    """The order-P triangle mesh X [3][n_v(P)] at parameter (theta, phi)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.zeros(3)
+    lib().orc_mesh_point(P, _d(X), float(theta), float(phi), _d(out))
     return out
 
 

@@ -164,6 +164,75 @@ void orc_synth_vesicle(int p, int P, const double* coef, double* X) {
   for (int f = 0; f < 6; ++f) orc_synth(p, P, coef + (size_t)f * nc, X + (size_t)f * nv);
 }
 
+/* Mesh fidelity (Sec. 3.1.2: the triangle mesh of the q^up-grid must stay
+ * within alpha d_m of the smooth surface, ||X^{q^up} - X(phi, theta)||_inf;
+ * Fig. 6 estimates the smooth surface by a 4x upsampled grid).  The mesh is
+ * read as a map from parameter space: on the grid cell [theta_i,
+ * theta_{i+1}] x [phi_j, phi_{j+1}] with a = (theta - theta_i) /
+ * (theta_{i+1} - theta_i), b = (phi - phi_j) / (phi_{j+1} - phi_j) it is the
+ * planar triangle [q, r, s] = [(i,j), (i+1,j), (i+1,j+1)] for a >= b,
+ * q + a (r - q) + b (s - r), and [q, s, u] with u = (i,j+1) for a < b,
+ * q + b (u - q) + a (s - u); above ring 0 (below ring P) it is the pole fan
+ * N + t ((1-b) X_{0,j} + b X_{0,j+1} - N) with t = theta / theta_0 (S and
+ * t = (pi - theta) / (pi - theta_P)).  The error of one field triple is
+ * the largest Euclidean distance |mesh(theta, phi) - X(theta, phi)| over the
+ * points of the order-(factor P) grid (its Gauss-Legendre rings and
+ * phi_k = pi k / (factor P), poles excluded).  X: [3][n_v(P)] mesh vertices
+ * of one time level; coef: [3][(p+1)^2]. */
+/* The mesh point at parameter (theta, phi) (the map described above); X: [3][n_v(P)]. */
+void orc_mesh_point(int P, const double* X, double theta, double phi, double* out) {
+  int W = 2 * P, nv = orc_nverts(P);
+  double* th = (double*)malloc(sizeof(double) * (P + 1));
+  grid_angles(P, th);
+  double u = phi / (ORC_PI / P);        /* longitude in cell units */
+  int j = (int)floor(u);
+  double b = u - j;
+  j = ((j % W) + W) % W;
+  int j1 = (j + 1) % W;
+  for (int c = 0; c < 3; ++c) {
+    const double* x = X + (size_t)c * nv;
+    double m;
+    if (theta < th[0]) {
+      double t = theta / th[0], N = x[2 * P * (P + 1)];
+      m = N + t * ((1.0 - b) * x[j] + b * x[j1] - N);
+    } else if (theta > th[P]) {
+      double t = (ORC_PI - theta) / (ORC_PI - th[P]), Sv = x[2 * P * (P + 1) + 1];
+      m = Sv + t * ((1.0 - b) * x[P * W + j] + b * x[P * W + j1] - Sv);
+    } else {
+      int i = 0;
+      while (i + 1 < P && th[i + 1] <= theta) ++i;
+      double a = (theta - th[i]) / (th[i + 1] - th[i]);
+      double q = x[i * W + j], rr = x[(i + 1) * W + j], sv = x[(i + 1) * W + j1], uu = x[i * W + j1];
+      m = a >= b ? q + a * (rr - q) + b * (sv - rr) : q + b * (uu - q) + a * (sv - uu);
+    }
+    out[c] = m;
+  }
+  free(th);
+}
+
+double orc_mesh_fidelity(int p, int P, int factor, const double* coef, const double* X) {
+  int Pf = factor * P, nc = (p + 1) * (p + 1);
+  double* thf = (double*)malloc(sizeof(double) * (Pf + 1));
+  double* work = (double*)malloc(sizeof(double) * (p + 1) * (p + 2) / 2);
+  double* row = (double*)malloc(sizeof(double) * nc);
+  grid_angles(Pf, thf);
+  double worst = 0.0;
+  for (int r = 0; r <= Pf; ++r) {
+    for (int k = 0; k < 2 * Pf; ++k) {
+      double theta = thf[r], phi = ORC_PI * k / Pf, mp[3], d2 = 0.0;
+      orc_mesh_point(P, X, theta, phi, mp);
+      for (int c = 0; c < 3; ++c) {
+        double e = mp[c] - sh_eval(p, coef + (size_t)c * nc, theta, phi, work, row);
+        d2 += e * e;
+      }
+      double d = sqrt(d2);
+      if (d > worst) worst = d;
+    }
+  }
+  free(thf); free(work); free(row);
+  return worst;
+}
+
 /* Fig. 3: split each grid quad along the diagonal (i,j)-(i+1,j+1); close the
  * poles with triangle fans.  Orientation is chosen so that normals point out
  * of the surface (theta runs south, phi east).  tri: [n_f][3].  Triangle id:

@@ -192,6 +192,7 @@ extern "C" int stiv_destroy(stiv_handle* h) {
   if (h->tc_status) cudaFree(h->tc_status);
   if (h->lcp_ws) cudaFree(h->lcp_ws);
   if (h->lcp_ws2) cudaFree(h->lcp_ws2);
+  if (h->fid_x) cudaFree(h->fid_x);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->ws) cudaFree(h->ws);
   stiv_profile(h, 0);

@@ -46,6 +46,8 @@ struct stiv_handle {
   size_t lcp_ws_bytes;
   void* lcp_ws2;
   size_t lcp_ws2_bytes;
+  double* fid_x;          // fine-grid nodes of the mesh-fidelity estimate
+  size_t fid_x_bytes;
   // launch shapes of the narrow phase (0 = default), set by stiv_autotune
   int32_t tune[STIV_NTUNE];
   void* ws;

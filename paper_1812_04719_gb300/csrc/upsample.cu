@@ -161,6 +161,258 @@ __global__ void __launch_bounds__(256) synth_kernel(synth_args a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mesh fidelity (Sec. 3.1.2: the q^up-grid triangle mesh must stay within
+// alpha d_m of the smooth surface, ||X^{q^up} - X(phi, theta)||_inf; Fig. 6
+// estimates the smooth surface on a 4x upsampled grid).  The mesh is read as
+// a map from parameter space: on the grid cell [theta_i, theta_{i+1}] x
+// [phi_j, phi_{j+1}], with a, b the cell fractions in theta and phi, the
+// triangle [(i,j), (i+1,j), (i+1,j+1)] for a >= b and [(i,j), (i+1,j+1),
+// (i,j+1)] for a < b (the Fig. 3 split); above ring 0 and below ring P the
+// pole fans.  One CTA per (vesicle, time level) takes the largest distance
+// between that map and the order-p series over the order-(factor P) grid
+// (its Gauss-Legendre rings, phi_k = pi k / (factor P); poles excluded).
+// ---------------------------------------------------------------------------
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Column m of the normalised associated Legendre table at x = cos(theta),
+// s = sin(theta), no Condon-Shortley phase, sqrt(2) folded in for m > 0:
+// L[n(n+1)/2 + m] for n = m .. p, by the recurrences of tables_kernel with
+// their coefficients tabulated: dg[k] = sqrt((2k+1)/(2k)), sd[m] =
+// sqrt(2m+3), ra and rb[n(n+1)/2+m] the three-term coefficients of (n, m).
+__device__ void legendre_column_tab(int p, int m, double x, double s, const double* dg, const double* sd,
+                                    const double* ra, const double* rb, double* L) {
+  double d = 0.28209479177387814347;  // 1/sqrt(4 pi)
+  for (int k = 1; k <= m; ++k) d = dg[k] * s * d;
+  double r2 = m ? 1.41421356237309504880 : 1.0;
+  L[m * (m + 1) / 2 + m] = d * r2;
+  if (m < p) {
+    double e = sd[m] * x * d;
+    L[(m + 1) * (m + 2) / 2 + m] = e * r2;
+    double l2 = d, l1 = e;
+    for (int n = m + 2; n <= p; ++n) {
+      int idx = n * (n + 1) / 2 + m;
+      double l0 = ra[idx] * (x * l1 - rb[idx] * l2);
+      L[idx] = l0 * r2;
+      l2 = l1; l1 = l0;
+    }
+  }
+}
+
+struct fid_args {
+  const int32_t* p;
+  const int64_t* coef_off;
+  const double* coef;
+  const int64_t* vert_off;
+  const void* verts;
+  int mixed;
+  int factor;
+  const double* theta[STIV_MAX_P + 1];
+  const double* xfine;   // fine-grid nodes x = cos(theta), order factor*2p at xfine + xoff[p]
+  int xoff[STIV_MAX_P + 1];
+  double* err;
+};
+
+// Gauss-Legendre node x_i (descending) of order n, Newton's method on P_n from
+// the same start as gl_node, at most 8 steps (quadratic convergence reaches
+// the last bits in about 5), stopping once a step is below 4e-16 |x|.
+__device__ double fine_node(int n, int i) {
+  double z = cospi((i + 0.75) / (n + 0.5));
+  for (int it = 0; it < 8; ++it) {
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1; p1 = p2;
+    }
+    double dz = p1 / (n * (z * p1 - p0) / (z * z - 1.0));
+    z -= dz;
+    if (fabs(dz) <= 4e-16 * fabs(z)) break;
+  }
+  return z;
+}
+
+// Fine-grid Gauss-Legendre nodes for every order p <= p_max (computed once per
+// call, not per CTA): order Pf = factor 2p at xs + off(p), off(p) = sum over
+// p' < p of (factor 2p' + 1).
+__global__ void fine_nodes_kernel(int p_max, int factor, double* xs) {
+  int total = 0;
+  for (int p = 1; p <= p_max; ++p) total += factor * 2 * p + 1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    int p = 1, off = 0;
+    while (e >= off + factor * 2 * p + 1) { off += factor * 2 * p + 1; ++p; }
+    int Pf = factor * 2 * p, r = e - off;
+    int ih = r <= Pf / 2 ? r : Pf - r;
+    double x = (2 * ih == Pf) ? 0.0 : fine_node(Pf + 1, ih);
+    xs[e] = r > Pf / 2 ? -x : x;
+  }
+}
+
+__device__ __forceinline__ double vert_at(const fid_args& a, size_t idx) {
+  return a.mixed ? (double)((const float*)a.verts)[idx] : ((const double*)a.verts)[idx];
+}
+
+constexpr int FRMAX = 8;   // fine rings per pass at most
+
+// Fine rings per pass for order p: as many as keep the pass's point tasks
+// (one per ring and longitude quarter) within one round of 256 threads.
+__host__ __device__ inline int fid_rings(int p, int factor) {
+  int nq = factor * p + 1, r = 256 / nq;
+  return r < 1 ? 1 : (r > FRMAX ? FRMAX : r);
+}
+
+__host__ __device__ inline size_t fid_smem_doubles(int p, int factor) {
+  int P = 2 * p, Pf = factor * P, nl = (p + 1) * (p + 2) / 2, FR = fid_rings(p, factor);
+  return (size_t)3 * (p + 1) * (p + 1) + (P + 1) + (Pf + 1) + (size_t)FR * nl + (size_t)FR * 3 * (2 * p + 1) +
+         (size_t)(Pf / 2 + 1) * 2 * (p + 1) + (Pf + 1) + 2 * (size_t)nl + 2 * (size_t)(p + 1);
+}
+
+// The mesh's value for coordinate field o at a fine point: ring zone / cell
+// (i, a_) or pole fraction tp; longitude cell j, j1 = j + 1 (mod 2P), b.
+__device__ __forceinline__ double mesh_value(const fid_args& a, size_t o, int P, int W, int zone, int i, double a_,
+                                             double tp, int j, int j1, double b) {
+  if (zone == 0) {
+    double N = vert_at(a, o + 2 * (size_t)P * (P + 1));
+    return N + tp * ((1.0 - b) * vert_at(a, o + j) + b * vert_at(a, o + j1) - N);
+  }
+  if (zone == 2) {
+    double S = vert_at(a, o + 2 * (size_t)P * (P + 1) + 1);
+    return S + tp * ((1.0 - b) * vert_at(a, o + (size_t)P * W + j) + b * vert_at(a, o + (size_t)P * W + j1) - S);
+  }
+  double q = vert_at(a, o + (size_t)i * W + j), rr = vert_at(a, o + (size_t)(i + 1) * W + j);
+  double s3 = vert_at(a, o + (size_t)(i + 1) * W + j1), u = vert_at(a, o + (size_t)i * W + j1);
+  return a_ >= b ? q + a_ * (rr - q) + b * (s3 - rr) : q + b * (u - q) + a_ * (s3 - u);
+}
+
+// One CTA per (vesicle, time level), FR fine rings per pass.  The series is
+// evaluated like the synthesis: ring sums G(m), then per longitude pair the
+// even and odd partial Fourier sums, which give the four longitudes
+// phi_k, pi - phi_k, pi + phi_k and 2 pi - phi_k (k <= Pf / 2) at once;
+// cos(m phi_k), sin(m phi_k) come from a table built per CTA.
+__global__ void __launch_bounds__(256) fidelity_kernel(fid_args a) {
+  extern __shared__ double sm[];
+  __shared__ double red[256 / 32];
+  int v = blockIdx.x, t = blockIdx.y;
+  int p = a.p[v], P = 2 * p, Pf = a.factor * P, W = 2 * P, nv = 2 * P * (P + 1) + 2;
+  int nc = (p + 1) * (p + 1), nl = (p + 1) * (p + 2) / 2, ns = 2 * p + 1, nq = Pf / 2 + 1;
+  int FR = fid_rings(p, a.factor);
+  double* C = sm;                   // [3][nc]
+  double* thc = C + 3 * nc;         // [P+1]  mesh rings (ascending theta)
+  double* xf = thc + (P + 1);       // [Pf+1] fine rings, x = cos(theta)
+  double* L = xf + (Pf + 1);        // [FR][nl] Legendre values of the current rings
+  double* G = L + FR * nl;          // [FR][3][ns] ring sums (slot 0: m=0; 2m-1: cos m; 2m: sin m)
+  double* T = G + FR * 3 * ns;      // [nq][2][p+1] cos, sin (m phi_k), k <= Pf/2
+  double* thf = T + (size_t)nq * 2 * (p + 1);   // [Pf+1] fine ring angles
+  double* ra = thf + (Pf + 1);      // [nl] Legendre recurrence coefficients
+  double* rb = ra + nl;             // [nl]
+  double* dg = rb + nl;             // [p+1]
+  double* sd = dg + (p + 1);        // [p+1]
+  const double* coef = a.coef + a.coef_off[v] + (size_t)t * 3 * nc;
+  for (int k = threadIdx.x; k < 3 * nc; k += blockDim.x) C[k] = coef[k];
+  for (int i = threadIdx.x; i <= P; i += blockDim.x) thc[i] = a.theta[p][i];
+  for (int r = threadIdx.x; r <= Pf; r += blockDim.x) {
+    double x = a.xfine[a.xoff[p] + r];
+    xf[r] = x;
+    thf[r] = acos(x);
+  }
+  for (int m = threadIdx.x; m <= p; m += blockDim.x) {
+    dg[m] = m ? sqrt((2.0 * m + 1.0) / (2.0 * m)) : 0.0;
+    sd[m] = sqrt(2.0 * m + 3.0);
+  }
+  for (int e = threadIdx.x; e < nl; e += blockDim.x) {
+    int n = 0;
+    while ((n + 1) * (n + 2) / 2 <= e) ++n;
+    int m = e - n * (n + 1) / 2;
+    if (n >= m + 2) {
+      ra[e] = sqrt((4.0 * n * n - 1.0) / ((double)(n - m) * (n + m)));
+      rb[e] = sqrt(((double)(n - 1 - m) * (n - 1 + m)) / (4.0 * (n - 1) * (n - 1) - 1.0));
+    } else {
+      ra[e] = 0.0; rb[e] = 0.0;
+    }
+  }
+  for (int e = threadIdx.x; e < nq * (p + 1); e += blockDim.x) {
+    int k = e / (p + 1), m = e % (p + 1);
+    int kk = (m * k) % (2 * Pf);            // exact argument reduction
+    double sv, cv;
+    sincospi((double)kk / Pf, &sv, &cv);
+    T[(size_t)k * 2 * (p + 1) + m] = cv;
+    T[(size_t)k * 2 * (p + 1) + (p + 1) + m] = sv;
+  }
+  __syncthreads();
+  size_t base = a.vert_off[v] + (size_t)t * 3 * nv;
+  double worst2 = 0.0, inv_factor = 1.0 / a.factor;
+  for (int r0 = 0; r0 <= Pf; r0 += FR) {
+    int nr = Pf + 1 - r0 < FR ? Pf + 1 - r0 : FR;
+    if (threadIdx.x < nr * (p + 1)) {
+      int rr = threadIdx.x / (p + 1), m = threadIdx.x % (p + 1);
+      double x = xf[r0 + rr];
+      legendre_column_tab(p, m, x, sqrt((1.0 - x) * (1.0 + x)), dg, sd, ra, rb, L + rr * nl);
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < nr * 3 * ns; task += blockDim.x) {
+      int rr = task / (3 * ns), rem = task % (3 * ns), f = rem / ns, sl = rem % ns, m = (sl + 1) >> 1;
+      int sgn = sl == 0 ? 0 : ((sl & 1) ? 1 : -1);
+      const double* Lr = L + rr * nl;
+      double acc = 0.0;
+      for (int n = m; n <= p; ++n) acc = fma(C[f * nc + n * n + n + sgn * m], Lr[n * (n + 1) / 2 + m], acc);
+      G[(rr * 3 + f) * ns + sl] = acc;
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < nr * nq; task += blockDim.x) {
+      int rr = task / nq, q = task % nq;
+      double theta = thf[r0 + rr];
+      int zone = 1, i = 0;
+      double a_ = 0.0, tp = 0.0;
+      if (theta < thc[0]) { zone = 0; tp = theta / thc[0]; }
+      else if (theta > thc[P]) { zone = 2; tp = (kPi - theta) / (kPi - thc[P]); }
+      else {
+        while (i + 1 < P && thc[i + 1] <= theta) ++i;
+        a_ = (theta - thc[i]) / (thc[i + 1] - thc[i]);
+      }
+      const double* cs = T + (size_t)q * 2 * (p + 1);
+      const double* sn = cs + (p + 1);
+      int kq[4] = {q, Pf - q, Pf + q, (2 * Pf - q) % (2 * Pf)};
+      double val[4][3];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        const double* g = G + (size_t)(rr * 3 + f) * ns;
+        double Ce = g[0], Co = 0.0, Se = 0.0, So = 0.0;
+        for (int m = 1; m <= p; m += 2) { Co = fma(g[2 * m - 1], cs[m], Co); So = fma(g[2 * m], sn[m], So); }
+        for (int m = 2; m <= p; m += 2) { Ce = fma(g[2 * m - 1], cs[m], Ce); Se = fma(g[2 * m], sn[m], Se); }
+        val[0][f] = (Ce + Co) + (Se + So);     // phi_q
+        val[1][f] = (Ce - Co) + (So - Se);     // pi - phi_q
+        val[2][f] = (Ce - Co) + (Se - So);     // pi + phi_q
+        val[3][f] = (Ce + Co) - (Se + So);     // 2 pi - phi_q
+      }
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        int k = kq[w];
+        bool dup = (w == 1 && k == kq[0]) || (w == 2 && (k == kq[1] || k >= 2 * Pf)) ||
+                   (w == 3 && (k == kq[0] || k == kq[2]));
+        if (dup) continue;
+        int j = k / a.factor, j1 = (j + 1) % W;
+        double b = (double)(k % a.factor) * inv_factor;
+        double d2 = 0.0;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          double e = mesh_value(a, base + (size_t)f * nv, P, W, zone, i, a_, tp, j, j1, b) - val[w][f];
+          d2 += e * e;
+        }
+        worst2 = fmax(worst2, d2);   // squared distance; one square root at the end
+      }
+    }
+    __syncthreads();   // L and G are rewritten for the next rings
+  }
+  for (int off = 16; off > 0; off >>= 1) worst2 = fmax(worst2, __shfl_xor_sync(0xffffffffu, worst2, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = worst2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double w = red[0];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) w = fmax(w, red[q]);
+    a.err[2 * (size_t)v + t] = sqrt(w);
+  }
+}
+
 }  // namespace
 
 int stiv_ensure_tables(stiv_handle* h, cudaStream_t st, int p) {
@@ -205,6 +457,46 @@ extern "C" int stiv_upsample(stiv_handle* h, void* stream, int32_t n_ves, int32_
   STIV_CUDA(h, cudaFuncSetAttribute(synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   STIV_PROF(h, st, "synth");
   synth_kernel<<<dim3(n_ves, 2), 256, smem, st>>>(a);
+  STIV_LAUNCH(h);
+  return STIV_OK;
+}
+
+extern "C" int stiv_mesh_fidelity(stiv_handle* h, void* stream, int32_t n_ves, int32_t p_max, const int32_t* p_dev,
+                                  const int64_t* coef_off_dev, const double* coef_dev, const int64_t* vert_off_dev,
+                                  const void* verts_dev, int32_t factor, double* err_dev) {
+  if (!h || n_ves < 0 || p_max < 1 || p_max > STIV_MAX_P || factor < 1 || factor > 8) return STIV_ERR_ARG;
+  if (n_ves == 0) return STIV_OK;
+  if (!p_dev || !coef_off_dev || !coef_dev || !vert_off_dev || !verts_dev || !err_dev) return STIV_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  fid_args a;
+  a.p = p_dev; a.coef_off = coef_off_dev; a.coef = coef_dev; a.vert_off = vert_off_dev; a.verts = verts_dev;
+  a.mixed = h->prm.precision == STIV_MIXED; a.factor = factor; a.err = err_dev;
+  for (int p = 0; p <= STIV_MAX_P; ++p) a.theta[p] = nullptr;
+  for (int p = 1; p <= p_max; ++p) {
+    int rc = stiv_ensure_tables(h, st, p);
+    if (rc) return rc;
+    a.theta[p] = h->tab[p].theta;
+  }
+  int nx = 0;
+  for (int p = 1; p <= p_max; ++p) { a.xoff[p] = nx; nx += factor * 2 * p + 1; }
+  a.xoff[0] = 0;
+  if (sizeof(double) * (size_t)nx > h->fid_x_bytes) {
+    if (h->fid_x) { STIV_CUDA(h, cudaFree(h->fid_x)); h->fid_x = nullptr; h->fid_x_bytes = 0; }
+    STIV_CUDA(h, cudaMalloc(&h->fid_x, sizeof(double) * (size_t)nx));
+    h->fid_x_bytes = sizeof(double) * (size_t)nx;
+  }
+  a.xfine = h->fid_x;
+  size_t smem = 0;
+  for (int p = 1; p <= p_max; ++p) {
+    size_t b = sizeof(double) * fid_smem_doubles(p, factor);
+    smem = b > smem ? b : smem;
+  }
+  if (smem > 220 * 1024) return STIV_ERR_ARG;
+  if (smem > 48 * 1024)
+    STIV_CUDA(h, cudaFuncSetAttribute(fidelity_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  STIV_PROF_N(h, st, "mesh_fidelity", 2);
+  fine_nodes_kernel<<<(nx + 127) / 128, 128, 0, st>>>(p_max, factor, h->fid_x);
+  fidelity_kernel<<<dim3(n_ves, 2), 256, smem, st>>>(a);
   STIV_LAUNCH(h);
   return STIV_OK;
 }

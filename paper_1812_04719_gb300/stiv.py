@@ -34,7 +34,8 @@ EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_
            "stiv_upsample", "stiv_detect", "stiv_stiv", "stiv_stiv_grad", "stiv_grad_scatter",
            "stiv_grad_to_coef", "stiv_step", "stiv_sync_counts", "stiv_sort_scratch_bytes", "stiv_sort_pairs",
            "stiv_profile", "stiv_profile_read", "stiv_sort_pairs_static", "stiv_autotune", "stiv_set_tuning",
-           "stiv_wait_selftest", "stiv_lcp_matrix", "stiv_lcp_solve"]
+           "stiv_wait_selftest", "stiv_lcp_matrix", "stiv_lcp_solve",
+           "stiv_mesh_fidelity"]
 TUNE_NAMES = ("narrow_ctas_per_sm", "pieces_ctas_per_sm", "fp64_blocks_per_sm", "patch_blocks_per_sm",
               "piece_levels")
 SORT_STATIC_MAX = 1 << 20
@@ -106,6 +107,7 @@ def lib() -> ctypes.CDLL:
     L.stiv_wait_selftest.argtypes = [vp, i64, vp]
     L.stiv_lcp_matrix.argtypes = [vp, vp, i32, i32, P(StivPairs), P(StivContacts), vp, vp, vp, vp, vp, vp, vp,
                                   P(StivLcp)]
+    L.stiv_mesh_fidelity.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, i32, vp]
     L.stiv_lcp_solve.argtypes = [vp, vp, P(StivLcp), ctypes.c_double, i32, i32, vp, vp]
     L.stiv_profile.argtypes = [vp, i32]
     L.stiv_profile_read.argtypes = [vp, i32, vp, vp, vp, vp]
@@ -393,6 +395,16 @@ class Stiv:
             res["best_ms"] = best.value
             return res
         raise StivError(STIV_ERR_CAPACITY, "autotune: capacities kept overflowing")
+
+    def mesh_fidelity(self, ds: DeviceScene, factor: int = 4, stream=None) -> torch.Tensor:
+        """Per vesicle and time level, the largest distance between the order-2p
+        triangle mesh in ds.verts (as upsampled) and the smooth order-p surface,
+        on the order-(factor 2p) grid (Sec. 3.1.2, Fig. 6).  float64 [n, 2]."""
+        err = torch.zeros(ds.n, 2, dtype=torch.float64, device=self.device)
+        _check(lib().stiv_mesh_fidelity(self.h, _stream(stream), ds.n, ds.p_max, _ptr(ds.p), _ptr(ds.coef_off),
+                                        _ptr(ds.coef), _ptr(ds.vert_off), _ptr(ds.verts), int(factor), _ptr(err)),
+               "stiv_mesh_fidelity")
+        return err
 
     def set_tuning(self, **values):
         """Pin launch shapes by name (see TUNE_NAMES); unnamed ones keep 0 (default)."""
