@@ -96,7 +96,15 @@ typedef struct stiv_params {
   int32_t exact_only;  /* 1: skip the certified FP32 rejection and run the FP64 contact
                           test on every primitive pair whose boxes overlap (same results,
                           slower; for cross-checks) */
+  int32_t velocity;    /* enum stiv_velocity: the reading of U_k in Eq. 3.2 */
 } stiv_params;
+
+/* U_k in Eq. 3.2.  RELATIVE (default): the velocity of the contact point
+ * relative to the opposite primitive (VF: D_p - sum beta_i D_i; EE:
+ * D_q(u) - D_p(s)), Galilean-invariant.  ABSOLUTE: the literal reading, the
+ * contact point's own velocity (VF: D_p; EE: D_p(s), the point on the first
+ * edge).  Detection does not depend on it. */
+enum stiv_velocity { STIV_VEL_RELATIVE = 0, STIV_VEL_ABSOLUTE = 1 };
 
 /* Candidate vesicle pairs (Alg. 1 output, i < j), sorted by (i, j, shift).
  * shift = 9 (sx+1) + 3 (sy+1) + (sz+1): vesicle j is taken at X + s * box_L. */
@@ -185,6 +193,15 @@ int stiv_stiv_grad(stiv_handle* h, void* stream, int32_t n_ves, const int32_t* p
                    const stiv_contacts* contacts, const int64_t* counts_dev,
                    double* V_contact_dev, double* V_pair_dev,
                    double* grad_dev, int32_t* g_ves_dev, int32_t* g_vid_dev);
+
+/* dV_k/dX0 per contact (the start-of-step positions, X1 fixed): the same
+ * layout and point order as the rows of stiv_stiv_grad (whose g_ves, g_vid
+ * apply), [k][4][3].  With Y = X0 + tau (X1 - X0) and tau following
+ * f(tau; X0) = 0, the rows satisfy dV/dX0 + dV/dX1 = 0 summed over the four
+ * points (a rigid translation of both time levels leaves V unchanged). */
+int stiv_stiv_grad_x0(stiv_handle* h, void* stream, int32_t n_ves, const int32_t* p_dev,
+                      const int64_t* vert_off_dev, const void* verts_dev, const stiv_pairs* cand,
+                      const stiv_contacts* contacts, const int64_t* counts_dev, double* grad_x0_dev);
 
 /* Scatter-add per-contact gradient rows, each scaled by weight_pair[pair] (or
  * 1 if weight_pair is NULL), into a dense array in the vertex layout (only the

@@ -68,8 +68,10 @@ def lib() -> ctypes.CDLL:
             L.orc_candidate_pairs.restype = ctypes.c_int64
             L.orc_ccd_primitive.argtypes = [ctypes.c_int, dp, dp, dp]
             L.orc_stiv_primitive.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
+            L.orc_stiv_primitive_v.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
             L.orc_contacts.argtypes = [ctypes.c_int, ip, lp, dp, ctypes.c_int64, ip, dp,
-                                       ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int,
                                        ctypes.c_int64, ip, ip, ip, ip, dp, dp, dp, dp, dp, ip, ip, lp]
             L.orc_contacts.restype = ctypes.c_int64
             _lib = L
@@ -217,14 +219,18 @@ class Contacts(dict):
 
 
 def contacts(P_ves, X_list_or_flat, pairs, L, eps_dt: float, prune: bool = True,
-             include_ee: bool = True, grad: bool = True, nthreads: int = 0, voff=None):
+             include_ee: bool = True, grad: bool = True, nthreads: int = 0, voff=None,
+             velocity: str = "relative", grad_wrt: str = "X1"):
     """Alg. 2 checkContact over candidate vesicle pairs.
 
     P_ves: grid order per vesicle.  X: either a list of [2][3][n_v] arrays or
     a flat float64 array with offsets ``voff``.  pairs: rows (i, j, sx, sy, sz).
     Returns a dict: pair, type, a, b, tau, w[.,2], V (per contact), V_pair (per
     pair row), grad [.,4,3], gves/gvid [.,4], counts (contacts, prim pairs
-    tested, degenerate, floating-point operations of the contact tests)."""
+    tested, degenerate, floating-point operations of the contact tests).
+    velocity "absolute" takes U_k as the contact point's own velocity (the
+    literal reading); grad_wrt "X0" differentiates with respect to X0."""
+    assert velocity in ("relative", "absolute") and grad_wrt in ("X1", "X0")
     P_ves = np.ascontiguousarray(P_ves, dtype=np.int32)
     if voff is None:
         sizes = [6 * nverts(int(P)) for P in P_ves]
@@ -240,7 +246,8 @@ def contacts(P_ves, X_list_or_flat, pairs, L, eps_dt: float, prune: bool = True,
     V_pair = np.zeros(max(npairs, 1))
     L_ = lib()
     args_head = (len(P_ves), _i(P_ves), _l(voff), _d(flat), npairs, _i(pairs if npairs else np.zeros((1, 5), np.int32)),
-                 _d(Lv), int(prune), int(include_ee), float(eps_dt), int(nthreads))
+                 _d(Lv), int(prune), int(include_ee), float(eps_dt), int(velocity == "absolute"),
+                 int(grad_wrt == "X0"), int(nthreads))
 
     def run(cap):
         c = max(cap, 1)
@@ -260,3 +267,14 @@ def contacts(P_ves, X_list_or_flat, pairs, L, eps_dt: float, prune: bool = True,
     out["V_pair"] = V_pair[:npairs].copy()
     out["counts"] = counts.copy()
     return out
+
+
+def stiv_primitive_variant(kind: str, X0, X1, eps_dt: float, velocity: str = "relative", grad_wrt: str = "X1"):
+    """stiv_primitive with the literal velocity reading and/or the gradient
+    with respect to X0."""
+    X0 = np.ascontiguousarray(X0, dtype=np.float64).reshape(4, 3)
+    X1 = np.ascontiguousarray(X1, dtype=np.float64).reshape(4, 3)
+    out = np.zeros(13)
+    st = lib().orc_stiv_primitive_v(0 if kind == "vf" else 1, _d(X0), _d(X1), float(eps_dt),
+                                    int(velocity == "absolute"), int(grad_wrt == "X0"), _d(out))
+    return st, out[0], out[1:].reshape(4, 3)

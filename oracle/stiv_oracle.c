@@ -577,16 +577,24 @@ static d3 d3lerp(d3 x0, dual t, d3 d) { return d3add(x0, d3scale(t, d)); }
  * same weight |m|/2 of the two edge vectors is used.  The gradient with respect
  * to X1 follows tau through the implicit function f(tau; X1) = 0,
  * d tau = -(df/dX1)/f'(tau), and the inside-test weights through their normal
- * equations.  X0, X1: [4][3].  out: V, then grad [4][3]. */
-static double stiv_pair_dual(int kind, const v3* P0, const v3* P1, double tau, double eps_dt, double* grad) {
+ * equations.  X0, X1: [4][3].  out: V, then grad [4][3].
+ *
+ * Variants (the literal readings): velocity_abs = 1 takes U_k as the
+ * absolute velocity of the contact point instead of the relative one: for VF
+ * the vertex's displacement D_p, for EE that of the point p(s) on the first
+ * edge.  grad_x0 = 1 differentiates with respect to the start positions X0
+ * (X1 fixed) instead: tau follows through f(tau; X0) = 0 the same way. */
+static double stiv_pair_dual(int kind, const v3* P0, const v3* P1, double tau, double eps_dt, int velocity_abs,
+                             int grad_x0, double* grad) {
   d3 X0[4], X1[4], D[4];
   for (int q = 0; q < 4; ++q) {
     X0[q].x = dc_(P0[q].x); X0[q].y = dc_(P0[q].y); X0[q].z = dc_(P0[q].z);
     X1[q].x = dc_(P1[q].x); X1[q].y = dc_(P1[q].y); X1[q].z = dc_(P1[q].z);
-    X1[q].x.d[3 * q + 0] = 1.0; X1[q].y.d[3 * q + 1] = 1.0; X1[q].z.d[3 * q + 2] = 1.0;
+    d3* seed = grad_x0 ? &X0[q] : &X1[q];
+    seed->x.d[3 * q + 0] = 1.0; seed->y.d[3 * q + 1] = 1.0; seed->z.d[3 * q + 2] = 1.0;
     D[q] = d3sub(X1[q], X0[q]);
   }
-  /* df/dX1 at fixed tau, by evaluating the coplanarity function on duals */
+  /* df/dX at fixed tau, by evaluating the coplanarity function on duals */
   dual tc = dc_(tau);
   d3 Y[4];
   for (int q = 0; q < 4; ++q) Y[q] = d3lerp(X0[q], tc, D[q]);
@@ -622,7 +630,7 @@ static double stiv_pair_dual(int kind, const v3* P0, const v3* P1, double tau, d
     dual b0 = dsub(dsub(dc_(1.0), b1), b2);
     m = d3cross(ea, eb);
     d3 Dtri = d3add(d3add(d3scale(b0, D[1]), d3scale(b1, D[2])), d3scale(b2, D[3]));
-    Drel = d3sub(D[0], Dtri);
+    Drel = velocity_abs ? D[0] : d3sub(D[0], Dtri);
   } else {
     d3 d1 = d3sub(Y[1], Y[0]), d2 = d3sub(Y[3], Y[2]), r = d3sub(Y[0], Y[2]);
     dual A = d3dot(d1, d1), B = d3dot(d1, d2), E = d3dot(d2, d2);
@@ -633,7 +641,7 @@ static double stiv_pair_dual(int kind, const v3* P0, const v3* P1, double tau, d
     m = d3cross(d1, d2);
     d3 Dp = d3add(d3scale(dsub(dc_(1.0), s), D[0]), d3scale(s, D[1]));
     d3 Dq = d3add(d3scale(dsub(dc_(1.0), u), D[2]), d3scale(u, D[3]));
-    Drel = d3sub(Dq, Dp);
+    Drel = velocity_abs ? Dp : d3sub(Dq, Dp);
   }
   dual e2 = dc_(eps_dt * eps_dt);
   dual dm = d3dot(Drel, m);
@@ -644,8 +652,10 @@ static double stiv_pair_dual(int kind, const v3* P0, const v3* P1, double tau, d
 }
 
 /* Exposed per-primitive volume: X0, X1 [4][3]; recomputes tau with the
- * contact test.  out: V, grad[12].  Returns the contact status. */
-int orc_stiv_primitive(int kind, const double* X0, const double* X1, double eps_dt, double* out) {
+ * contact test.  out: V, grad[12] (w.r.t. X0 when grad_x0).  Returns the
+ * contact status. */
+int orc_stiv_primitive_v(int kind, const double* X0, const double* X1, double eps_dt, int velocity_abs,
+                         int grad_x0, double* out) {
   v3 P0[4], P1[4], D[4];
   for (int q = 0; q < 4; ++q) {
     P0[q].x = X0[3 * q]; P0[q].y = X0[3 * q + 1]; P0[q].z = X0[3 * q + 2];
@@ -656,8 +666,12 @@ int orc_stiv_primitive(int kind, const double* X0, const double* X1, double eps_
   int st = ccd_pair(kind, P0, D, &t, &w1, &w2, NULL);
   memset(out, 0, sizeof(double) * 13);
   if (st != ORC_HIT) return st;
-  out[0] = stiv_pair_dual(kind, P0, P1, t, eps_dt, out + 1);
+  out[0] = stiv_pair_dual(kind, P0, P1, t, eps_dt, velocity_abs, grad_x0, out + 1);
   return st;
+}
+
+int orc_stiv_primitive(int kind, const double* X0, const double* X1, double eps_dt, double* out) {
+  return orc_stiv_primitive_v(kind, X0, X1, eps_dt, 0, 0, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -861,14 +875,15 @@ static ves_view make_view(topo_cache* tc, const int* Pv, const int64_t* voff, co
  * Output contacts grouped by pair in input order, each group ordered as in
  * pair_contacts.  cpair[k] is the row of the pair.  V_pair[npairs] gets the
  * sum of the pair's V_k in that order.  If grad != NULL, per contact the
- * gradient [4][3] w.r.t. X1 of the 4 points and, per point, its vesicle
- * (gves) and local vertex id (gvid) are written.
+ * gradient [4][3] w.r.t. X1 (X0 when grad_x0) of the 4 points and, per
+ * point, its vesicle (gves) and local vertex id (gvid) are written;
+ * velocity_abs selects the literal reading of U_k (see stiv_pair_dual).
  * counts[0] = contacts, [1] = primitive pairs tested, [2] = degenerate,
  * [3] = floating-point operations of the contact tests (ccd_pair's count).
  * OpenMP over pairs when compiled with it (nthreads <= 0: default). */
 int64_t orc_contacts(int nv_ves, const int* Pv, const int64_t* voff, const double* X,
                      int64_t npairs, const int32_t* pairs, const double* L,
-                     int prune, int include_ee, double eps_dt, int nthreads,
+                     int prune, int include_ee, double eps_dt, int velocity_abs, int grad_x0, int nthreads,
                      int64_t cap, int32_t* cpair, int32_t* ctype, int32_t* ca, int32_t* cb,
                      double* ctau, double* cw, double* cV, double* V_pair,
                      double* grad, int32_t* gves, int32_t* gvid, int64_t* counts) {
@@ -909,7 +924,7 @@ int64_t orc_contacts(int nv_ves, const int* Pv, const int64_t* voff, const doubl
       contact_points(&A, &B, outs[r].type[q], outs[r].a[q], outs[r].b[q], P0, P1, side, vid);
       int kind = outs[r].type[q] == 2 ? ORC_EE : ORC_VF;
       double g[12];
-      double V = stiv_pair_dual(kind, P0, P1, outs[r].tau[q], eps_dt, g);
+      double V = stiv_pair_dual(kind, P0, P1, outs[r].tau[q], eps_dt, velocity_abs, grad_x0, g);
       vsum += V;
       if (k < cap) {
         cpair[k] = (int32_t)r; ctype[k] = outs[r].type[q]; ca[k] = outs[r].a[q]; cb[k] = outs[r].b[q];

@@ -171,6 +171,7 @@ extern "C" int stiv_create(stiv_handle** out, const stiv_params* prm) {
   for (int c = 0; c < 3; ++c) if (!(prm->box_L[c] >= 0.0)) return STIV_ERR_ARG;
   if (!(prm->eps > 0.0) || !(prm->dt > 0.0) || !(prm->d_m >= 0.0)) return STIV_ERR_ARG;
   if (prm->precision != STIV_FP64 && prm->precision != STIV_MIXED) return STIV_ERR_ARG;
+  if (prm->velocity != STIV_VEL_RELATIVE && prm->velocity != STIV_VEL_ABSOLUTE) return STIV_ERR_ARG;
   stiv_handle* h = (stiv_handle*)calloc(1, sizeof(stiv_handle));
   if (!h) return STIV_ERR_ARG;
   h->prm = *prm;

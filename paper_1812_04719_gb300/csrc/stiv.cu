@@ -39,8 +39,15 @@ struct contact_in {
   double w1, w2;  // inside-test weights of the detection at tau (VF: b1, b2; EE: s, u)
 };
 
-// V and (optionally) dV/dX1 [4] of one contact.
-__device__ double stiv_one(const contact_in& c, double e2, d3* g) {
+// V and (optionally) dV/dX1 [4] (g1) and dV/dX0 [4] (g0) of one contact.
+// vabs: U_k read as the absolute velocity of the contact point (the literal
+// reading: VF the vertex's displacement, EE that of the point p(s) on the
+// first edge) instead of the velocity relative to the opposite primitive.
+// Reverse mode: adjoints of the positions at tau (Yb), of the displacements
+// (Db) and of tau (taub); with Y = X0 + tau D, D = X1 - X0 and tau moving
+// along f(tau; X) = 0, dV/dX1 = Db + tau Yb - taub tau fY / f' and
+// dV/dX0 = -Db + (1 - tau) Yb - taub (1 - tau) fY / f'.
+__device__ double stiv_one(const contact_in& c, double e2, int vabs, d3* g, d3* g0) {
   d3 D[4], Y[4];
   for (int q = 0; q < 4; ++q) { D[q] = c.X1[q] - c.X0[q]; Y[q] = mk(fma(c.tau, D[q].x, c.X0[q].x), fma(c.tau, D[q].y, c.X0[q].y), fma(c.tau, D[q].z, c.X0[q].z)); }
   const double tau = c.tau;
@@ -54,18 +61,23 @@ __device__ double stiv_one(const contact_in& c, double e2, d3* g) {
     (void)d20; (void)d21;
     double b1 = c.w1, b2 = c.w2, b0 = 1.0 - b1 - b2;
     d3 m = cross(a, b);
-    d3 Dr = D[0] - (b0 * D[1] + b1 * D[2] + b2 * D[3]);
+    d3 Dr = vabs ? D[0] : D[0] - (b0 * D[1] + b1 * D[2] + b2 * D[3]);
     double dm = dot(Dr, m);
     double Q = e2 * dot(m, m) + dm * dm;
     double S = sqrt(Q);
     V = 0.5 * (1.0 - tau) * S;
-    if (!g) return V;
+    if (!g && !g0) return V;
     double Qb = 0.5 * (1.0 - tau) / (2.0 * S);
     d3 mb = (2.0 * Qb) * (e2 * m + dm * Dr);
     d3 Drb = (2.0 * Qb * dm) * m;
     taub = -0.5 * S;
-    Db[0] = Drb; Db[1] = -b0 * Drb; Db[2] = -b1 * Drb; Db[3] = -b2 * Drb;
-    double bb0 = -dot(Drb, D[1]), bb1 = -dot(Drb, D[2]), bb2 = -dot(Drb, D[3]);
+    double bb0 = 0.0, bb1 = 0.0, bb2 = 0.0;
+    if (vabs) {
+      Db[0] = Drb;
+    } else {
+      Db[0] = Drb; Db[1] = -b0 * Drb; Db[2] = -b1 * Drb; Db[3] = -b2 * Drb;
+      bb0 = -dot(Drb, D[1]); bb1 = -dot(Drb, D[2]); bb2 = -dot(Drb, D[3]);
+    }
     double g1 = bb1 - bb0, g2 = bb2 - bb0;
     d3 ab = cross(b, mb), bbv = cross(mb, a), cb = mk(0, 0, 0);
     // least squares beta = M^-1 G^T c, G = [a b]
@@ -85,18 +97,25 @@ __device__ double stiv_one(const contact_in& c, double e2, d3* g) {
     (void)C; (void)F;
     double s = c.w1, u = c.w2;
     d3 m = cross(d1, d2);
-    d3 Dr = ((1.0 - u) * D[2] + u * D[3]) - ((1.0 - s) * D[0] + s * D[1]);
+    d3 Dp = (1.0 - s) * D[0] + s * D[1];
+    d3 Dr = vabs ? Dp : ((1.0 - u) * D[2] + u * D[3]) - Dp;
     double dm = dot(Dr, m);
     double Q = e2 * dot(m, m) + dm * dm;
     double S = sqrt(Q);
     V = 0.5 * (1.0 - tau) * S;
-    if (!g) return V;
+    if (!g && !g0) return V;
     double Qb = 0.5 * (1.0 - tau) / (2.0 * S);
     d3 mb = (2.0 * Qb) * (e2 * m + dm * Dr);
     d3 Drb = (2.0 * Qb * dm) * m;
     taub = -0.5 * S;
-    Db[2] = (1.0 - u) * Drb; Db[3] = u * Drb; Db[0] = -(1.0 - s) * Drb; Db[1] = -s * Drb;
-    double sb = -dot(Drb, D[1] - D[0]), ub = dot(Drb, D[3] - D[2]);
+    double sb, ub;
+    if (vabs) {
+      Db[0] = (1.0 - s) * Drb; Db[1] = s * Drb;
+      sb = dot(Drb, D[1] - D[0]); ub = 0.0;
+    } else {
+      Db[2] = (1.0 - u) * Drb; Db[3] = u * Drb; Db[0] = -(1.0 - s) * Drb; Db[1] = -s * Drb;
+      sb = -dot(Drb, D[1] - D[0]); ub = dot(Drb, D[3] - D[2]);
+    }
     d3 d1b = cross(d2, mb), d2b = cross(mb, d1);
     // least squares (s, u) = M^-1 G^T c, G = [d1, -d2], c = -r; M = [[A, -B], [-B, E]]
     double z1 = (E * sb + B * ub) * iden, z2 = (B * sb + A * ub) * iden;
@@ -113,7 +132,10 @@ __device__ double stiv_one(const contact_in& c, double e2, d3* g) {
   }
   double fp = 0.0;
   for (int q = 0; q < 4; ++q) { taub += dot(Yb[q], D[q]); fp += dot(fY[q], D[q]); }
-  for (int q = 0; q < 4; ++q) g[q] = (Db[q] + tau * Yb[q]) - ((taub * tau / fp) * fY[q]);
+  if (g)
+    for (int q = 0; q < 4; ++q) g[q] = (Db[q] + tau * Yb[q]) - ((taub * tau / fp) * fY[q]);
+  if (g0)
+    for (int q = 0; q < 4; ++q) g0[q] = ((1.0 - tau) * Yb[q] - Db[q]) - ((taub * (1.0 - tau) / fp) * fY[q]);
   return V;
 }
 
@@ -128,8 +150,10 @@ struct stiv_args {
   const int64_t* counts;
   int64_t cap;
   double e2;
+  int vabs;
   double* Vc;
   double* grad;
+  double* grad0;   // dV/dX0 rows (or NULL)
   int32_t* gves;
   int32_t* gvid;
 };
@@ -177,8 +201,8 @@ __global__ void __launch_bounds__(128) stiv_kernel(stiv_args A) {
       c.X0[q] = vpos(A, ves[q], 0, vid[q], sh[q]);
       c.X1[q] = vpos(A, ves[q], 1, vid[q], sh[q]);
     }
-    d3 g[4];
-    double V = stiv_one(c, A.e2, A.grad ? g : nullptr);
+    d3 g[4], g0[4];
+    double V = stiv_one(c, A.e2, A.vabs, A.grad ? g : nullptr, A.grad0 ? g0 : nullptr);
     if (A.Vc) A.Vc[k] = V;
     if (A.grad) {
       for (int q = 0; q < 4; ++q) {
@@ -186,6 +210,11 @@ __global__ void __launch_bounds__(128) stiv_kernel(stiv_args A) {
         A.gves[4 * k + q] = ves[q]; A.gvid[4 * k + q] = vid[q];
       }
     }
+    if (A.grad0)
+      for (int q = 0; q < 4; ++q) {
+        A.grad0[12 * k + 3 * q + 0] = g0[q].x; A.grad0[12 * k + 3 * q + 1] = g0[q].y;
+        A.grad0[12 * k + 3 * q + 2] = g0[q].z;
+      }
   }
 }
 
@@ -445,7 +474,7 @@ int stiv_contact_order(stiv_handle* h, cudaStream_t st, const stiv_pairs* cand, 
 
 static int run_stiv(stiv_handle* h, void* stream, const int32_t* p_dev, const int64_t* vert_off_dev,
                     const void* verts_dev, const stiv_pairs* cand, const stiv_contacts* ct, const int64_t* counts_dev,
-                    double* Vc, double* Vp, double* grad, int32_t* gves, int32_t* gvid) {
+                    double* Vc, double* Vp, double* grad, int32_t* gves, int32_t* gvid, double* grad0 = nullptr) {
   if (!h || !p_dev || !vert_off_dev || !verts_dev || !cand || !ct || !counts_dev) return STIV_ERR_ARG;
   if (grad && (!gves || !gvid)) return STIV_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -463,11 +492,12 @@ static int run_stiv(stiv_handle* h, void* stream, const int32_t* p_dev, const in
   A.counts = counts_dev; A.cap = ct->capacity;
   double edt = h->prm.eps * h->prm.dt;
   A.e2 = edt * edt;
-  A.Vc = Vtmp; A.grad = grad; A.gves = gves; A.gvid = gvid;
+  A.vabs = h->prm.velocity == STIV_VEL_ABSOLUTE;
+  A.Vc = Vtmp; A.grad = grad; A.gves = gves; A.gvid = gvid; A.grad0 = grad0;
   int dev_sms = 152;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device);
-  if (Vtmp || grad) {
-    STIV_PROF(h, st, A.grad ? "stiv_grad" : "stiv");
+  if (Vtmp || grad || grad0) {
+    STIV_PROF(h, st, A.grad ? "stiv_grad" : (A.grad0 ? "stiv_grad_x0" : "stiv"));
     stiv_kernel<<<dev_sms * 8, 128, 0, st>>>(A);
     STIV_LAUNCH(h);
   }
@@ -496,6 +526,15 @@ extern "C" int stiv_stiv_grad(stiv_handle* h, void* stream, int32_t n_ves, const
   if (!grad_dev) return STIV_ERR_ARG;
   return run_stiv(h, stream, p_dev, vert_off_dev, verts_dev, cand, contacts, counts_dev, V_contact_dev, V_pair_dev,
                   grad_dev, g_ves_dev, g_vid_dev);
+}
+
+extern "C" int stiv_stiv_grad_x0(stiv_handle* h, void* stream, int32_t n_ves, const int32_t* p_dev,
+                                 const int64_t* vert_off_dev, const void* verts_dev, const stiv_pairs* cand,
+                                 const stiv_contacts* contacts, const int64_t* counts_dev, double* grad_x0_dev) {
+  (void)n_ves;
+  if (!grad_x0_dev) return STIV_ERR_ARG;
+  return run_stiv(h, stream, p_dev, vert_off_dev, verts_dev, cand, contacts, counts_dev, nullptr, nullptr, nullptr,
+                  nullptr, nullptr, grad_x0_dev);
 }
 
 extern "C" int stiv_grad_scatter(stiv_handle* h, void* stream, const int32_t* p_dev, const stiv_contacts* contacts,

@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(HERE, "libstiv.so")
 
 STIV_OK, STIV_ERR_ARG, STIV_ERR_CAPACITY, STIV_ERR_TIMEOUT, STIV_ERR_CUDA, STIV_ERR_INPUT = range(6)
 STIV_FP64, STIV_MIXED = 0, 1
+STIV_VEL_RELATIVE, STIV_VEL_ABSOLUTE = 0, 1
 C_PAIRS, C_PRIM, C_VF, C_EE, C_CPAIRS, C_DEGEN, C_STATUS, C_PATCH, C_FLOPS, C_EXACT = range(10)
 NCOUNTS = 10
 F_PAIRS_OVERFLOW, F_CONTACTS_OVERFLOW, F_BOX_TOO_SMALL, F_NONFINITE, F_WORK_OVERFLOW, F_TIMEOUT = 1, 2, 4, 8, 16, 32
@@ -35,7 +36,7 @@ EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_
            "stiv_grad_to_coef", "stiv_step", "stiv_sync_counts", "stiv_sort_scratch_bytes", "stiv_sort_pairs",
            "stiv_profile", "stiv_profile_read", "stiv_sort_pairs_static", "stiv_autotune", "stiv_set_tuning",
            "stiv_wait_selftest", "stiv_lcp_matrix", "stiv_lcp_solve",
-           "stiv_mesh_fidelity"]
+           "stiv_mesh_fidelity", "stiv_stiv_grad_x0"]
 TUNE_NAMES = ("narrow_ctas_per_sm", "pieces_ctas_per_sm", "fp64_blocks_per_sm", "patch_blocks_per_sm",
               "piece_levels")
 SORT_STATIC_MAX = 1 << 20
@@ -56,7 +57,7 @@ class StivLcp(ctypes.Structure):
 class StivParams(ctypes.Structure):
     _fields_ = [("d_m", ctypes.c_double), ("eps", ctypes.c_double), ("dt", ctypes.c_double),
                 ("box_L", ctypes.c_double * 3), ("precision", ctypes.c_int32), ("include_ee", ctypes.c_int32),
-                ("exact_only", ctypes.c_int32)]
+                ("exact_only", ctypes.c_int32), ("velocity", ctypes.c_int32)]
 
 
 class StivPairs(ctypes.Structure):
@@ -107,6 +108,7 @@ def lib() -> ctypes.CDLL:
     L.stiv_wait_selftest.argtypes = [vp, i64, vp]
     L.stiv_lcp_matrix.argtypes = [vp, vp, i32, i32, P(StivPairs), P(StivContacts), vp, vp, vp, vp, vp, vp, vp,
                                   P(StivLcp)]
+    L.stiv_stiv_grad_x0.argtypes = [vp, vp, i32, vp, vp, vp, P(StivPairs), P(StivContacts), vp, vp]
     L.stiv_mesh_fidelity.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, i32, vp]
     L.stiv_lcp_solve.argtypes = [vp, vp, P(StivLcp), ctypes.c_double, i32, i32, vp, vp]
     L.stiv_profile.argtypes = [vp, i32]
@@ -142,9 +144,9 @@ def _stream(stream=None) -> int:
 # ---------------------------------------------------------------------------
 
 def stiv_create(d_m=0.0, eps=1.0, dt=0.1, box_L=(0.0, 0.0, 0.0), precision=STIV_FP64, include_ee=True,
-                exact_only=False) -> int:
+                exact_only=False, velocity=0) -> int:
     prm = StivParams(float(d_m), float(eps), float(dt), (ctypes.c_double * 3)(*[float(x) for x in box_L]),
-                     int(precision), int(bool(include_ee)), int(bool(exact_only)))
+                     int(precision), int(bool(include_ee)), int(bool(exact_only)), int(velocity))
     h = ctypes.c_void_p()
     _check(lib().stiv_create(ctypes.byref(h), ctypes.byref(prm)), "stiv_create")
     return h.value
@@ -315,11 +317,11 @@ class Stiv:
     """One library handle plus the buffers of the per-step path."""
 
     def __init__(self, box_L=(0.0, 0.0, 0.0), eps=1.0, dt=0.1, d_m=0.0, precision=STIV_FP64, include_ee=True,
-                 pair_cap=1024, contact_cap=1 << 16, device="cuda", exact_only=False):
+                 pair_cap=1024, contact_cap=1 << 16, device="cuda", exact_only=False, velocity=STIV_VEL_RELATIVE):
         self.precision = precision
         self.device = torch.device(device)
         self.h = stiv_create(d_m=d_m, eps=eps, dt=dt, box_L=box_L, precision=precision, include_ee=include_ee,
-                             exact_only=exact_only)
+                             exact_only=exact_only, velocity=velocity)
         self.pair_cap, self.contact_cap = pair_cap, contact_cap
         self.buf = None
 
@@ -395,6 +397,17 @@ class Stiv:
             res["best_ms"] = best.value
             return res
         raise StivError(STIV_ERR_CAPACITY, "autotune: capacities kept overflowing")
+
+    def grad_x0(self, ds: DeviceScene, stream=None) -> torch.Tensor:
+        """dV_k/dX0 rows [contacts][4][3] of the last step's contacts (points
+        as in that step's gves / gvid)."""
+        b = self.buf
+        nc = int(b.counts[C_VF].item() + b.counts[C_EE].item())
+        g0 = torch.zeros(max(b.contact_cap, 1), 4, 3, dtype=torch.float64, device=self.device)
+        _check(lib().stiv_stiv_grad_x0(self.h, _stream(stream), ds.n, _ptr(ds.p), _ptr(ds.vert_off), _ptr(ds.verts),
+                                       ctypes.byref(b.pairs_struct()), ctypes.byref(b.contacts_struct()),
+                                       _ptr(b.counts), _ptr(g0)), "stiv_stiv_grad_x0")
+        return g0[:nc]
 
     def mesh_fidelity(self, ds: DeviceScene, factor: int = 4, stream=None) -> torch.Tensor:
         """Per vesicle and time level, the largest distance between the order-2p
