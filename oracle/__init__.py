@@ -68,10 +68,13 @@ def lib() -> ctypes.CDLL:
             L.orc_candidate_pairs.restype = ctypes.c_int64
             L.orc_ccd_primitive.argtypes = [ctypes.c_int, dp, dp, dp]
             L.orc_stiv_primitive.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
-            L.orc_stiv_primitive_v.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
+            L.orc_stiv_primitive_v.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                               ctypes.c_int, dp]
+            L.orc_ccd_primitive_dm.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
+            L.orc_poly_roots01.argtypes = [dp, ctypes.c_int, dp]
             L.orc_contacts.argtypes = [ctypes.c_int, ip, lp, dp, ctypes.c_int64, ip, dp,
-                                       ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int64, ip, ip, ip, ip, dp, dp, dp, dp, dp, ip, ip, lp]
             L.orc_contacts.restype = ctypes.c_int64
             _lib = L
@@ -220,7 +223,7 @@ class Contacts(dict):
 
 def contacts(P_ves, X_list_or_flat, pairs, L, eps_dt: float, prune: bool = True,
              include_ee: bool = True, grad: bool = True, nthreads: int = 0, voff=None,
-             velocity: str = "relative", grad_wrt: str = "X1"):
+             velocity: str = "relative", grad_wrt: str = "X1", d_m: float = 0.0):
     """Alg. 2 checkContact over candidate vesicle pairs.
 
     P_ves: grid order per vesicle.  X: either a list of [2][3][n_v] arrays or
@@ -229,7 +232,9 @@ def contacts(P_ves, X_list_or_flat, pairs, L, eps_dt: float, prune: bool = True,
     pair row), grad [.,4,3], gves/gvid [.,4], counts (contacts, prim pairs
     tested, degenerate, floating-point operations of the contact tests).
     velocity "absolute" takes U_k as the contact point's own velocity (the
-    literal reading); grad_wrt "X0" differentiates with respect to X0."""
+    literal reading); grad_wrt "X0" differentiates with respect to X0; d_m > 0
+    uses the degree-six test of Eq. 3.1 (contact within d_m) and widens the
+    second vesicle's primitive boxes by d_m."""
     assert velocity in ("relative", "absolute") and grad_wrt in ("X1", "X0")
     P_ves = np.ascontiguousarray(P_ves, dtype=np.int32)
     if voff is None:
@@ -246,7 +251,7 @@ def contacts(P_ves, X_list_or_flat, pairs, L, eps_dt: float, prune: bool = True,
     V_pair = np.zeros(max(npairs, 1))
     L_ = lib()
     args_head = (len(P_ves), _i(P_ves), _l(voff), _d(flat), npairs, _i(pairs if npairs else np.zeros((1, 5), np.int32)),
-                 _d(Lv), int(prune), int(include_ee), float(eps_dt), int(velocity == "absolute"),
+                 _d(Lv), int(prune), int(include_ee), float(d_m), float(eps_dt), int(velocity == "absolute"),
                  int(grad_wrt == "X0"), int(nthreads))
 
     def run(cap):
@@ -269,12 +274,32 @@ def contacts(P_ves, X_list_or_flat, pairs, L, eps_dt: float, prune: bool = True,
     return out
 
 
-def stiv_primitive_variant(kind: str, X0, X1, eps_dt: float, velocity: str = "relative", grad_wrt: str = "X1"):
-    """stiv_primitive with the literal velocity reading and/or the gradient
-    with respect to X0."""
+def stiv_primitive_variant(kind: str, X0, X1, eps_dt: float, velocity: str = "relative", grad_wrt: str = "X1",
+                           d_m: float = 0.0):
+    """stiv_primitive with the literal velocity reading, the gradient with
+    respect to X0 and/or d_m > 0 (the degree-six contact time)."""
     X0 = np.ascontiguousarray(X0, dtype=np.float64).reshape(4, 3)
     X1 = np.ascontiguousarray(X1, dtype=np.float64).reshape(4, 3)
     out = np.zeros(13)
-    st = lib().orc_stiv_primitive_v(0 if kind == "vf" else 1, _d(X0), _d(X1), float(eps_dt),
+    st = lib().orc_stiv_primitive_v(0 if kind == "vf" else 1, _d(X0), _d(X1), float(eps_dt), float(d_m),
                                     int(velocity == "absolute"), int(grad_wrt == "X0"), _d(out))
     return st, out[0], out[1:].reshape(4, 3)
+
+
+def ccd_primitive_dm(kind: str, X0, X1, d_m: float):
+    """Single primitive pair with minimum separation d_m (Eq. 3.1, degree six
+    for d_m > 0).  Returns (status, tau, w1, w2)."""
+    X0 = np.ascontiguousarray(X0, dtype=np.float64).reshape(4, 3)
+    X1 = np.ascontiguousarray(X1, dtype=np.float64).reshape(4, 3)
+    out = np.zeros(3)
+    st = lib().orc_ccd_primitive_dm(0 if kind == "vf" else 1, _d(X0), _d(X1), float(d_m), _d(out))
+    return st, out[0], out[1], out[2]
+
+
+def poly_roots01(c) -> np.ndarray:
+    """Roots in (0, 1) of the polynomial c[0] + c[1] t + ... (degree <= 6),
+    ascending, by the derivative-chain isolation of the d_m > 0 test."""
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    out = np.zeros(6)
+    n = lib().orc_poly_roots01(_d(c), len(c) - 1, _d(out))
+    return out[:n].copy()

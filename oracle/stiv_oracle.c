@@ -538,6 +538,158 @@ int orc_ccd_primitive(int kind, const double* X0, const double* X1, double* out)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Eq. 3.1 with d_m > 0: the degree-six equation                              */
+/* ------------------------------------------------------------------------ */
+
+/* Horner value of the degree-n polynomial c[0..n] at t (fused multiply-adds). */
+static double horner_n(const double* c, int n, double t) {
+  double r = c[n];
+  for (int i = n - 1; i >= 0; --i) r = fma(r, t, c[i]);
+  return r;
+}
+
+/* The cubic test's bisection for a degree-n polynomial. */
+static double bisect_n(const double* c, int n, double lo, double hi, double flo) {
+  for (int it = 0; it < 64; ++it) {
+    double mid = (lo + hi) * 0.5;
+    if (!(mid > lo && mid < hi)) break;
+    double fm = horner_n(c, n, mid);
+    if (fm == 0.0) return mid;
+    if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; }
+    else hi = mid;
+  }
+  return lo;
+}
+
+/* Roots in (0, 1) of the degree-n polynomial c (1 <= n <= 6), ascending.
+ * The roots of the derivative (found the same way, down to a linear
+ * function) split [0, 1] into pieces on which c is monotone, so each piece
+ * holds at most one root; a piece is taken as in the cubic test: its left end
+ * if c vanishes there, else its right end if c vanishes there, else the
+ * bisection of a sign change. */
+static int poly_roots01(const double* c, int n, double* out) {
+  if (n == 1) {
+    if (c[1] == 0.0) return 0;
+    double t = -c[0] / c[1];
+    if (t > 0.0 && t < 1.0) { out[0] = t; return 1; }
+    return 0;
+  }
+  double dc[6];
+  for (int i = 0; i < n; ++i) dc[i] = (double)(i + 1) * c[i + 1];
+  double cp[6];
+  int ncp = poly_roots01(dc, n - 1, cp);
+  double ends[8]; int ne = 0;
+  ends[ne++] = 0.0;
+  for (int i = 0; i < ncp; ++i) ends[ne++] = cp[i];
+  ends[ne++] = 1.0;
+  int nr = 0;
+  for (int s = 0; s + 1 < ne; ++s) {
+    double l = ends[s], r = ends[s + 1];
+    double fl = horner_n(c, n, l), fr = horner_n(c, n, r), t;
+    if (fl == 0.0) t = l;
+    else if (fr == 0.0) t = r;
+    else if ((fl < 0.0) != (fr < 0.0)) t = bisect_n(c, n, l, r, fl);
+    else continue;
+    if (t > 0.0 && t < 1.0 && (nr == 0 || t > out[nr - 1])) out[nr++] = t;
+  }
+  return nr;
+}
+
+/* Coefficients g[0..6] of g(t) = f(t)^2 - d_m^2 |m(t)|^2 (Eq. 3.1): f the
+ * coplanarity cubic (k), m(t) = n0 + n1 t + n2 t^2 the normal a x b (VF) or
+ * d1 x d2 (EE); |f| / |m| is the distance of the point to the plane (VF) or
+ * between the lines (EE).  Fixed order of the FP64 operations. */
+static void sextic_coeffs(v3 a, v3 b, v3 c, v3 da, v3 db, v3 dc, double dm, double g[7]) {
+  double k[4];
+  cubic_coeffs(a, b, c, da, db, dc, k);
+  v3 n0 = v3cross(a, b);
+  v3 n1 = v3add(v3cross(da, b), v3cross(a, db));
+  v3 n2 = v3cross(da, db);
+  double q0 = v3dot(n0, n0);
+  double q1 = 2.0 * v3dot(n0, n1);
+  double q2 = v3dot(n1, n1) + 2.0 * v3dot(n0, n2);
+  double q3 = 2.0 * v3dot(n1, n2);
+  double q4 = v3dot(n2, n2);
+  double dd = dm * dm;
+  g[0] = k[0] * k[0] - dd * q0;
+  g[1] = 2.0 * (k[0] * k[1]) - dd * q1;
+  g[2] = (2.0 * (k[0] * k[2]) + k[1] * k[1]) - dd * q2;
+  g[3] = 2.0 * (k[0] * k[3] + k[1] * k[2]) - dd * q3;
+  g[4] = (2.0 * (k[1] * k[3]) + k[2] * k[2]) - dd * q4;
+  g[5] = 2.0 * (k[2] * k[3]);
+  g[6] = k[3] * k[3];
+}
+
+static void prim_vectors(int kind, const v3* P0, const v3* D, v3* a, v3* b, v3* c, v3* da, v3* db, v3* dc) {
+  if (kind == ORC_VF) {
+    *a = v3sub(P0[2], P0[1]); *b = v3sub(P0[3], P0[1]); *c = v3sub(P0[0], P0[1]);
+    *da = v3sub(D[2], D[1]); *db = v3sub(D[3], D[1]); *dc = v3sub(D[0], D[1]);
+  } else {
+    *a = v3sub(P0[1], P0[0]); *b = v3sub(P0[3], P0[2]); *c = v3sub(P0[2], P0[0]);
+    *da = v3sub(D[1], D[0]); *db = v3sub(D[3], D[2]); *dc = v3sub(D[2], D[0]);
+  }
+}
+
+/* Earliest time in [0, 1] at which the point comes within d_m of the
+ * triangle's plane (the lines come within d_m), with the inside test of the
+ * cubic at that time (the point's projection in the closed triangle; the
+ * closest points within both edges).  The roots of g' split [0, 1] into
+ * monotone pieces, visited in time order and taken as in the cubic test; the
+ * first piece is also taken at t = 0 when g(0) <= 0 (already within d_m at the
+ * start of the step).  All g identically zero is degenerate. */
+static int ccd_pair_dm(int kind, const v3* P0, const v3* D, double dm, double* tau, double* w1, double* w2) {
+  v3 a, b, c, da, db, dc;
+  prim_vectors(kind, P0, D, &a, &b, &c, &da, &db, &dc);
+  double g[7];
+  sextic_coeffs(a, b, c, da, db, dc, dm, g);
+  int allz = 1;
+  for (int i = 0; i <= 6; ++i) if (g[i] != 0.0) allz = 0;
+  if (allz) return ORC_DEGEN;
+  double dg[6];
+  for (int i = 0; i < 6; ++i) dg[i] = (double)(i + 1) * g[i + 1];
+  double cp[6];
+  int ncp = poly_roots01(dg, 5, cp);
+  double ends[8]; int ne = 0;
+  ends[ne++] = 0.0;
+  for (int i = 0; i < ncp; ++i) ends[ne++] = cp[i];
+  ends[ne++] = 1.0;
+  int degen = 0;
+  for (int s = 0; s + 1 < ne; ++s) {
+    double l = ends[s], r = ends[s + 1];
+    double gl = horner_n(g, 6, l), gr = horner_n(g, 6, r), t;
+    if (s == 0 && gl <= 0.0) t = l;
+    else if (gl == 0.0) t = l;
+    else if (gr == 0.0) t = r;
+    else if ((gl < 0.0) != (gr < 0.0)) t = bisect_n(g, 6, l, r, gl);
+    else continue;
+    v3 Y[4];
+    for (int q = 0; q < 4; ++q) Y[q] = v3lerp(P0[q], t, D[q]);
+    double u1 = 0.0, u2 = 0.0;
+    int64_t uncounted = 0;   /* the operation count covers the d_m = 0 procedure */
+    int in = inside_test(kind, Y, &u1, &u2, &uncounted);
+    if (in < 0) { degen = 1; continue; }
+    if (in == 1) { *tau = t; *w1 = u1; *w2 = u2; return ORC_HIT; }
+  }
+  return degen ? ORC_DEGEN : 0;
+}
+
+/* Exposed root isolation (pins): roots in (0, 1) of c[0..n], n <= 6. */
+int orc_poly_roots01(const double* c, int n, double* out) { return poly_roots01(c, n, out); }
+
+/* Exposed single-primitive test with d_m > 0 (closed-form pins). */
+int orc_ccd_primitive_dm(int kind, const double* X0, const double* X1, double dm, double* out) {
+  v3 P0[4], D[4];
+  for (int q = 0; q < 4; ++q) {
+    P0[q].x = X0[3 * q]; P0[q].y = X0[3 * q + 1]; P0[q].z = X0[3 * q + 2];
+    D[q].x = X1[3 * q] - X0[3 * q]; D[q].y = X1[3 * q + 1] - X0[3 * q + 1]; D[q].z = X1[3 * q + 2] - X0[3 * q + 2];
+  }
+  double t = 0.0, w1 = 0.0, w2 = 0.0;
+  int st = dm > 0.0 ? ccd_pair_dm(kind, P0, D, dm, &t, &w1, &w2) : ccd_pair(kind, P0, D, &t, &w1, &w2, NULL);
+  out[0] = t; out[1] = w1; out[2] = w2;
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Eq. 3.2 and App. A: contact volume of one primitive pair and its gradient */
 /* with respect to the end-of-step positions X1 (X0 fixed).                   */
 /* ------------------------------------------------------------------------ */
@@ -584,8 +736,8 @@ static d3 d3lerp(d3 x0, dual t, d3 d) { return d3add(x0, d3scale(t, d)); }
  * the vertex's displacement D_p, for EE that of the point p(s) on the first
  * edge.  grad_x0 = 1 differentiates with respect to the start positions X0
  * (X1 fixed) instead: tau follows through f(tau; X0) = 0 the same way. */
-static double stiv_pair_dual(int kind, const v3* P0, const v3* P1, double tau, double eps_dt, int velocity_abs,
-                             int grad_x0, double* grad) {
+static double stiv_pair_dual(int kind, const v3* P0, const v3* P1, double tau, double eps_dt, double dm,
+                             int velocity_abs, int grad_x0, double* grad) {
   d3 X0[4], X1[4], D[4];
   for (int q = 0; q < 4; ++q) {
     X0[q].x = dc_(P0[q].x); X0[q].y = dc_(P0[q].y); X0[q].z = dc_(P0[q].z);
@@ -599,8 +751,14 @@ static double stiv_pair_dual(int kind, const v3* P0, const v3* P1, double tau, d
   d3 Y[4];
   for (int q = 0; q < 4; ++q) Y[q] = d3lerp(X0[q], tc, D[q]);
   dual f;
-  if (kind == ORC_VF) f = d3dot(d3sub(Y[0], Y[1]), d3cross(d3sub(Y[2], Y[1]), d3sub(Y[3], Y[1])));
-  else f = d3dot(d3sub(Y[2], Y[0]), d3cross(d3sub(Y[1], Y[0]), d3sub(Y[3], Y[2])));
+  d3 mt;   /* the normal at fixed tau */
+  if (kind == ORC_VF) {
+    mt = d3cross(d3sub(Y[2], Y[1]), d3sub(Y[3], Y[1]));
+    f = d3dot(d3sub(Y[0], Y[1]), mt);
+  } else {
+    mt = d3cross(d3sub(Y[1], Y[0]), d3sub(Y[3], Y[2]));
+    f = d3dot(d3sub(Y[2], Y[0]), mt);
+  }
   /* f'(tau) from the cubic's coefficients */
   v3 a, b, c, da, db, dcv;
   v3 Dv[4];
@@ -615,6 +773,13 @@ static double stiv_pair_dual(int kind, const v3* P0, const v3* P1, double tau, d
   double k[4];
   cubic_coeffs(a, b, c, da, db, dcv, k);
   double fp = (3.0 * k[3] * tau + 2.0 * k[2]) * tau + k[1];
+  if (dm > 0.0) {
+    /* tau follows g = f^2 - d_m^2 |m|^2 = 0 (Eq. 3.1) instead of f = 0 */
+    double g[7];
+    sextic_coeffs(a, b, c, da, db, dcv, dm, g);
+    fp = ((((6.0 * g[6] * tau + 5.0 * g[5]) * tau + 4.0 * g[4]) * tau + 3.0 * g[3]) * tau + 2.0 * g[2]) * tau + g[1];
+    f = dsub(dmul(f, f), dmul(dc_(dm * dm), d3dot(mt, mt)));
+  }
   dual td = dc_(tau);
   for (int i = 0; i < ND; ++i) td.d[i] = -f.d[i] / fp;
   /* positions at the contact time, now carrying d tau */
@@ -644,8 +809,8 @@ static double stiv_pair_dual(int kind, const v3* P0, const v3* P1, double tau, d
     Drel = velocity_abs ? Dp : d3sub(Dq, Dp);
   }
   dual e2 = dc_(eps_dt * eps_dt);
-  dual dm = d3dot(Drel, m);
-  dual Q = dadd(dmul(e2, d3dot(m, m)), dmul(dm, dm));
+  dual um = d3dot(Drel, m);
+  dual Q = dadd(dmul(e2, d3dot(m, m)), dmul(um, um));
   dual V = dmul(dmul(dc_(0.5), dsub(dc_(1.0), td)), dsqrt(Q));
   if (grad) for (int i = 0; i < ND; ++i) grad[i] = V.d[i];
   return V.v;
@@ -654,7 +819,7 @@ static double stiv_pair_dual(int kind, const v3* P0, const v3* P1, double tau, d
 /* Exposed per-primitive volume: X0, X1 [4][3]; recomputes tau with the
  * contact test.  out: V, grad[12] (w.r.t. X0 when grad_x0).  Returns the
  * contact status. */
-int orc_stiv_primitive_v(int kind, const double* X0, const double* X1, double eps_dt, int velocity_abs,
+int orc_stiv_primitive_v(int kind, const double* X0, const double* X1, double eps_dt, double dm, int velocity_abs,
                          int grad_x0, double* out) {
   v3 P0[4], P1[4], D[4];
   for (int q = 0; q < 4; ++q) {
@@ -663,15 +828,15 @@ int orc_stiv_primitive_v(int kind, const double* X0, const double* X1, double ep
     D[q] = v3sub(P1[q], P0[q]);
   }
   double t, w1, w2;
-  int st = ccd_pair(kind, P0, D, &t, &w1, &w2, NULL);
+  int st = dm > 0.0 ? ccd_pair_dm(kind, P0, D, dm, &t, &w1, &w2) : ccd_pair(kind, P0, D, &t, &w1, &w2, NULL);
   memset(out, 0, sizeof(double) * 13);
   if (st != ORC_HIT) return st;
-  out[0] = stiv_pair_dual(kind, P0, P1, t, eps_dt, velocity_abs, grad_x0, out + 1);
+  out[0] = stiv_pair_dual(kind, P0, P1, t, eps_dt, dm, velocity_abs, grad_x0, out + 1);
   return st;
 }
 
 int orc_stiv_primitive(int kind, const double* X0, const double* X1, double eps_dt, double* out) {
-  return orc_stiv_primitive_v(kind, X0, X1, eps_dt, 0, 0, out);
+  return orc_stiv_primitive_v(kind, X0, X1, eps_dt, 0.0, 0, 0, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -742,7 +907,9 @@ static void free_contacts(contact_out* o) {
 /* Swept boxes of every vertex, triangle and edge of one vesicle view. */
 typedef struct { double* vb; double* tb; double* eb; } prim_boxes;
 
-static prim_boxes make_boxes(const ves_view* V) {
+/* pad > 0 widens every box by pad on each side (FP64, as computed), so that
+ * two primitives within pad of each other have overlapping boxes. */
+static prim_boxes make_boxes(const ves_view* V, double pad) {
   prim_boxes r;
   r.vb = (double*)malloc(sizeof(double) * 6 * V->nv);
   r.tb = (double*)malloc(sizeof(double) * 6 * V->nf);
@@ -757,6 +924,13 @@ static prim_boxes make_boxes(const ves_view* V) {
     for (int q = 0; q < 2; ++q) { P0[q] = vpos(V, 0, V->edge[2 * e + q]); P1[q] = vpos(V, 1, V->edge[2 * e + q]); }
     prim_box(P0, P1, 2, r.eb + 6 * e);
   }
+  if (pad > 0.0) {
+    double* all[3] = {r.vb, r.tb, r.eb};
+    int cnt[3] = {V->nv, V->nf, V->ne};
+    for (int w = 0; w < 3; ++w)
+      for (int e = 0; e < cnt[w]; ++e)
+        for (int c = 0; c < 3; ++c) { all[w][6 * e + c] = all[w][6 * e + c] - pad; all[w][6 * e + 3 + c] = all[w][6 * e + 3 + c] + pad; }
+  }
   return r;
 }
 
@@ -766,9 +940,11 @@ static void free_boxes(prim_boxes* b) { free(b->vb); free(b->tb); free(b->eb); }
  * type 0 = vertex of A vs triangle of B, type 1 = vertex of B vs triangle of
  * A, type 2 = edge of A vs edge of B (edge index in the sorted edge list);
  * within a type by ascending primitive ids.  prune = 1 skips pairs whose swept boxes
- * do not overlap (a necessary condition for contact). */
-static void pair_contacts(const ves_view* A, const ves_view* B, int prune, int include_ee, contact_out* o) {
-  prim_boxes bA = make_boxes(A), bB = make_boxes(B);
+ * do not overlap (a necessary condition for contact); with d_m > 0 B's boxes
+ * are widened by d_m and the contact test is the degree-six one. */
+static void pair_contacts(const ves_view* A, const ves_view* B, int prune, int include_ee, double dm,
+                          contact_out* o) {
+  prim_boxes bA = make_boxes(A, 0.0), bB = make_boxes(B, dm);
   for (int dir = 0; dir < 2; ++dir) {
     const ves_view* V = dir == 0 ? A : B;   /* vertex side */
     const ves_view* T = dir == 0 ? B : A;   /* triangle side */
@@ -787,7 +963,8 @@ static void pair_contacts(const ves_view* A, const ves_view* B, int prune, int i
         for (int q = 0; q < 4; ++q) D[q] = v3sub(P1[q], P0[q]);
         o->n_ops += 12;  /* the displacements */
         double tau, w1, w2;
-        int st = ccd_pair(ORC_VF, P0, D, &tau, &w1, &w2, &o->n_ops);
+        int st = dm > 0.0 ? ccd_pair_dm(ORC_VF, P0, D, dm, &tau, &w1, &w2)
+                          : ccd_pair(ORC_VF, P0, D, &tau, &w1, &w2, &o->n_ops);
         if (st == ORC_HIT) push_contact(o, dir, vp, t, tau, w1, w2);
         else if (st == ORC_DEGEN) o->n_degen++;
       }
@@ -810,7 +987,8 @@ static void pair_contacts(const ves_view* A, const ves_view* B, int prune, int i
         for (int q = 0; q < 4; ++q) D[q] = v3sub(P1[q], P0[q]);
         o->n_ops += 12;  /* the displacements */
         double tau, w1, w2;
-        int st = ccd_pair(ORC_EE, P0, D, &tau, &w1, &w2, &o->n_ops);
+        int st = dm > 0.0 ? ccd_pair_dm(ORC_EE, P0, D, dm, &tau, &w1, &w2)
+                          : ccd_pair(ORC_EE, P0, D, &tau, &w1, &w2, &o->n_ops);
         if (st == ORC_HIT) push_contact(o, 2, ea, eb, tau, w1, w2);
         else if (st == ORC_DEGEN) o->n_degen++;
       }
@@ -883,7 +1061,8 @@ static ves_view make_view(topo_cache* tc, const int* Pv, const int64_t* voff, co
  * OpenMP over pairs when compiled with it (nthreads <= 0: default). */
 int64_t orc_contacts(int nv_ves, const int* Pv, const int64_t* voff, const double* X,
                      int64_t npairs, const int32_t* pairs, const double* L,
-                     int prune, int include_ee, double eps_dt, int velocity_abs, int grad_x0, int nthreads,
+                     int prune, int include_ee, double dm, double eps_dt, int velocity_abs, int grad_x0,
+                     int nthreads,
                      int64_t cap, int32_t* cpair, int32_t* ctype, int32_t* ca, int32_t* cb,
                      double* ctau, double* cw, double* cV, double* V_pair,
                      double* grad, int32_t* gves, int32_t* gvid, int64_t* counts) {
@@ -906,7 +1085,7 @@ int64_t orc_contacts(int nv_ves, const int* Pv, const int64_t* voff, const doubl
     ves_view A = make_view(topo_for(cache, &ncache, Pv[i]), Pv, voff, X, i, NULL, L);
     ves_view B = make_view(topo_for(cache, &ncache, Pv[j]), Pv, voff, X, j, s, L);
     memset(&outs[r], 0, sizeof(contact_out));
-    pair_contacts(&A, &B, prune, include_ee, &outs[r]);
+    pair_contacts(&A, &B, prune, include_ee, dm, &outs[r]);
     int64_t n = outs[r].n;
     nbox += outs[r].n_boxpairs; ndeg += outs[r].n_degen; nops += outs[r].n_ops;
     pcnt[r] = n;
@@ -924,7 +1103,7 @@ int64_t orc_contacts(int nv_ves, const int* Pv, const int64_t* voff, const doubl
       contact_points(&A, &B, outs[r].type[q], outs[r].a[q], outs[r].b[q], P0, P1, side, vid);
       int kind = outs[r].type[q] == 2 ? ORC_EE : ORC_VF;
       double g[12];
-      double V = stiv_pair_dual(kind, P0, P1, outs[r].tau[q], eps_dt, velocity_abs, grad_x0, g);
+      double V = stiv_pair_dual(kind, P0, P1, outs[r].tau[q], eps_dt, dm, velocity_abs, grad_x0, g);
       vsum += V;
       if (k < cap) {
         cpair[k] = (int32_t)r; ctype[k] = outs[r].type[q]; ca[k] = outs[r].a[q]; cb[k] = outs[r].b[q];
