@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lcp", action="store_true", help="skip timing the contact LCP (assembly + solve)")
     ap.add_argument("--no-fidelity", action="store_true", help="skip the mesh-fidelity diagnostic")
+    ap.add_argument("--no-dm", action="store_true", help="skip timing the step with minimum separation d_m > 0")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -553,6 +554,37 @@ def run_ours(args, rank, world, local):
                    "median_err": float(np.median(e)), "max_err_over_R0": float(e.max() / G.R0_PAPER),
                    "points_per_launch": int(sum(2 * (4 * int(P) + 1) * 8 * int(P) for P in sc.P))}
 
+    # the step with minimum separation d_m > 0 (Eq. 3.1, degree six): the
+    # paper's d_m = 0.009 at R0 = 1.136 (Fig. 6), scaled to this R0 and
+    # inflated to (1 + 2 alpha) d_m with alpha = 0.05 (Sec. 3.1.2)
+    dm_rec = None
+    if not args.no_dm:
+        import dataclasses
+        from paper_1812_04719_gb300 import scenegen as G
+        dm_val = (1.0 + 2 * 0.05) * (0.009 / 1.136) * G.R0_PAPER
+        sc_dm = dataclasses.replace(sc, d_m=dm_val)
+        eng_dm = S.Stiv.for_scene(sc_dm, precision=prec, pair_cap=8192, contact_cap=1 << 20, device=dev)
+        ds_dm = S.DeviceScene.from_scene(sc_dm, precision=prec, device=dev)
+        eng_dm.step(ds_dm, grad=True)          # sizes the buffers
+        ms_d = []
+        for k in range(4):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rd = eng_dm.step(ds_dm, grad=True, use_graph=True, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if k >= 1:
+                ms_d.append(e0.elapsed_time(e1))
+        cdm = rd["counts"]
+        dm_rec = {"d_m": dm_val, "ms_per_step": float(np.mean(ms_d)),
+                  "value": sc.n * world / (float(np.mean(ms_d)) * 1e-3), "unit": UNIT,
+                  "contacts": int(cdm[S.C_VF] + cdm[S.C_EE]), "contact_pairs": int(cdm[S.C_CPAIRS]),
+                  "prim_pairs_tested": int(cdm[S.C_PRIM]),
+                  "note": "the same step (upsample + detect + V + dV/dX1) with the degree-six test on every "
+                          "primitive pair of the widened box test (no FP32 rejection)"}
+        eng_dm.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         nv, secs, threads, desc = oracle_sample(sc, args.cpu_seconds)
@@ -576,7 +608,7 @@ def run_ours(args, rank, world, local):
                            "prim_pairs_tested": int(counts[S.C_PRIM]), "patch_pairs": int(counts[S.C_PATCH]),
                            "prim_pairs_fp64": int(counts[S.C_EXACT])},
                 "roofline": roof, "roofline_fp64_kernel": roof_fp64, "fp64_form": fp64_form,
-                "cpu_baseline": cpu, "e2e": e2e, "lcp": lcp_rec, "mesh_fidelity": fid_rec,
+                "cpu_baseline": cpu, "e2e": e2e, "lcp": lcp_rec, "mesh_fidelity": fid_rec, "dm_step": dm_rec,
                 "gpu_launches": launches,
                 "clocks": clk, "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda x: -x[1])},
                 "wall_s": t_wall}

@@ -227,7 +227,7 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   if (w.W < out->capacity) w.W = out->capacity;
   w.C = out->capacity > 0 ? out->capacity : 1;
   w.Q3 = 16 * w.C + 4096;
-  w.Q2 = (h->prm.exact_only ? 32 : 4) * w.C + 4096;
+  w.Q2 = (h->prm.exact_only || h->prm.d_m > 0.0 ? 32 : 4) * w.C + 4096;
   int64_t smax = w.R > w.Q ? w.R : w.Q;
   if (w.C > smax) smax = w.C;
   w.sort_scratch_bytes = stiv_sort_scratch_impl(smax);
@@ -268,7 +268,8 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   char* b = (char*)h->ws;
   w.vbox = (double*)(b + o_vbox); w.pbox = (float*)(b + o_pbox); w.grid = (double*)(b + o_grid);
   w.vorg = (float*)(b + o_vorg); w.fprep = (float*)(b + o_fprep);
-  w.exact_only = h->prm.exact_only;
+  // the certified FP32 rejection is proved for the cubic (d_m = 0) only
+  w.exact_only = h->prm.exact_only || h->prm.d_m > 0.0;
   w.cell_count = (int32_t*)(b + o_cc); w.cell_off = (int32_t*)(b + o_co);
   w.rec_key = (uint64_t*)(b + o_rk); w.rec_val = (int32_t*)(b + o_rv);
   w.rec_key2 = (uint64_t*)(b + o_rk2); w.rec_val2 = (int32_t*)(b + o_rv2);

@@ -84,6 +84,7 @@ struct narrow_args {
   int64_t W;
   int include_ee;
   int exact_only;
+  double dm;                // minimum separation d_m (> 0: the degree-six contact test)
   int nlevel;               // refinement levels of the piece test (<= NLEVEL)
   const float* vorg;
   const float* fprep;
@@ -187,10 +188,10 @@ __device__ __forceinline__ int slot_vid(int k, int r0, int c0, int W, int P, boo
 // slot's conservative FP32 swept box (also returned in b).  s: periodic image
 // of the vesicle (applied to both time levels in FP64, as the contact test
 // sees it); off: FP32 offset of the vesicle's frame origin in the pair frame.
-template <bool MIXED>
+template <bool MIXED, bool DM>
 __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int64_t base, const float* fp, int nv,
                                            int vid, int k, const int* s, const double* sh, const float* off, float dx,
-                                           float* b) {
+                                           float* b, double pad, float padf) {
   int v = vid >= 0 ? vid : 0;
   S.vid[k] = vid;
   double x0[3], x1[3];
@@ -206,12 +207,19 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
     double p0 = x0[c], p1 = x1[c];
     if (s[c] != 0) { p0 = p0 + sh[c]; p1 = p1 + sh[c]; }
     long long k0 = dkey(p0), k1 = dkey(p1);
-    S.key[c][k] = k0 < k1 ? k0 : k1;
-    S.key[3 + c][k] = k0 < k1 ? k1 : k0;
+    if (DM && pad > 0.0) {   // d_m > 0: this side's boxes widened by d_m (FP64, as computed)
+      double lo = k0 < k1 ? p0 : p1, hi = k0 < k1 ? p1 : p0;
+      S.key[c][k] = dkey(__dsub_rn(lo, pad));
+      S.key[3 + c][k] = dkey(__dadd_rn(hi, pad));
+    } else {
+      S.key[c][k] = k0 < k1 ? k0 : k1;
+      S.key[3 + c][k] = k0 < k1 ? k1 : k0;
+    }
     float x = xf[c] + off[c], d = df[c];
     S.x[c][k] = x;
     S.d[c][k] = d;
     float m = dx + 4.7683716e-7f * (fabsf(x) + fabsf(d));  // 2^-21 (|x| + |d|)
+    if (DM) m = __fadd_ru(m, padf);                        // + d_m
     float lo = vid >= 0 ? fminf(x, x + d) - m : INFINITY;
     float hi = vid >= 0 ? fmaxf(x, x + d) + m : -INFINITY;
     S.lo[c][k] = lo;
@@ -224,7 +232,7 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
 // Stage the two patches of a patch pair (A: patch pa of vesicle i, unshifted;
 // B: patch pb of vesicle j at its periodic image), lanes over slots, both
 // patches' loads in flight together; patch boxes by warp reduction.
-template <bool MIXED>
+template <bool MIXED, bool DM>
 __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const PatchTopo* topo,
                                         const stiv_pair_info& pi, int pa, int pb, int lane) {
   int vi = pi.vi, vj = pi.vj, code = pi.code;
@@ -244,8 +252,10 @@ __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const 
   if (lane < NS) {
     int vidA = slot_vid(lane, IA * STIV_BR, JA * STIV_BC, WA, PA, fA, lA);
     int vidB = slot_vid(lane, IB * STIV_BR, JB * STIV_BC, WB, PB, fB, lB);
-    stage_slot<MIXED>(ws.A, a, pi.voff_i, a.fprep + (size_t)vi * a.fstride, nvA, vidA, lane, s0, sh0, offA, dx, bA);
-    stage_slot<MIXED>(ws.B, a, pi.voff_j, a.fprep + (size_t)vj * a.fstride, nvB, vidB, lane, s1, sh1, offB, dx, bB);
+    stage_slot<MIXED, DM>(ws.A, a, pi.voff_i, a.fprep + (size_t)vi * a.fstride, nvA, vidA, lane, s0, sh0, offA, dx, bA,
+                      0.0, 0.0f);
+    stage_slot<MIXED, DM>(ws.B, a, pi.voff_j, a.fprep + (size_t)vj * a.fstride, nvB, vidB, lane, s1, sh1, offB, dx, bB,
+                      a.dm, __double2float_ru(a.dm));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -788,6 +798,110 @@ __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w
 }
 
 // ---------------------------------------------------------------------------
+// Eq. 3.1 with d_m > 0: g(t) = f(t)^2 - d_m^2 |m(t)|^2 (f the cubic, m the
+// normal), degree six.  The roots of the derivatives, found from the linear
+// one upward, split [0, 1] into pieces on which each derivative (and finally
+// g) is monotone; each piece is taken as in the cubic test, and the first
+// piece also at t = 0 when g(0) <= 0.  The fixed FP64 sequence of the method
+// definition (plain FP64 instructions, no sign tiers); the stage-4 operation
+// count covers the d_m = 0 procedure only.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double horner_n(const double* c, int n, double t) {
+  double r = c[n];
+  for (int i = n - 1; i >= 0; --i) r = __fma_rn(r, t, c[i]);
+  return r;
+}
+
+__device__ double bisect_n(const double* c, int n, double lo, double hi, double flo) {
+  for (int it = 0; it < 64; ++it) {
+    double mid = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+    if (!(mid > lo && mid < hi)) break;
+    double fm = horner_n(c, n, mid);
+    if (is_zero(fm)) return mid;
+    if (is_neg(fm) == is_neg(flo)) { lo = mid; flo = fm; }
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __noinline__ int ccd64_dm(int kind, const d3* X0, const d3* D, double dm, double& tau, double& w1,
+                                     double& w2) {
+  d3 a, b, c, da, db, dc;
+  if (kind == KIND_VF) {
+    a = d3_sub(X0[2], X0[1]); b = d3_sub(X0[3], X0[1]); c = d3_sub(X0[0], X0[1]);
+    da = d3_sub(D[2], D[1]); db = d3_sub(D[3], D[1]); dc = d3_sub(D[0], D[1]);
+  } else {
+    a = d3_sub(X0[1], X0[0]); b = d3_sub(X0[3], X0[2]); c = d3_sub(X0[2], X0[0]);
+    da = d3_sub(D[1], D[0]); db = d3_sub(D[3], D[2]); dc = d3_sub(D[2], D[0]);
+  }
+  d3 n0 = d3_cross(a, b);
+  d3 n1 = d3_add(d3_cross(da, b), d3_cross(a, db));
+  d3 n2 = d3_cross(da, db);
+  double k0 = d3_dot(c, n0);
+  double k1 = __dadd_rn(d3_dot(dc, n0), d3_dot(c, n1));
+  double k2 = __dadd_rn(d3_dot(c, n2), d3_dot(dc, n1));
+  double k3 = d3_dot(dc, n2);
+  double q0 = d3_dot(n0, n0);
+  double q1 = __dmul_rn(2.0, d3_dot(n0, n1));
+  double q2 = __dadd_rn(d3_dot(n1, n1), __dmul_rn(2.0, d3_dot(n0, n2)));
+  double q3 = __dmul_rn(2.0, d3_dot(n1, n2));
+  double q4 = d3_dot(n2, n2);
+  double dd = __dmul_rn(dm, dm);
+  // C[k]: the k-th derivative of g, degree 6 - k
+  double C[6][7];
+  C[0][0] = __dsub_rn(__dmul_rn(k0, k0), __dmul_rn(dd, q0));
+  C[0][1] = __dsub_rn(__dmul_rn(2.0, __dmul_rn(k0, k1)), __dmul_rn(dd, q1));
+  C[0][2] = __dsub_rn(__dadd_rn(__dmul_rn(2.0, __dmul_rn(k0, k2)), __dmul_rn(k1, k1)), __dmul_rn(dd, q2));
+  C[0][3] = __dsub_rn(__dmul_rn(2.0, __dadd_rn(__dmul_rn(k0, k3), __dmul_rn(k1, k2))), __dmul_rn(dd, q3));
+  C[0][4] = __dsub_rn(__dadd_rn(__dmul_rn(2.0, __dmul_rn(k1, k3)), __dmul_rn(k2, k2)), __dmul_rn(dd, q4));
+  C[0][5] = __dmul_rn(2.0, __dmul_rn(k2, k3));
+  C[0][6] = __dmul_rn(k3, k3);
+  bool allz = true;
+  for (int i = 0; i <= 6; ++i) allz = allz && is_zero(C[0][i]);
+  if (allz) return 2;
+  for (int k = 1; k < 6; ++k)
+    for (int i = 0; i <= 6 - k; ++i) C[k][i] = __dmul_rn((double)(i + 1), C[k - 1][i + 1]);
+  // roots in (0, 1) of C[5] (linear), then C[4], ..., C[1] = g'
+  double rts[6], nrt[6];
+  int nr = 0;
+  if (!is_zero(C[5][1])) {
+    double t = __ddiv_rn(-C[5][0], C[5][1]);
+    if (t > 0.0 && t < 1.0) rts[nr++] = t;
+  }
+  for (int k = 4; k >= 1; --k) {
+    int n = 6 - k, nn = 0;
+    for (int sgi = 0; sgi <= nr; ++sgi) {
+      double l = sgi == 0 ? 0.0 : rts[sgi - 1], r = sgi == nr ? 1.0 : rts[sgi];
+      double fl = horner_n(C[k], n, l), fr = horner_n(C[k], n, r), t;
+      if (is_zero(fl)) t = l;
+      else if (is_zero(fr)) t = r;
+      else if (is_neg(fl) != is_neg(fr)) t = bisect_n(C[k], n, l, r, fl);
+      else continue;
+      if (t > 0.0 && t < 1.0 && (nn == 0 || t > nrt[nn - 1])) nrt[nn++] = t;
+    }
+    for (int i = 0; i < nn; ++i) rts[i] = nrt[i];
+    nr = nn;
+  }
+  bool degen = false;
+  for (int sgi = 0; sgi <= nr; ++sgi) {
+    double l = sgi == 0 ? 0.0 : rts[sgi - 1], r = sgi == nr ? 1.0 : rts[sgi];
+    double gl = horner_n(C[0], 6, l), gr = horner_n(C[0], 6, r), t;
+    if (sgi == 0 && (is_neg(gl) || is_zero(gl))) t = l;
+    else if (is_zero(gl)) t = l;
+    else if (is_zero(gr)) t = r;
+    else if (is_neg(gl) != is_neg(gr)) t = bisect_n(C[0], 6, l, r, gl);
+    else continue;
+    d3 Y[4];
+    for (int q = 0; q < 4; ++q) Y[q] = d3_at(X0[q], t, D[q]);
+    double u1 = 0.0, u2 = 0.0;
+    int in = inside64(kind, Y, u1, u2);
+    if (in < 0) { degen = true; continue; }
+    if (in == 1) { tau = t; w1 = u1; w2 = u2; return 1; }
+  }
+  return degen ? 2 : 0;
+}
+
+// ---------------------------------------------------------------------------
 // stages 2-4 on queued pairs
 // ---------------------------------------------------------------------------
 // queue entry: kind (0 = VF A->B, 1 = VF B->A, 2 = EE) << 16 | x << 8 | y
@@ -946,7 +1060,7 @@ __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, in
 }
 
 // Stages 1-3a: one warp per patch pair.
-template <bool MIXED>
+template <bool MIXED, bool DM>
 __global__ void __launch_bounds__(NW * 32, 4) narrow_kernel(narrow_args a) {
   extern __shared__ unsigned char smraw[];
   __shared__ PatchTopo topo[NVAR];
@@ -967,7 +1081,7 @@ __global__ void __launch_bounds__(NW * 32, 4) narrow_kernel(narrow_args a) {
     uint64_t w = a.work[item];
     int r = (int)(w >> 32), pa = (int)((w >> 16) & 0xFFFF), pb = (int)(w & 0xFFFF);
     stiv_pair_info pi = a.pinfo[r];
-    stage_pair<MIXED>(ws, a, topo, pi, pa, pb, lane);
+    stage_pair<MIXED, DM>(ws, a, topo, pi, pa, pb, lane);
     filter_patch(ws.A, ws.B.box, lane, ws.elo, ws.ehi);
     filter_patch(ws.B, ws.A.box, lane, nullptr, nullptr);
     int n1 = 0;
@@ -1153,7 +1267,7 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
 // ---------------------------------------------------------------------------
 // stage 4: the FP64 contact test, one descriptor per thread.
 // ---------------------------------------------------------------------------
-template <bool MIXED>
+template <bool MIXED, bool DM>
 __global__ void __launch_bounds__(128) fp64_kernel(narrow_args a) {
   int lane = threadIdx.x & 31;
   int64_t n2 = a.ctr[15];
@@ -1190,7 +1304,8 @@ __global__ void __launch_bounds__(128) fp64_kernel(narrow_args a) {
         D[q] = {__dsub_rn(p1[0], p0[0]), __dsub_rn(p1[1], p0[1]), __dsub_rn(p1[2], p0[2])};
       }
       flops += 12;  // displacements
-      int st = ccd64(ty == 2 ? KIND_EE : KIND_VF, X0, D, tau, w1, w2, flops);
+      int st = DM ? ccd64_dm(ty == 2 ? KIND_EE : KIND_VF, X0, D, a.dm, tau, w1, w2)
+                  : ccd64(ty == 2 ? KIND_EE : KIND_VF, X0, D, tau, w1, w2, flops);
       if (st == 1) {
         type = ty;
         if (ty == 2) {   // edge indices of the two edges (their vertex ids are ordered)
@@ -1239,7 +1354,7 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
                                                           const int32_t* cj, const int32_t* cs, int64_t cap,
                                                           int64_t W, uint64_t* work, int64_t* ctr, int mp,
                                                           const float* vorg, const int64_t* voff,
-                                                          stiv_pair_info* pinfo) {
+                                                          stiv_pair_info* pinfo, double dm) {
   extern __shared__ float psm[];
   int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* sbw = psm + (size_t)wid * 2 * mp * 6;                       // [2][mp][6]
@@ -1272,7 +1387,8 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
     float shlo[3], shhi[3];
     for (int c = 0; c < 3; ++c) {
       double sh = s[c] * L[c];
-      shlo[c] = __double2float_rd(sh); shhi[c] = __double2float_ru(sh);
+      // d_m > 0: vesicle j's patch boxes widened by d_m (rounded outward)
+      shlo[c] = __double2float_rd(__dsub_rd(sh, dm)); shhi[c] = __double2float_ru(__dadd_ru(sh, dm));
     }
     float bi[6], bj[6];
     for (int c = 0; c < 3; ++c) {
@@ -1346,7 +1462,7 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
     STIV_PROF(h, st, "patch_pairs");
     patch_pairs_kernel<<<blocks, 128, psmem, st>>>(p_dev, w.vbox, w.pbox, L[0], L[1], L[2], cand->i, cand->j,
                                                    cand->shift, cand->capacity, w.W, w.work, w.ctr, mp, w.vorg,
-                                                   voff, w.pinfo);
+                                                   voff, w.pinfo, h->prm.d_m);
   }
   STIV_LAUNCH(h);
   narrow_args a;
@@ -1356,6 +1472,7 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   a.L[0] = L[0]; a.L[1] = L[1]; a.L[2] = L[2];
   a.ci = cand->i; a.cj = cand->j; a.cs = cand->shift;
   a.work = w.work; a.W = w.W; a.include_ee = h->prm.include_ee; a.exact_only = w.exact_only;
+  a.dm = h->prm.d_m;
   a.nlevel = h->tune[STIV_TUNE_PIECE_LEVELS] > 0 ? h->tune[STIV_TUNE_PIECE_LEVELS] : 2;
   if (a.nlevel > NLEVEL) a.nlevel = NLEVEL;
   if (a.nlevel < 1) a.nlevel = 1;
@@ -1366,7 +1483,10 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   a.rc_tau = w.tmp_f64; a.rc_w = w.tmp_f64 + w.C;
   a.ctr = w.ctr;
   size_t smem = stiv_narrow_smem();
-  auto nk = mixed ? narrow_kernel<true> : narrow_kernel<false>;
+  // d_m > 0: widened boxes and the degree-six test, in kernels of their own
+  bool dmk = h->prm.d_m > 0.0;
+  auto nk = mixed ? (dmk ? narrow_kernel<true, true> : narrow_kernel<true, false>)
+                  : (dmk ? narrow_kernel<false, true> : narrow_kernel<false, false>);
   STIV_CUDA(h, cudaFuncSetAttribute(nk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   STIV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nk, NW * 32, smem));
@@ -1391,7 +1511,8 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   STIV_LAUNCH(h);
   {
     STIV_PROF(h, st, "fp64");
-    auto fk = mixed ? fp64_kernel<true> : fp64_kernel<false>;
+    auto fk = mixed ? (dmk ? fp64_kernel<true, true> : fp64_kernel<true, false>)
+                    : (dmk ? fp64_kernel<false, true> : fp64_kernel<false, false>);
     int fm = h->tune[STIV_TUNE_FP64_BLOCKS] > 0 ? h->tune[STIV_TUNE_FP64_BLOCKS] : 16;
     fk<<<num_sms * fm, 128, 0, st>>>(a);
   }

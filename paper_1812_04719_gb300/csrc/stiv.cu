@@ -46,8 +46,10 @@ struct contact_in {
 // Reverse mode: adjoints of the positions at tau (Yb), of the displacements
 // (Db) and of tau (taub); with Y = X0 + tau D, D = X1 - X0 and tau moving
 // along f(tau; X) = 0, dV/dX1 = Db + tau Yb - taub tau fY / f' and
-// dV/dX0 = -Db + (1 - tau) Yb - taub (1 - tau) fY / f'.
-__device__ double stiv_one(const contact_in& c, double e2, int vabs, d3* g, d3* g0) {
+// dV/dX0 = -Db + (1 - tau) Yb - taub (1 - tau) fY / f'.  dm2 = d_m^2 > 0:
+// tau is a root of g = f^2 - d_m^2 |m|^2 (Eq. 3.1, degree six) and fY, f'
+// are those of g: gY = 2 f fY - d_m^2 d|m|^2/dY, g' = sum gY . D.
+__device__ double stiv_one(const contact_in& c, double e2, int vabs, double dm2, d3* g, d3* g0) {
   d3 D[4], Y[4];
   for (int q = 0; q < 4; ++q) { D[q] = c.X1[q] - c.X0[q]; Y[q] = mk(fma(c.tau, D[q].x, c.X0[q].x), fma(c.tau, D[q].y, c.X0[q].y), fma(c.tau, D[q].z, c.X0[q].z)); }
   const double tau = c.tau;
@@ -90,6 +92,14 @@ __device__ double stiv_one(const contact_in& c, double e2, int vabs, d3* g, d3* 
     Yb[2] = ab; Yb[3] = bbv; Yb[0] = cb; Yb[1] = -(ab + bbv + cb);
     // df/dY of f = c . (a x b)
     fY[0] = m; fY[2] = cross(b, cc); fY[3] = cross(cc, a); fY[1] = -(fY[0] + fY[2] + fY[3]);
+    if (dm2 > 0.0) {   // d|m|^2 / dY2 = 2 b x m, dY3 = 2 m x a
+      double f2 = 2.0 * dot(cc, m);
+      d3 mY2 = 2.0 * cross(b, m), mY3 = 2.0 * cross(m, a), mY1 = -(mY2 + mY3);
+      fY[0] = f2 * fY[0];
+      fY[1] = f2 * fY[1] - dm2 * mY1;
+      fY[2] = f2 * fY[2] - dm2 * mY2;
+      fY[3] = f2 * fY[3] - dm2 * mY3;
+    }
   } else {
     d3 d1 = Y[1] - Y[0], d2 = Y[3] - Y[2], r = Y[0] - Y[2];
     double A = dot(d1, d1), B = dot(d1, d2), E = dot(d2, d2), C = dot(d1, r), F = dot(d2, r);
@@ -129,6 +139,14 @@ __device__ double stiv_one(const contact_in& c, double e2, int vabs, d3* g, d3* 
     d3 ce = Y[2] - Y[0];
     d3 fc = m, f1 = cross(d2, ce), f2 = cross(ce, d1);
     fY[2] = fc - f2; fY[0] = -fc - f1; fY[1] = f1; fY[3] = f2;
+    if (dm2 > 0.0) {   // d|m|^2 / dd1 = 2 d2 x m, dd2 = 2 m x d1
+      double ff = 2.0 * dot(ce, m);
+      d3 mY1 = 2.0 * cross(d2, m), mY3 = 2.0 * cross(m, d1);
+      fY[0] = ff * fY[0] + dm2 * mY1;
+      fY[1] = ff * fY[1] - dm2 * mY1;
+      fY[2] = ff * fY[2] + dm2 * mY3;
+      fY[3] = ff * fY[3] - dm2 * mY3;
+    }
   }
   double fp = 0.0;
   for (int q = 0; q < 4; ++q) { taub += dot(Yb[q], D[q]); fp += dot(fY[q], D[q]); }
@@ -150,6 +168,7 @@ struct stiv_args {
   const int64_t* counts;
   int64_t cap;
   double e2;
+  double dm2;      // d_m^2 (0: the cubic of Eq. 3.1)
   int vabs;
   double* Vc;
   double* grad;
@@ -202,7 +221,7 @@ __global__ void __launch_bounds__(128) stiv_kernel(stiv_args A) {
       c.X1[q] = vpos(A, ves[q], 1, vid[q], sh[q]);
     }
     d3 g[4], g0[4];
-    double V = stiv_one(c, A.e2, A.vabs, A.grad ? g : nullptr, A.grad0 ? g0 : nullptr);
+    double V = stiv_one(c, A.e2, A.vabs, A.dm2, A.grad ? g : nullptr, A.grad0 ? g0 : nullptr);
     if (A.Vc) A.Vc[k] = V;
     if (A.grad) {
       for (int q = 0; q < 4; ++q) {
@@ -493,6 +512,7 @@ static int run_stiv(stiv_handle* h, void* stream, const int32_t* p_dev, const in
   double edt = h->prm.eps * h->prm.dt;
   A.e2 = edt * edt;
   A.vabs = h->prm.velocity == STIV_VEL_ABSOLUTE;
+  A.dm2 = h->prm.d_m * h->prm.d_m;
   A.Vc = Vtmp; A.grad = grad; A.gves = gves; A.gvid = gvid; A.grad0 = grad0;
   int dev_sms = 152;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device);

@@ -111,3 +111,41 @@ def test_whole_scene_lists(orc, name, prec):
     assert np.array_equal(bits(g["w"]), bits(c["w"]))
     assert np.all(np.abs(g["V_pair"] - c["V_pair"]) <= 1e-10 * np.abs(c["V_pair"]))
     assert g["counts"][S.C_PRIM] == c["counts"][1]
+
+
+def test_dm_sampled_pairs_1440(orc):
+    """The 1440-vesicle workload with minimum separation d_m (the paper's
+    0.009 at R0 = 1.136 scaled to R0 and inflated by 1 + 2 alpha, the degree-six
+    test), MIXED form, graph replay on the oracle's vertices: the candidate
+    list bit for bit, and contacts, volumes and gradient rows on a sample of
+    pairs the oracle recomputes."""
+    import dataclasses
+    dm = 1.1 * (0.009 / 1.136) * G.R0_PAPER
+    sc = dataclasses.replace(G.scene_1440(), d_m=dm)
+    g = run_gpu_on(sc, oracle_vertices(sc), precision=S.STIV_MIXED, grad=True, use_graph=True, replays=3,
+                   pair_cap=8192, contact_cap=1 << 20)
+    Xs = verts_list(sc, g["verts"])
+    boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
+    pairs = orc.candidate_pairs(boxes, sc.L)
+    assert np.array_equal(gpu_pairs_rows(g), pairs)
+    rng = np.random.default_rng(12)
+    hit = np.nonzero(g["V_pair"] > 0)[0]
+    miss = np.nonzero(g["V_pair"] == 0)[0]
+    sample = np.sort(np.concatenate([rng.choice(hit, 16, replace=False), rng.choice(miss, 8, replace=False)]))
+    c = orc.contacts(sc.P, Xs, pairs[sample], sc.L, sc.eps * sc.dt, grad=True, d_m=dm)
+    n_checked = 0
+    for k, r in enumerate(sample):
+        gm = g["pair"] == r
+        cm = c["pair"] == k
+        for key in ("type", "a", "b"):
+            assert np.array_equal(g[key][gm], c[key][cm]), (r, key)
+        assert np.array_equal(bits(g["tau"][gm]), bits(c["tau"][cm]))
+        assert np.array_equal(bits(g["w"][gm]), bits(c["w"][cm]))
+        assert abs(g["V_pair"][r] - c["V_pair"][k]) <= 1e-10 * abs(c["V_pair"][k])
+        gr, cr = g["grad"][gm], c["grad"][cm]
+        if len(cr):
+            scale = np.abs(cr).reshape(len(cr), -1).max(axis=1)
+            err = np.abs(gr - cr).reshape(len(cr), -1).max(axis=1)
+            assert np.all(err <= 1e-9 * scale + 1e-300)
+        n_checked += int(gm.sum())
+    assert n_checked > 500
