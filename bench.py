@@ -591,8 +591,8 @@ def run_ours(args, rank, world, local):
                   "value": sc.n * world / (float(np.mean(ms_d)) * 1e-3), "unit": UNIT,
                   "contacts": int(cdm[S.C_VF] + cdm[S.C_EE]), "contact_pairs": int(cdm[S.C_CPAIRS]),
                   "prim_pairs_tested": int(cdm[S.C_PRIM]),
-                  "note": "the same step (upsample + detect + V + dV/dX1) with the degree-six test on every "
-                          "primitive pair of the widened box test (no FP32 rejection)"}
+                  "note": "the same step (upsample + detect + V + dV/dX1) with the degree-six test on the "
+                          "primitive pairs of the widened box test that the certified FP32 band rejection keeps"}
         eng_dm.close()
 
     cpu = None

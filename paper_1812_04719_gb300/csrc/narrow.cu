@@ -85,6 +85,7 @@ struct narrow_args {
   int include_ee;
   int exact_only;
   double dm;                // minimum separation d_m (> 0: the degree-six contact test)
+  int dm_filter;            // d_m > 0: the certified FP32 band rejection (off with exact_only)
   int nlevel;               // refinement levels of the piece test (<= NLEVEL)
   const float* vorg;
   const float* fprep;
@@ -519,6 +520,41 @@ __device__ int bernstein_reject(const cubic32& q) {
   if (fabsf(q.k0) <= q.E && fabsf(q.k1) <= q.E && fabsf(q.k2) <= q.E && fabsf(q.k3) <= q.E) return 0;
   float b1 = q.k0 + q.k1 * (1.f / 3.f), b2 = q.k0 + (2.f * q.k1 + q.k2) * (1.f / 3.f), b3 = q.k0 + q.k1 + q.k2 + q.k3;
   return certain_sign4(q.k0, b1, b2, b3, q.E) ? 1 : 0;
+}
+
+// Stage 3a with d_m > 0: 1 if the point certainly stays farther than d_m from
+// the triangle's plane (the lines farther than d_m apart) over the whole step,
+// so that g = f^2 - d_m^2 |m|^2 stays positive and the FP64 degree-six test
+// finds no candidate time.  min |f| over [0, 1] is bounded below by the
+// smallest Bernstein coefficient of the cubic (all of one sign beyond the
+// error bound E); |m(t)| <= |n0| + |n1| + |n2| is bounded above from the FP32
+// cross products with their error bounds (the error model of cubic_fp32); a
+// margin of 1e-12 of the squared magnitudes covers the FP64 evaluation of g.
+__device__ int band_reject(int kind, const f3* x, const f3* d, float ep, float dm) {
+  cubic32 q = cubic_fp32(kind, x, d, ep);
+  float b1 = q.k0 + q.k1 * (1.f / 3.f), b2 = q.k0 + (2.f * q.k1 + q.k2) * (1.f / 3.f), b3 = q.k0 + q.k1 + q.k2 + q.k3;
+  if (!certain_sign4(q.k0, b1, b2, b3, q.E)) return 0;
+  float fmin = fminf(fminf(fabsf(q.k0), fabsf(b1)), fminf(fabsf(b2), fabsf(b3))) - q.E;
+  f3 a, b, da, db;
+  if (kind == 0) {
+    a = fsub(x[2], x[1]); b = fsub(x[3], x[1]); da = fsub(d[2], d[1]); db = fsub(d[3], d[1]);
+  } else {
+    a = fsub(x[1], x[0]); b = fsub(x[3], x[2]); da = fsub(d[1], d[0]); db = fsub(d[3], d[2]);
+  }
+  f3 n0 = fcross(a, b), n1 = fadd(fcross(da, b), fcross(a, db)), n2 = fcross(da, db);
+  float A = fmaxf(amax3(a), amax3(b)), Ad = fmaxf(amax3(da), amax3(db));
+  float Dm = 0.f;
+  for (int k = 0; k < 4; ++k) Dm = fmaxf(Dm, amax3(d[k]));
+  float ed = 2.0f * U32 * Dm + 1e-12f;
+  float epd = 2.0f * ep + 2.0f * U32 * A, edd = 2.0f * ed + 2.0f * U32 * Ad;
+  float en = 2.0f * ((4.f * epd * A + 4.f * U32 * A * A) + (4.f * edd * A + 4.f * epd * Ad + 8.f * U32 * A * Ad) +
+                     (4.f * edd * Ad + 4.f * U32 * Ad * Ad));
+  float mn = fnorm(n0) + fnorm(n1) + fnorm(n2);
+  float mmax = mn * (1.f + 8.f * U32) + en;
+  float S = fabsf(q.k0) + fabsf(q.k1) + fabsf(q.k2) + fabsf(q.k3) + 4.f * q.E;
+  float dmm = dm * (1.f + 4.f * U32) * mmax;
+  float rhs = dmm * dmm * (1.f + 1e-5f) + 1e-12f * (S * S + dmm * dmm);
+  return (fmin > 0.f && fmin * fmin * (1.f - 1e-5f) > rhs) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -992,6 +1028,7 @@ __device__ __forceinline__ void load_f32(const int* sl, int kind, const PatchSm*
 // Stage 2 (exact box) and 3a (Bernstein) on up to n entries of q1; survivors
 // go to the global list of stage 3b (of stage 4 when the FP32 rejection is
 // off) as descriptors.
+template <bool DM>
 __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, const narrow_args& a,
                                           long long& nprim) {
   bool keep = false;
@@ -1014,7 +1051,13 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
     if (hit) {
       ++nprim;
       keep = true;
-      if (!a.exact_only) {
+      if (DM) {
+        if (a.dm_filter) {   // d_m > 0: drop pairs that certainly stay out of the d_m band
+          f3 xq[4], dq[4];
+          load_f32(sl, kind, SA, SB, xq, dq);
+          keep = !band_reject(kind == 2 ? 1 : 0, xq, dq, ws.dx, (float)a.dm);
+        }
+      } else if (!a.exact_only) {
         f3 xq[4], dq[4];
         load_f32(sl, kind, SA, SB, xq, dq);
         cubic32 q = cubic_fp32(kind == 2 ? 1 : 0, xq, dq, ws.dx);
@@ -1036,12 +1079,13 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
       }
     }
   }
-  if (a.exact_only) push_global(a.q2, a.Q2, &a.ctr[15], &a.ctr[STIV_C_STATUS], keep, desc, lane);
+  if (DM || a.exact_only) push_global(a.q2, a.Q2, &a.ctr[15], &a.ctr[STIV_C_STATUS], keep, desc, lane);
   else push_global(a.q3, a.Q3, &a.ctr[14], &a.ctr[STIV_C_STATUS], keep, desc, lane);
 }
 
 // Queue the hits of one stage-1 test (n1: the queue length, the same in every
 // lane); 32 queued entries go through stages 2 and 3a.
+template <bool DM>
 __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, int lane, int r, const narrow_args& a,
                                         long long& nprim, int& n1) {
   unsigned m = __ballot_sync(0xffffffffu, hit);
@@ -1050,7 +1094,7 @@ __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, in
   n1 += __popc(m);
   if (n1 >= 32) {
     __syncwarp();
-    stage_filter(ws, 32, lane, r, a, nprim);
+    stage_filter<DM>(ws, 32, lane, r, a, nprim);
     unsigned rest = (lane + 32 < n1) ? ws.q1[lane + 32] : 0;
     __syncwarp();
     if (lane + 32 < n1) ws.q1[lane] = rest;
@@ -1101,7 +1145,7 @@ __global__ void __launch_bounds__(NW * 32, 4) narrow_kernel(narrow_args a) {
           float4 lo = V.vlo[xk], hi = V.vhi[xk];
           float vb[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
           bool hit = valid && fbox_hit(vb, tb);
-          enqueue(ws, hit, ((unsigned)dir << 16) | ((unsigned)V.vf[xk] << 8) | (unsigned)y, lane, r, a, nprim, n1);
+          enqueue<DM>(ws, hit, ((unsigned)dir << 16) | ((unsigned)V.vf[xk] << 8) | (unsigned)y, lane, r, a, nprim, n1);
         }
       }
     }
@@ -1117,12 +1161,12 @@ __global__ void __launch_bounds__(NW * 32, 4) narrow_kernel(narrow_args a) {
           float4 lo = ws.elo[xk], hi = ws.ehi[xk];
           float ab[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
           bool hit = valid && fbox_hit(ab, eb);
-          enqueue(ws, hit, (2u << 16) | ((unsigned)ws.A.ef[xk] << 8) | (unsigned)y, lane, r, a, nprim, n1);
+          enqueue<DM>(ws, hit, (2u << 16) | ((unsigned)ws.A.ef[xk] << 8) | (unsigned)y, lane, r, a, nprim, n1);
         }
       }
     }
     __syncwarp();
-    if (n1 > 0) stage_filter(ws, n1, lane, r, a, nprim);
+    if (n1 > 0) stage_filter<DM>(ws, n1, lane, r, a, nprim);
     item = __shfl_sync(0xffffffffu, next, 0);
   }
   for (int off = 16; off > 0; off >>= 1) nprim += __shfl_down_sync(0xffffffffu, nprim, off);
@@ -1473,6 +1517,7 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   a.ci = cand->i; a.cj = cand->j; a.cs = cand->shift;
   a.work = w.work; a.W = w.W; a.include_ee = h->prm.include_ee; a.exact_only = w.exact_only;
   a.dm = h->prm.d_m;
+  a.dm_filter = !h->prm.exact_only;
   a.nlevel = h->tune[STIV_TUNE_PIECE_LEVELS] > 0 ? h->tune[STIV_TUNE_PIECE_LEVELS] : 2;
   if (a.nlevel > NLEVEL) a.nlevel = NLEVEL;
   if (a.nlevel < 1) a.nlevel = 1;

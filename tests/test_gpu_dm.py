@@ -58,3 +58,29 @@ def test_dm_graph_replay_and_more_contacts():
     assert np.array_equal(bits(e["tau"]), bits(r["tau"]))
     z = run_gpu_on(sc0, X)
     assert len(e["pair"]) > len(z["pair"])
+
+
+@pytest.mark.parametrize("precision", [S.STIV_FP64, S.STIV_MIXED])
+def test_dm_band_filter_is_exact(precision):
+    """The certified FP32 band rejection changes no result: with and without
+    it (exact_only) the contact lists, times, weights and counts agree bit for
+    bit on the 144-vesicle piece of the 58% lattice, and it keeps a large
+    share of the pairs (those that certainly stay out of the band over the
+    whole step) away from the FP64 degree-six test."""
+    from paper_1812_04719_gb300 import scenegen as G
+    dm = 1.1 * (0.009 / 1.136) * G.R0_PAPER
+    sc = dataclasses.replace(G.scene_lattice58((6, 6, 2)), d_m=dm)
+    X = oracle_vertices(sc)
+    kw = dict(precision=precision, pair_cap=2048, contact_cap=1 << 18)
+    f = run_gpu_on(sc, X, **kw)
+    x = run_gpu_on(sc, X, eng=S.Stiv.for_scene(sc, precision=precision, pair_cap=2048, contact_cap=1 << 18,
+                                                exact_only=True), **kw)
+    assert f["counts"][S.C_VF] + f["counts"][S.C_EE] > 10000
+    for k in ("i", "j", "shift", "pair", "type", "a", "b"):
+        assert np.array_equal(f[k], x[k]), k
+    assert np.array_equal(bits(f["tau"]), bits(x["tau"]))
+    assert np.array_equal(bits(f["w"]), bits(x["w"]))
+    for c in (S.C_PAIRS, S.C_PRIM, S.C_VF, S.C_EE, S.C_CPAIRS, S.C_DEGEN):
+        assert f["counts"][c] == x["counts"][c], c
+    assert f["counts"][S.C_EXACT] < 0.7 * x["counts"][S.C_EXACT]
+    print(f"band filter: {f['counts'][S.C_EXACT]} of {x['counts'][S.C_EXACT]} pairs reach the FP64 test")
