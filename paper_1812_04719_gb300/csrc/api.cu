@@ -268,8 +268,7 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   char* b = (char*)h->ws;
   w.vbox = (double*)(b + o_vbox); w.pbox = (float*)(b + o_pbox); w.grid = (double*)(b + o_grid);
   w.vorg = (float*)(b + o_vorg); w.fprep = (float*)(b + o_fprep);
-  // the certified FP32 rejection is proved for the cubic (d_m = 0) only
-  w.exact_only = h->prm.exact_only || h->prm.d_m > 0.0;
+  w.exact_only = h->prm.exact_only;
   w.cell_count = (int32_t*)(b + o_cc); w.cell_off = (int32_t*)(b + o_co);
   w.rec_key = (uint64_t*)(b + o_rk); w.rec_val = (int32_t*)(b + o_rv);
   w.rec_key2 = (uint64_t*)(b + o_rk2); w.rec_val2 = (int32_t*)(b + o_rv2);

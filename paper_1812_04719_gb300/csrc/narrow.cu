@@ -85,7 +85,6 @@ struct narrow_args {
   int include_ee;
   int exact_only;
   double dm;                // minimum separation d_m (> 0: the degree-six contact test)
-  int dm_filter;            // d_m > 0: the certified FP32 band rejection (off with exact_only)
   int nlevel;               // refinement levels of the piece test (<= NLEVEL)
   const float* vorg;
   const float* fprep;
@@ -530,11 +529,8 @@ __device__ int bernstein_reject(const cubic32& q) {
 // error bound E); |m(t)| <= |n0| + |n1| + |n2| is bounded above from the FP32
 // cross products with their error bounds (the error model of cubic_fp32); a
 // margin of 1e-12 of the squared magnitudes covers the FP64 evaluation of g.
-__device__ int band_reject(int kind, const f3* x, const f3* d, float ep, float dm) {
-  cubic32 q = cubic_fp32(kind, x, d, ep);
-  float b1 = q.k0 + q.k1 * (1.f / 3.f), b2 = q.k0 + (2.f * q.k1 + q.k2) * (1.f / 3.f), b3 = q.k0 + q.k1 + q.k2 + q.k3;
-  if (!certain_sign4(q.k0, b1, b2, b3, q.E)) return 0;
-  float fmin = fminf(fminf(fabsf(q.k0), fabsf(b1)), fminf(fabsf(b2), fabsf(b3))) - q.E;
+// Right-hand side of the band test: (d_m max|m|)^2 with its margins.
+__device__ float band_rhs(int kind, const f3* x, const f3* d, float ep, float dm, const cubic32& q) {
   f3 a, b, da, db;
   if (kind == 0) {
     a = fsub(x[2], x[1]); b = fsub(x[3], x[1]); da = fsub(d[2], d[1]); db = fsub(d[3], d[1]);
@@ -553,8 +549,22 @@ __device__ int band_reject(int kind, const f3* x, const f3* d, float ep, float d
   float mmax = mn * (1.f + 8.f * U32) + en;
   float S = fabsf(q.k0) + fabsf(q.k1) + fabsf(q.k2) + fabsf(q.k3) + 4.f * q.E;
   float dmm = dm * (1.f + 4.f * U32) * mmax;
-  float rhs = dmm * dmm * (1.f + 1e-5f) + 1e-12f * (S * S + dmm * dmm);
-  return (fmin > 0.f && fmin * fmin * (1.f - 1e-5f) > rhs) ? 1 : 0;
+  return dmm * dmm * (1.f + 1e-5f) + 1e-12f * (S * S + dmm * dmm);
+}
+
+// 1 if the Bernstein coefficients c0..c3 (error E) of the cubic on an
+// interval prove |f| > d_m max|m| there (rhs: band_rhs).
+__device__ __forceinline__ bool out_of_band(float c0, float c1, float c2, float c3, float E, float rhs) {
+  if (!certain_sign4(c0, c1, c2, c3, E)) return false;
+  float fmin = fminf(fminf(fabsf(c0), fabsf(c1)), fminf(fabsf(c2), fabsf(c3))) - E;
+  return fmin > 0.f && fmin * fmin * (1.f - 1e-5f) > rhs;
+}
+
+__device__ int band_reject(int kind, const f3* x, const f3* d, float ep, float dm) {
+  cubic32 q = cubic_fp32(kind, x, d, ep);
+  float b1 = q.k0 + q.k1 * (1.f / 3.f), b2 = q.k0 + (2.f * q.k1 + q.k2) * (1.f / 3.f), b3 = q.k0 + q.k1 + q.k2 + q.k3;
+  if (!certain_sign4(q.k0, b1, b2, b3, q.E)) return 0;
+  return out_of_band(q.k0, b1, b2, b3, q.E, band_rhs(kind, x, d, ep, dm, q)) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1051,12 +1061,10 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
     if (hit) {
       ++nprim;
       keep = true;
-      if (DM) {
-        if (a.dm_filter) {   // d_m > 0: drop pairs that certainly stay out of the d_m band
-          f3 xq[4], dq[4];
-          load_f32(sl, kind, SA, SB, xq, dq);
-          keep = !band_reject(kind == 2 ? 1 : 0, xq, dq, ws.dx, (float)a.dm);
-        }
+      if (DM && !a.exact_only) {   // d_m > 0: drop pairs that certainly stay out of the d_m band
+        f3 xq[4], dq[4];
+        load_f32(sl, kind, SA, SB, xq, dq);
+        keep = !band_reject(kind == 2 ? 1 : 0, xq, dq, ws.dx, (float)a.dm);
       } else if (!a.exact_only) {
         f3 xq[4], dq[4];
         load_f32(sl, kind, SA, SB, xq, dq);
@@ -1079,7 +1087,7 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
       }
     }
   }
-  if (DM || a.exact_only) push_global(a.q2, a.Q2, &a.ctr[15], &a.ctr[STIV_C_STATUS], keep, desc, lane);
+  if (a.exact_only) push_global(a.q2, a.Q2, &a.ctr[15], &a.ctr[STIV_C_STATUS], keep, desc, lane);
   else push_global(a.q3, a.Q3, &a.ctr[14], &a.ctr[STIV_C_STATUS], keep, desc, lane);
 }
 
@@ -1189,11 +1197,17 @@ static_assert(NPIECE << (NLEVEL - 1) <= 1024, "piece index fits 10 bits");
 struct PieceWarp {
   float x[32][4][3], d[32][4][3];
   float k[32][4], E[32], ep[32], ed[32];
+  float rhs[32];   // d_m > 0: band_rhs of each pair
   int kind[32], fail[32];
   unsigned short task[MAXTASK], task2[MAXTASK];
   int ntask2;
 };
 
+// DM (d_m > 0): a piece is kept when the point may be within d_m of the plane
+// there (out_of_band fails) instead of when the cubic may have a root; the
+// inside certificate is the same, because the degree-six test uses the same
+// inside test at its candidate times.
+template <bool DM>
 __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
   extern __shared__ unsigned char psraw[];
   PieceWarp& W = ((PieceWarp*)psraw)[threadIdx.x >> 5];
@@ -1220,6 +1234,7 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
       }
       W.k[lane][0] = q.k0; W.k[lane][1] = q.k1; W.k[lane][2] = q.k2; W.k[lane][3] = q.k3;
       W.E[lane] = q.E; W.ep[lane] = ep; W.ed[lane] = q.ed; W.kind[lane] = kind;
+      if (DM) W.rhs[lane] = band_rhs(kind, xq, dq, ep, (float)a.dm, q);
       if (fabsf(q.k0) <= q.E && fabsf(q.k1) <= q.E && fabsf(q.k2) <= q.E && fabsf(q.k3) <= q.E) {
         W.fail[lane] = 1;   // may vanish identically: FP64 decides (degenerate)
       } else {
@@ -1230,8 +1245,9 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
           float f0 = fmaf(fmaf(fmaf(q.k3, t0, q.k2), t0, q.k1), t0, q.k0);
           float fp1 = fmaf(fmaf(3.f * q.k3, t0, 2.f * q.k2), t0, q.k1);
           float g1 = w * fp1, g2 = w * w * fmaf(3.f * q.k3, t0, q.k2), g3 = w * w * w * q.k3;
-          if (!certain_sign4(f0, f0 + g1 * (1.f / 3.f), f0 + (2.f * g1 + g2) * (1.f / 3.f), f0 + g1 + g2 + g3, q.E))
-            mask |= 1u << p;
+          float c1 = f0 + g1 * (1.f / 3.f), c2 = f0 + (2.f * g1 + g2) * (1.f / 3.f), c3 = f0 + g1 + g2 + g3;
+          bool keep_p = DM ? !out_of_band(f0, c1, c2, c3, q.E, W.rhs[lane]) : !certain_sign4(f0, c1, c2, c3, q.E);
+          if (keep_p) mask |= 1u << p;
         }
       }
     }
@@ -1269,8 +1285,8 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
             float f0 = fmaf(fmaf(fmaf(k3, tl, k2), tl, k1), tl, k0);
             float fp1 = fmaf(fmaf(3.f * k3, tl, 2.f * k2), tl, k1);
             float g1 = w * fp1, g2 = w * w * fmaf(3.f * k3, tl, k2), g3 = w * w * w * k3;
-            may_root = !certain_sign4(f0, f0 + g1 * (1.f / 3.f), f0 + (2.f * g1 + g2) * (1.f / 3.f),
-                                      f0 + g1 + g2 + g3, E);
+            float c1 = f0 + g1 * (1.f / 3.f), c2 = f0 + (2.f * g1 + g2) * (1.f / 3.f), c3 = f0 + g1 + g2 + g3;
+            may_root = DM ? !out_of_band(f0, c1, c2, c3, E, W.rhs[owner]) : !certain_sign4(f0, c1, c2, c3, E);
           }
           if (may_root) {
             f3 xq[4], dq[4];
@@ -1517,7 +1533,6 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   a.ci = cand->i; a.cj = cand->j; a.cs = cand->shift;
   a.work = w.work; a.W = w.W; a.include_ee = h->prm.include_ee; a.exact_only = w.exact_only;
   a.dm = h->prm.d_m;
-  a.dm_filter = !h->prm.exact_only;
   a.nlevel = h->tune[STIV_TUNE_PIECE_LEVELS] > 0 ? h->tune[STIV_TUNE_PIECE_LEVELS] : 2;
   if (a.nlevel > NLEVEL) a.nlevel = NLEVEL;
   if (a.nlevel < 1) a.nlevel = 1;
@@ -1544,14 +1559,15 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   STIV_LAUNCH(h);
   if (!w.exact_only) {
     size_t psm2 = sizeof(PieceWarp) * PW;
-    STIV_CUDA(h, cudaFuncSetAttribute(pieces_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm2));
+    auto pk = dmk ? pieces_kernel<true> : pieces_kernel<false>;
+    STIV_CUDA(h, cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm2));
     int per_sm2 = 0;
-    STIV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, pieces_kernel, PW * 32, psm2));
+    STIV_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, pk, PW * 32, psm2));
     if (h->tune[STIV_TUNE_PIECES_CTAS] > 0 && h->tune[STIV_TUNE_PIECES_CTAS] < per_sm2)
       per_sm2 = h->tune[STIV_TUNE_PIECES_CTAS];
     if (per_sm2 < 1) per_sm2 = 1;
     STIV_PROF(h, st, "pieces");
-    pieces_kernel<<<per_sm2 * num_sms, PW * 32, psm2, st>>>(a);
+    pk<<<per_sm2 * num_sms, PW * 32, psm2, st>>>(a);
   }
   STIV_LAUNCH(h);
   {

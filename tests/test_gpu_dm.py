@@ -64,9 +64,9 @@ def test_dm_graph_replay_and_more_contacts():
 def test_dm_band_filter_is_exact(precision):
     """The certified FP32 band rejection changes no result: with and without
     it (exact_only) the contact lists, times, weights and counts agree bit for
-    bit on the 144-vesicle piece of the 58% lattice, and it keeps a large
-    share of the pairs (those that certainly stay out of the band over the
-    whole step) away from the FP64 degree-six test."""
+    bit on the 144-vesicle piece of the 58% lattice, and it keeps most pairs
+    away from the FP64 degree-six test (those certainly out of the band over
+    the step, and those outside the primitive wherever they may be in it)."""
     from paper_1812_04719_gb300 import scenegen as G
     dm = 1.1 * (0.009 / 1.136) * G.R0_PAPER
     sc = dataclasses.replace(G.scene_lattice58((6, 6, 2)), d_m=dm)
@@ -82,5 +82,5 @@ def test_dm_band_filter_is_exact(precision):
     assert np.array_equal(bits(f["w"]), bits(x["w"]))
     for c in (S.C_PAIRS, S.C_PRIM, S.C_VF, S.C_EE, S.C_CPAIRS, S.C_DEGEN):
         assert f["counts"][c] == x["counts"][c], c
-    assert f["counts"][S.C_EXACT] < 0.7 * x["counts"][S.C_EXACT]
+    assert f["counts"][S.C_EXACT] < 0.2 * x["counts"][S.C_EXACT]
     print(f"band filter: {f['counts'][S.C_EXACT]} of {x['counts'][S.C_EXACT]} pairs reach the FP64 test")
