@@ -1111,9 +1111,10 @@ __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, in
   }
 }
 
-// Stages 1-3a: one warp per patch pair.
+// Stages 1-3a: one warp per patch pair.  Three CTAs per SM leave 80
+// registers a thread (four leave 64, with spills in the staging code).
 template <bool MIXED, bool DM>
-__global__ void __launch_bounds__(NW * 32, 4) narrow_kernel(narrow_args a) {
+__global__ void __launch_bounds__(NW * 32, 3) narrow_kernel(narrow_args a) {
   extern __shared__ unsigned char smraw[];
   __shared__ PatchTopo topo[NVAR];
   WarpSm& ws = ((WarpSm*)smraw)[threadIdx.x >> 5];
