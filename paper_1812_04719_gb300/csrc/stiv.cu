@@ -49,7 +49,11 @@ struct contact_in {
 // dV/dX0 = -Db + (1 - tau) Yb - taub (1 - tau) fY / f'.  dm2 = d_m^2 > 0:
 // tau is a root of g = f^2 - d_m^2 |m|^2 (Eq. 3.1, degree six) and fY, f'
 // are those of g: gY = 2 f fY - d_m^2 d|m|^2/dY, g' = sum gY . D.
+// VAR = false compiles the common case (relative velocity, d_m = 0, no X0
+// rows) without the variants' code.
+template <bool VAR>
 __device__ double stiv_one(const contact_in& c, double e2, int vabs, double dm2, d3* g, d3* g0) {
+  if (!VAR) { vabs = 0; dm2 = 0.0; g0 = nullptr; }
   d3 D[4], Y[4];
   for (int q = 0; q < 4; ++q) { D[q] = c.X1[q] - c.X0[q]; Y[q] = mk(fma(c.tau, D[q].x, c.X0[q].x), fma(c.tau, D[q].y, c.X0[q].y), fma(c.tau, D[q].z, c.X0[q].z)); }
   const double tau = c.tau;
@@ -194,7 +198,10 @@ __device__ __forceinline__ int64_t n_contacts(const int64_t* counts, int64_t cap
   return n < cap ? n : cap;
 }
 
-__global__ void __launch_bounds__(128) stiv_kernel(stiv_args A) {
+// VAR: the variants (absolute velocity, d_m > 0, X0 rows) in an instance of
+// their own; the common one fits 128 registers (4 CTAs per SM).
+template <bool VAR>
+__global__ void __launch_bounds__(128, 4) stiv_kernel(stiv_args A) {
   int64_t n = n_contacts(A.counts, A.cap);
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     int r = A.pair[k], ty = A.type[k], pa = A.a[k], pb = A.b[k];
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(128) stiv_kernel(stiv_args A) {
       c.X1[q] = vpos(A, ves[q], 1, vid[q], sh[q]);
     }
     d3 g[4], g0[4];
-    double V = stiv_one(c, A.e2, A.vabs, A.dm2, A.grad ? g : nullptr, A.grad0 ? g0 : nullptr);
+    double V = stiv_one<VAR>(c, A.e2, A.vabs, A.dm2, A.grad ? g : nullptr, A.grad0 ? g0 : nullptr);
     if (A.Vc) A.Vc[k] = V;
     if (A.grad) {
       for (int q = 0; q < 4; ++q) {
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(128) stiv_kernel(stiv_args A) {
         A.gves[4 * k + q] = ves[q]; A.gvid[4 * k + q] = vid[q];
       }
     }
-    if (A.grad0)
+    if (VAR && A.grad0)
       for (int q = 0; q < 4; ++q) {
         A.grad0[12 * k + 3 * q + 0] = g0[q].x; A.grad0[12 * k + 3 * q + 1] = g0[q].y;
         A.grad0[12 * k + 3 * q + 2] = g0[q].z;
@@ -518,7 +525,8 @@ static int run_stiv(stiv_handle* h, void* stream, const int32_t* p_dev, const in
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (Vtmp || grad || grad0) {
     STIV_PROF(h, st, A.grad ? "stiv_grad" : (A.grad0 ? "stiv_grad_x0" : "stiv"));
-    stiv_kernel<<<dev_sms * 8, 128, 0, st>>>(A);
+    if (A.vabs || A.dm2 > 0.0 || A.grad0) stiv_kernel<true><<<dev_sms * 8, 128, 0, st>>>(A);
+    else stiv_kernel<false><<<dev_sms * 8, 128, 0, st>>>(A);
     STIV_LAUNCH(h);
   }
   if (Vp) {
