@@ -6,8 +6,9 @@
 // image) that has contacts; V its volume (the library's volumes are >= 0 for
 // interference, the paper's constraint V >= 0 has the opposite sign, which B
 // does not see).  J = dV/dX1 (the gradient rows of stiv_stiv_grad, summed
-// per vertex); M block-diagonal, one scalar m_i per vesicle (M_ii = m_i I), a
-// stand-in for the locally implicit scheme's A^-1 G.
+// per vertex); M block-diagonal, M_ii = m_i I + t_i (1 1^T (x) I_3) per
+// vesicle (a local part and a rigid translation), a stand-in with the block
+// structure of the locally implicit scheme's A^-1 G.
 //
 // Assembly (Alg. 3):
 //   bounds_kernel   contact range of every candidate pair (contacts are
