@@ -29,7 +29,10 @@ __device__ __forceinline__ double vload(const void* X, int mixed, size_t i) {
   return mixed ? (double)((const float*)X)[i] : ((const double*)X)[i];
 }
 
-// One CTA per vesicle.
+// One CTA per vesicle.  MIXED (FP32 vertices): the min / max run in FP32,
+// which is exact, and widen exactly to FP64, so the boxes are those of the
+// FP64 reduction bit for bit without its FP64 instructions.
+template <bool MIXED>
 __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, const int64_t* voff, const void* X,
                                                     int mixed, double dm, double Lx, double Ly, double Lz,
                                                     double* vbox, float* pbox, int pstride, float* vorg,
@@ -42,16 +45,31 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
   __shared__ double red[6][256];
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   bool bad = false;
-  for (int k = threadIdx.x; k < nv; k += blockDim.x)
-    for (int c = 0; c < 3; ++c) {
-      double x0 = vload(X, mixed, base + (size_t)c * nv + k);
-      double x1 = vload(X, mixed, base + (size_t)(3 + c) * nv + k);
-      if (!finite_d(x0) || !finite_d(x1)) bad = true;
-      double a = fmin(x0, x1), b = fmax(x0, x1);
-      lo[c] = fmin(lo[c], a);
-      hi[c] = fmax(hi[c], b);
-      if (use_sm) { vbs[c * nv + k] = __double2float_rd(a); vbs[(3 + c) * nv + k] = __double2float_ru(b); }
-    }
+  if (MIXED) {
+    const float* Xf = (const float*)X;
+    float flo[3] = {INFINITY, INFINITY, INFINITY}, fhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int k = threadIdx.x; k < nv; k += blockDim.x)
+      for (int c = 0; c < 3; ++c) {
+        float x0 = Xf[base + (size_t)c * nv + k], x1 = Xf[base + (size_t)(3 + c) * nv + k];
+        if (!isfinite(x0) || !isfinite(x1)) bad = true;
+        float a = fminf(x0, x1), b = fmaxf(x0, x1);
+        flo[c] = fminf(flo[c], a);
+        fhi[c] = fmaxf(fhi[c], b);
+        if (use_sm) { vbs[c * nv + k] = a; vbs[(3 + c) * nv + k] = b; }
+      }
+    for (int c = 0; c < 3; ++c) { lo[c] = (double)flo[c]; hi[c] = (double)fhi[c]; }
+  } else {
+    for (int k = threadIdx.x; k < nv; k += blockDim.x)
+      for (int c = 0; c < 3; ++c) {
+        double x0 = vload(X, mixed, base + (size_t)c * nv + k);
+        double x1 = vload(X, mixed, base + (size_t)(3 + c) * nv + k);
+        if (!finite_d(x0) || !finite_d(x1)) bad = true;
+        double a = fmin(x0, x1), b = fmax(x0, x1);
+        lo[c] = fmin(lo[c], a);
+        hi[c] = fmax(hi[c], b);
+        if (use_sm) { vbs[c * nv + k] = __double2float_rd(a); vbs[(3 + c) * nv + k] = __double2float_ru(b); }
+      }
+  }
   for (int c = 0; c < 3; ++c) { red[c][threadIdx.x] = lo[c]; red[3 + c][threadIdx.x] = hi[c]; }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_NONFINITE);
   for (int s = 128; s > 0; s >>= 1) {
@@ -375,8 +393,9 @@ int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, const int32_t* p_de
   size_t nv_max = (size_t)(w.fstride / 8);
   size_t vb_cap = 6 * nv_max * sizeof(float) <= 96 * 1024 ? 6 * nv_max : 0;
   size_t bsmem = vb_cap * sizeof(float);
-  STIV_CUDA(h, cudaFuncSetAttribute(boxes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
-  boxes_kernel<<<n, 256, bsmem, st>>>(n, p_dev, voff, X, mixed, h->prm.d_m, L[0], L[1], L[2], w.vbox, w.pbox,
+  auto bk = mixed ? boxes_kernel<true> : boxes_kernel<false>;
+  STIV_CUDA(h, cudaFuncSetAttribute(bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
+  bk<<<n, 256, bsmem, st>>>(n, p_dev, voff, X, mixed, h->prm.d_m, L[0], L[1], L[2], w.vbox, w.pbox,
                                       w.pstride, w.vorg, w.fprep, w.fstride, ctr, vb_cap);
   }
   {

@@ -776,6 +776,17 @@ __device__ int inside64(int kind, const d3* Y, double& w1, double& w2) {
   }
 }
 
+// The rounded quotient n / d when it may lie in (0, 1), else -1: it cannot
+// when n is zero, the signs differ, or |n| >= |d| (then n / d >= 1 exactly,
+// and so rounded); only the remaining case is divided (an exact quotient in
+// (0, 1) may still round to 0 or 1, which the division decides).  Zero or
+// NaN d falls in the |n| >= |d| or sign cases exactly as the quotient would
+// fall outside (0, 1).
+__device__ __forceinline__ double quot01(double n, double d) {
+  if (is_zero(n) || is_neg(n) != is_neg(d) || !(fabs(n) < fabs(d))) return -1.0;
+  return __ddiv_rn(n, d);
+}
+
 // 0 no contact, 1 contact, 2 degenerate.
 __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w1, double& w2, long long& flops) {
   flops += 18 + 9 + 21 + 9 + 32;  // differences, cross products (+ sum), 6 dot products + 2 sums
@@ -805,10 +816,10 @@ __device__ int ccd64(int kind, const d3* X0, const d3* D, double& tau, double& w
       flops += 5;
       double sq = __dsqrt_rn(disc);
       double q = __dmul_rn(-0.5, __dadd_rn(e1, !is_neg(e1) ? sq : -sq));
-      r[0] = __ddiv_rn(q, e2); r[1] = __ddiv_rn(e0, q); nr = 2;
+      r[0] = quot01(q, e2); r[1] = quot01(e0, q); nr = 2;
     }
   } else if (!is_zero(e1)) {
-    r[0] = __ddiv_rn(-e0, e1); nr = 1;
+    r[0] = quot01(-e0, e1); nr = 1;
     flops += 1;
   }
   double cp[2]; int ncp = 0;
