@@ -83,7 +83,9 @@ enum stiv_flag {
   STIV_F_BOX_TOO_SMALL = 4,      /* a vesicle box spans >= L/2 on a periodic axis */
   STIV_F_NONFINITE = 8,          /* a vertex coordinate is NaN or infinite      */
   STIV_F_WORK_OVERFLOW = 16,     /* internal work list overflow (re-run)         */
-  STIV_F_TIMEOUT = 32            /* a bounded device wait gave up (mixed-form synthesis) */
+  STIV_F_TIMEOUT = 32,           /* a bounded device wait gave up (mixed-form synthesis) */
+  STIV_F_BAD_ORDER = 64          /* a vesicle's p_dev entry lies outside [1, p_max]: that
+                                    vesicle is left out of synthesis, boxes and contacts */
 };
 
 typedef struct stiv_params {
@@ -153,7 +155,10 @@ int stiv_last_cuda_error(const stiv_handle* h);
 int stiv_mesh_topology(int32_t P, int32_t* tri_dev, int32_t* edge_dev, void* stream);
 
 /* Sec. 3.1.2 upsampling: evaluate each vesicle's order-p series for X0 and X1
- * on its order-2p mesh (grid and poles).  p_dev[v] in [1, p_max], p_max <= 32.
+ * on its order-2p mesh (grid and poles).  p_dev[v] in [1, p_max], p_max <= 32;
+ * a vesicle whose p_dev entry lies outside [1, p_max] is skipped (its vertices
+ * are not written; stiv_detect then flags it as STIV_F_BAD_ORDER and leaves it
+ * out of the boxes and contacts, stiv_mesh_fidelity reports NaN for it).
  * STIV_FP64: FP64 synthesis, doubles in verts_dev.  STIV_MIXED: the synthesis
  * runs on the tensor cores as one contraction per order with 3xTF32 split
  * products accumulated in FP32 (the degree-0 term added in the epilogue) and

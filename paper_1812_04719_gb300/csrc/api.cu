@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, const int32_t* p_dev, const int64_t* voff,
+int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, int p_max, const int32_t* p_dev, const int64_t* voff,
                      const void* X, const stiv_pairs* cand, detect_ws& w, int64_t* ctr);
 int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, const int64_t* voff, const void* X,
                       const stiv_pairs* cand, detect_ws& w, int num_sms, int p_max);
@@ -310,7 +310,7 @@ extern "C" int stiv_detect(stiv_handle* h, void* stream, int32_t n_ves, int32_t 
   STIV_CUDA(h, cudaMemsetAsync(w.pair_fill, 0, sizeof(int32_t) * (size_t)cand->capacity, st));
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-  rc = stiv_broad_phase(h, st, n_ves, p_dev, vert_off_dev, verts_dev, cand, w, w.ctr);
+  rc = stiv_broad_phase(h, st, n_ves, p_max, p_dev, vert_off_dev, verts_dev, cand, w, w.ctr);
   if (rc) return rc;
   rc = stiv_narrow_phase(h, st, p_dev, vert_off_dev, verts_dev, cand, w, sms, p_max);
   if (rc) return rc;
@@ -395,7 +395,7 @@ extern "C" int stiv_sync_counts(void* stream, const int64_t* counts_dev, int64_t
     return STIV_ERR_CUDA;
   int64_t f = counts_host[STIV_C_STATUS];
   if (f & (STIV_F_PAIRS_OVERFLOW | STIV_F_CONTACTS_OVERFLOW | STIV_F_WORK_OVERFLOW)) return STIV_ERR_CAPACITY;
-  if (f & (STIV_F_BOX_TOO_SMALL | STIV_F_NONFINITE)) return STIV_ERR_INPUT;
+  if (f & (STIV_F_BOX_TOO_SMALL | STIV_F_NONFINITE | STIV_F_BAD_ORDER)) return STIV_ERR_INPUT;
   if (f & STIV_F_TIMEOUT) return STIV_ERR_TIMEOUT;
   return STIV_OK;
 }

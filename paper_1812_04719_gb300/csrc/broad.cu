@@ -36,9 +36,22 @@ template <bool MIXED>
 __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, const int64_t* voff, const void* X,
                                                     int mixed, double dm, double Lx, double Ly, double Lz,
                                                     double* vbox, float* pbox, int pstride, float* vorg,
-                                                    float* fprep, int64_t fstride, int64_t* ctr, size_t vb_cap) {
+                                                    float* fprep, int64_t fstride, int64_t* ctr, size_t vb_cap,
+                                                    int p_max) {
   extern __shared__ float vbs[];   // [6][nv]: swept FP32 box of each vertex (rounded outward), if it fits
   int v = blockIdx.x;
+  if (pv[v] < 1 || pv[v] > p_max) {
+    // an order outside [1, p_max]: flagged, and an inverted box keeps the
+    // vesicle out of every cell (the broad phase skips inverted boxes), so no
+    // later kernel reads its mesh
+    if (threadIdx.x == 0) atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_BAD_ORDER);
+    if (threadIdx.x < 3) {
+      vbox[6 * v + threadIdx.x] = INFINITY;
+      vbox[6 * v + 3 + threadIdx.x] = -INFINITY;
+    }
+    if (threadIdx.x < 4) vorg[4 * v + threadIdx.x] = 0.0f;
+    return;
+  }
   int P = 2 * pv[v], nv = stiv_nverts(P);
   bool use_sm = (size_t)6 * nv <= vb_cap;
   const size_t base = voff[v];
@@ -180,18 +193,24 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
 __global__ void __launch_bounds__(1024) grid_kernel(int n, const double* vbox, double Lx, double Ly, double Lz,
                                                     double* grid) {
   __shared__ double sdiag[1024], slo[3][1024], shi[3][1024];
+  __shared__ int scnt[1024];
   double d = 0.0, lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int nvalid = 0;
   for (int v = threadIdx.x; v < n; v += 1024) {
+    if (!(vbox[6 * v] <= vbox[6 * v + 3])) continue;   // inverted: a vesicle left out (bad order)
+    ++nvalid;
     double e0 = vbox[6 * v + 3] - vbox[6 * v], e1 = vbox[6 * v + 4] - vbox[6 * v + 1], e2 = vbox[6 * v + 5] - vbox[6 * v + 2];
     d += sqrt(e0 * e0 + e1 * e1 + e2 * e2);
     for (int c = 0; c < 3; ++c) { lo[c] = fmin(lo[c], vbox[6 * v + c]); hi[c] = fmax(hi[c], vbox[6 * v + 3 + c]); }
   }
   sdiag[threadIdx.x] = d;
+  scnt[threadIdx.x] = nvalid;
   for (int c = 0; c < 3; ++c) { slo[c][threadIdx.x] = lo[c]; shi[c][threadIdx.x] = hi[c]; }
   __syncthreads();
   for (int s = 512; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
       sdiag[threadIdx.x] += sdiag[threadIdx.x + s];
+      scnt[threadIdx.x] += scnt[threadIdx.x + s];
       for (int c = 0; c < 3; ++c) {
         slo[c][threadIdx.x] = fmin(slo[c][threadIdx.x], slo[c][threadIdx.x + s]);
         shi[c][threadIdx.x] = fmax(shi[c][threadIdx.x], shi[c][threadIdx.x + s]);
@@ -200,8 +219,10 @@ __global__ void __launch_bounds__(1024) grid_kernel(int n, const double* vbox, d
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double hm = sdiag[0] / n;
+    double hm = sdiag[0] / (scnt[0] > 0 ? scnt[0] : 1);
     if (!(hm > 0.0)) hm = 1.0;
+    for (int c = 0; c < 3; ++c)
+      if (!(slo[c][0] <= shi[c][0])) { slo[c][0] = 0.0; shi[c][0] = 0.0; }   // no valid box
     double L[3] = {Lx, Ly, Lz};
     for (int c = 0; c < 3; ++c) {
       if (L[c] > 0.0) {
@@ -236,6 +257,7 @@ __device__ __forceinline__ void cell_range(const double* grid, const double* box
 __global__ void cell_count_kernel(int n, const double* vbox, const double* grid, int32_t* cnt) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
+  if (!(vbox[6 * v] <= vbox[6 * v + 3])) { cnt[v] = 0; return; }   // inverted box: no cells
   int c = 1;
   for (int a = 0; a < 3; ++a) { int u0, u1; cell_range(grid, vbox + 6 * v, a, u0, u1); c *= (u1 - u0 + 1); }
   cnt[v] = c;
@@ -278,6 +300,7 @@ __global__ void cell_emit_kernel(int n, const double* vbox, const double* grid, 
   for (int a = 0; a < 3; ++a) { cell_range(grid, vbox + 6 * v, a, lo[a], hi[a]); G[a] = (int)grid[6 + a]; }
   int64_t r = off[v];
   if (v == n - 1) ctr[8] = off[n];
+  if (!(vbox[6 * v] <= vbox[6 * v + 3])) return;   // inverted box: no cells
   for (int x = lo[0]; x <= hi[0]; ++x)
     for (int y = lo[1]; y <= hi[1]; ++y)
       for (int z = lo[2]; z <= hi[2]; ++z, ++r) {
@@ -383,7 +406,7 @@ __global__ void __launch_bounds__(1024) unique_pairs_kernel(const int64_t* nkey_
 }  // namespace
 
 // Host side of steps 1-6.  ws: scratch views prepared by the caller.
-int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, const int32_t* p_dev, const int64_t* voff,
+int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, int p_max, const int32_t* p_dev, const int64_t* voff,
                      const void* X, const stiv_pairs* cand, detect_ws& w, int64_t* ctr) {
   int mixed = h->prm.precision == STIV_MIXED;
   const double* L = h->prm.box_L;
@@ -396,7 +419,7 @@ int stiv_broad_phase(stiv_handle* h, cudaStream_t st, int n, const int32_t* p_de
   auto bk = mixed ? boxes_kernel<true> : boxes_kernel<false>;
   STIV_CUDA(h, cudaFuncSetAttribute(bk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsmem));
   bk<<<n, 256, bsmem, st>>>(n, p_dev, voff, X, mixed, h->prm.d_m, L[0], L[1], L[2], w.vbox, w.pbox,
-                                      w.pstride, w.vorg, w.fprep, w.fstride, ctr, vb_cap);
+                                      w.pstride, w.vorg, w.fprep, w.fstride, ctr, vb_cap, p_max);
   }
   {
   STIV_PROF_N(h, st, "cells", 4);

@@ -414,6 +414,7 @@ struct adj_args {
 __global__ void __launch_bounds__(256) adjoint_kernel(adj_args a) {
   extern __shared__ double sm[];
   int v = blockIdx.x;
+  if (a.p[v] < 1 || a.p[v] > STIV_MAX_P || !a.leg[a.p[v]]) return;   // order outside [1, p_max]: skipped
   int p = a.p[v], P = 2 * p, nc = (p + 1) * (p + 1), nl = (p + 1) * (p + 2) / 2, ns = 2 * p + 1, W = 2 * P;
   int nv = stiv_nverts(P);
   double* G = sm;                    // [n_v]       one field of gX (X1 block), staged coalesced

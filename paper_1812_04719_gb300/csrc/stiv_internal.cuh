@@ -9,6 +9,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/stiv.h"
 
@@ -59,8 +60,9 @@ struct stiv_handle {
   void* prof;
 };
 
-// Brackets the launches of one named stage with CUDA events on its stream
-// while the profiler is on (no-op otherwise).
+// Brackets the launches of one named stage: an NVTX range of that name on the
+// calling thread (always; without an attached tool a push/pop costs a few
+// nanoseconds), and CUDA events on its stream while the profiler is on.
 // nk = number of kernels the stage launches.
 void stiv_prof_begin(stiv_handle* h, cudaStream_t st, const char* name, int nk);
 void stiv_prof_end(stiv_handle* h, cudaStream_t st);
@@ -68,9 +70,13 @@ void stiv_prof_drop_graph(stiv_handle* h);
 struct stiv_prof_scope {
   stiv_handle* h; cudaStream_t st;
   stiv_prof_scope(stiv_handle* h_, cudaStream_t st_, const char* name, int nk) : h(h_), st(st_) {
+    nvtxRangePushA(name);
     stiv_prof_begin(h, st, name, nk);
   }
-  ~stiv_prof_scope() { stiv_prof_end(h, st); }
+  ~stiv_prof_scope() {
+    stiv_prof_end(h, st);
+    nvtxRangePop();
+  }
 };
 #define STIV_PROF_CAT2(a, b) a##b
 #define STIV_PROF_CAT(a, b) STIV_PROF_CAT2(a, b)

@@ -283,9 +283,9 @@ __global__ void gprep_kernel(int p_max, const tc_group* g, const int* list, cons
 }
 
 // X0 blocks of the coefficient gradient are zero (X0 is a constant of the step).
-__global__ void zero_x0_kernel(int n, const int32_t* pv, const int64_t* coef_off, double* gcoef) {
+__global__ void zero_x0_kernel(int n, int p_max, const int32_t* pv, const int64_t* coef_off, double* gcoef) {
   int v = blockIdx.x;
-  if (v >= n) return;
+  if (v >= n || pv[v] < 1 || pv[v] > p_max) return;   // order outside [1, p_max]: skipped
   int nc = (pv[v] + 1) * (pv[v] + 1);
   for (int k = threadIdx.x; k < 3 * nc; k += blockDim.x) gcoef[coef_off[v] + k] = 0.0;
 }
@@ -645,7 +645,7 @@ int stiv_grad_to_coef_tc(stiv_handle* h, cudaStream_t st, int32_t n_ves, int32_t
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   STIV_PROF_N(h, st, "grad_to_coef", 4);
-  zero_x0_kernel<<<n_ves, 256, 0, st>>>(n_ves, p_dev, coef_off_dev, gcoef_dev);
+  zero_x0_kernel<<<n_ves, 256, 0, st>>>(n_ves, p_max, p_dev, coef_off_dev, gcoef_dev);
   group_kernel<<<1, 1024, 0, st>>>(n_ves, p_max, p_dev, g, ntiles, list, 1);
   gprep_kernel<<<sms * 8, 256, 0, st>>>(p_max, g, list, coef_off_dev, vert_off_dev, gX_dev, bblk, ci);
   gemm_args A;

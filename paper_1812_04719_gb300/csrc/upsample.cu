@@ -93,6 +93,7 @@ struct synth_args {
 __global__ void __launch_bounds__(256) synth_kernel(synth_args a) {
   extern __shared__ double sm[];
   int v = blockIdx.x, t = blockIdx.y;
+  if (a.p[v] < 1 || a.p[v] > STIV_MAX_P || !a.leg[a.p[v]]) return;   // order outside [1, p_max]: skipped
   int p = a.p[v], P = 2 * p, nc = (p + 1) * (p + 1), nl = (p + 1) * (p + 2) / 2, ns = 2 * p + 1;
   int nv = 2 * P * (P + 1) + 2;
   double* C = sm;                        // [3][nc]
@@ -293,6 +294,10 @@ __global__ void __launch_bounds__(256) fidelity_kernel(fid_args a) {
   extern __shared__ double sm[];
   __shared__ double red[256 / 32];
   int v = blockIdx.x, t = blockIdx.y;
+  if (a.p[v] < 1 || a.p[v] > STIV_MAX_P || !a.theta[a.p[v]]) {   // order outside [1, p_max]: NaN
+    if (threadIdx.x == 0) a.err[2 * (size_t)v + t] = __longlong_as_double(0x7ff8000000000000LL);
+    return;
+  }
   int p = a.p[v], P = 2 * p, Pf = a.factor * P, W = 2 * P, nv = 2 * P * (P + 1) + 2;
   int nc = (p + 1) * (p + 1), nl = (p + 1) * (p + 2) / 2, ns = 2 * p + 1, nq = Pf / 2 + 1;
   int FR = fid_rings(p, a.factor);

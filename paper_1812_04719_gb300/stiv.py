@@ -30,6 +30,8 @@ STIV_VEL_RELATIVE, STIV_VEL_ABSOLUTE = 0, 1
 C_PAIRS, C_PRIM, C_VF, C_EE, C_CPAIRS, C_DEGEN, C_STATUS, C_PATCH, C_FLOPS, C_EXACT = range(10)
 NCOUNTS = 10
 F_PAIRS_OVERFLOW, F_CONTACTS_OVERFLOW, F_BOX_TOO_SMALL, F_NONFINITE, F_WORK_OVERFLOW, F_TIMEOUT = 1, 2, 4, 8, 16, 32
+F_BAD_ORDER = 64
+MAX_ORDER = 32   # largest SH order p the library accepts (mesh order 64)
 
 EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_error", "stiv_mesh_topology",
            "stiv_upsample", "stiv_detect", "stiv_stiv", "stiv_stiv_grad", "stiv_grad_scatter",
@@ -271,6 +273,9 @@ class DeviceScene:
     @staticmethod
     def from_scene(sc, precision=STIV_FP64, device="cuda") -> "DeviceScene":
         dt = torch.float32 if precision == STIV_MIXED else torch.float64
+        p = np.asarray(sc.p)
+        if p.size and (p.min() < 1 or p.max() > MAX_ORDER):
+            raise ValueError(f"SH orders must lie in [1, {MAX_ORDER}], got [{p.min()}, {p.max()}]")
         vo = sc.vert_off()
         return DeviceScene(
             n=sc.n, p_max=int(sc.p.max()),
