@@ -157,6 +157,23 @@ def synth_flops(p: int) -> int:
     return leg + four + poles
 
 
+def fid_flops(p: int, factor: int) -> int:
+    """FP64 flops of the mesh-fidelity estimate for one (vesicle, time), as
+    the kernel's loops run them (mul, add = 1, fma = 2), per fine ring:
+    the Legendre column recurrences (4 per (n, m)), the ring sums (an FMA
+    per coefficient and field), per longitude quadruple the odd and even
+    partial Fourier sums (2 FMAs per order m and field) and their 8
+    combinations per field, and per fine point the mesh's bilinear value,
+    the difference and the squared distance (9 per field, 1 for the
+    longitude fraction)."""
+    P = 2 * p
+    Pf = factor * P
+    nl = (p + 1) * (p + 2) // 2
+    nq = Pf // 2 + 1
+    per_ring = 4 * nl + 6 * (p + 1) ** 2 + nq * (12 * p + 24) + 2 * Pf * 28
+    return (Pf + 1) * per_ring
+
+
 def load_peaks():
     try:
         with open(MEASURED_PEAKS) as f:
@@ -533,10 +550,22 @@ def run_ours(args, rank, world, local):
             if k >= 1:
                 ms_a.append(ev[0].elapsed_time(ev[1])); ms_s.append(ev[1].elapsed_time(ev[2]))
         info = lcp.info.cpu().numpy()
+        cl = b.counts.cpu().numpy()
+        ncon, npair = int(cl[S.C_VF] + cl[S.C_EE]), int(cl[S.C_PAIRS])
+        # bytes the assembly must move at least: each contact's pair index,
+        # gradient rows and their vesicle and vertex ids read once, the
+        # candidate pairs and V per pair read once, B (CSR) and q written once
+        lbytes = 132.0 * ncon + 20.0 * npair + 12.0 * A["nnz"] + 16.0 * A["n"]
+        lach = lbytes / (float(np.mean(ms_a)) * 1e-3) / 1e9
         lcp_rec = {"rows": A["n"], "nnz": A["nnz"], "assemble_ms": float(np.mean(ms_a)),
                    "solve_ms": float(np.mean(ms_s)), "newton_steps": int(info[0]), "cg_steps": int(info[2]),
                    "max_abs_phi": float(info[1]), "status": int(info[3]),
-                   "M": "per vesicle I + (1/n_v) 1 1^T (x) I_3"}
+                   "M": "per vesicle I + (1/n_v) 1 1^T (x) I_3",
+                   "roofline_assembly": {"bound": "hbm", "achieved": lach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                         "frac": lach / peaks["hbm_gbs"], "traffic_algorithmic": lbytes,
+                                         "peak_source": peak_src,
+                                         "note": "Alg. 3 runs as a sort by (row, side, vertex) and segmented "
+                                                 "scans: launch- and latency-bound at this size"}}
 
     # mesh fidelity of the step's meshes (Sec. 3.1.2, Fig. 6): the distance
     # between each order-2p triangle mesh and its smooth order-p surface on
@@ -560,7 +589,12 @@ def run_ours(args, rank, world, local):
                 ms_f.append(e0.elapsed_time(e1))
         from paper_1812_04719_gb300 import scenegen as G
         e = err.cpu().numpy()
+        fwork = float(sum(2 * fid_flops(int(p), 4) for p in sc.p))
+        fach = fwork / (float(np.mean(ms_f)) * 1e-3) / 1e9
         fid_rec = {"factor": 4, "ms": float(np.mean(ms_f)), "max_err": float(e.max()),
+                   "roofline": {"bound": "alu", "kernel": "fidelity_kernel", "achieved": fach,
+                                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": fach / FP64_PEAK_GFLOPS,
+                                "work_per_launch": fwork, "peak_source": "FP64 1.25 TFLOP/s nominal"},
                    "median_err": float(np.median(e)), "max_err_over_R0": float(e.max() / G.R0_PAPER),
                    "points_per_launch": int(sum(2 * (4 * int(P) + 1) * 8 * int(P) for P in sc.P))}
 
@@ -576,7 +610,9 @@ def run_ours(args, rank, world, local):
         eng_dm = S.Stiv.for_scene(sc_dm, precision=prec, pair_cap=8192, contact_cap=1 << 20, device=dev)
         ds_dm = S.DeviceScene.from_scene(sc_dm, precision=prec, device=dev)
         eng_dm.step(ds_dm, grad=True)          # sizes the buffers
+        S.stiv_profile(eng_dm.h, True)
         ms_d = []
+        prof_d = {}
         for k in range(4):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
@@ -584,13 +620,25 @@ def run_ours(args, rank, world, local):
             rd = eng_dm.step(ds_dm, grad=True, use_graph=True, stream=stream)
             e1.record(stream)
             torch.cuda.synchronize(dev)
+            prof_k = S.stiv_profile_read(eng_dm.h)
             if k >= 1:
                 ms_d.append(e0.elapsed_time(e1))
+                for name, (n, ms) in prof_k.items():
+                    prof_d[name] = prof_d.get(name, 0.0) + ms / 3
         cdm = rd["counts"]
+        fp64_dm = prof_d.get("fp64", 0.0)
+        dm_roof = {"bound": "alu", "kernel": "fp64 (degree-six contact tests on the band filter's survivors)",
+                   "achieved": float(cdm[S.C_FLOPS]) / (fp64_dm * 1e-3) / 1e9 if fp64_dm > 0 else None,
+                   "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "work_per_launch": float(cdm[S.C_FLOPS]),
+                   "avg_launch_ms": fp64_dm, "work": "FP64 operations the kernel executed, counted by it"}
+        if dm_roof["achieved"] is not None:
+            dm_roof["frac"] = dm_roof["achieved"] / FP64_PEAK_GFLOPS
         dm_rec = {"d_m": dm_val, "ms_per_step": float(np.mean(ms_d)),
                   "value": sc.n * world / (float(np.mean(ms_d)) * 1e-3), "unit": UNIT,
                   "contacts": int(cdm[S.C_VF] + cdm[S.C_EE]), "contact_pairs": int(cdm[S.C_CPAIRS]),
-                  "prim_pairs_tested": int(cdm[S.C_PRIM]),
+                  "prim_pairs_tested": int(cdm[S.C_PRIM]), "prim_pairs_fp64": int(cdm[S.C_EXACT]),
+                  "stage_ms": {k: round(v, 4) for k, v in sorted(prof_d.items(), key=lambda x: -x[1])},
+                  "roofline_fp64_kernel": dm_roof,
                   "note": "the same step (upsample + detect + V + dV/dX1) with the degree-six test on the "
                           "primitive pairs of the widened box test that the certified FP32 band rejection keeps"}
         eng_dm.close()

@@ -869,20 +869,92 @@ __device__ __forceinline__ double horner_n(const double* c, int n, double t) {
   return r;
 }
 
-__device__ double bisect_n(const double* c, int n, double lo, double hi, double flo) {
+// The bisection of a degree-N polynomial c on [lo, hi] (0 <= lo < hi <= 1),
+// taking exactly the FP64 path of the plain procedure: every midpoint is the
+// FP64 midpoint, every sign the sign of the FP64 Horner value.  As in the
+// cubic's bisection, that sign is read from cheaper evaluations when their
+// error bounds prove it.  With S = sum |c_i| and S1 = sum i |c_i|:
+//  - FP32 Horner at the truncated midpoint: |f64(mid) - f32| <=
+//    gamma_2N(2^-24) S + 2^-24 S + gamma_2N(2^-53) S + 2^-23 S1 (Horner error
+//    bounds with room to spare, coefficient rounding, the FP64 value's own
+//    error, the midpoint's truncation times max |f'| on [0, 1]) <=
+//    (2N + 1.5) 2^-24 S + 1.25e-7 S1 for N <= 6;
+//  - double-float Horner: N multiply-add steps at <= 2^-44 relative each, the
+//    coefficients' and the midpoint's representation (2^-48 |c_i|, 2^-47 mid
+//    times max |f'|) and the FP64 Horner error (< 2^-50 S) stay below
+//    2^-40 (S + S1) for N <= 6.
+// Above its bound a tier's value has the sign of the FP64 value, which is
+// then not zero.  Coefficients outside [1e-25, 1e25] (1e-20 for the
+// double-float tier) keep every FP32 term clear of underflow and overflow;
+// outside that range only FP64 is used.
+template <int N>
+__device__ __noinline__ double bisect_tn(const double* c, double lo, double hi, double flo, long long& flops) {
+  bool neg_lo = is_neg(flo);
+  float fc[N + 1];
+  dflt cd[N + 1];
+  float S = 0.0f, S1 = 0.0f, mk = 0.0f;
+#pragma unroll
+  for (int i = 0; i <= N; ++i) {
+    fc[i] = __double2float_rn(c[i]);
+    float ai = fabsf(fc[i]);
+    S = S + ai;
+    S1 = S1 + (float)i * ai;
+    mk = fmaxf(mk, ai);
+    cd[i] = {fc[i], __double2float_rn(__dsub_rn(c[i], (double)fc[i]))};
+  }
+  float E = 1.01f * ((2.0f * N + 1.5f) * 5.9604645e-8f * S + 1.25e-7f * S1);
+  float Edf = 1.01f * 9.094947e-13f * (S + S1);   // 2^-40
+  bool use_df = mk > 1e-20f && mk < 1e25f;
+  if (!(mk > 1e-25f && mk < 1e25f)) E = INFINITY;
+#pragma unroll 1
   for (int it = 0; it < 64; ++it) {
-    double mid = __dmul_rn(__dadd_rn(lo, hi), 0.5);
-    if (!(mid > lo && mid < hi)) break;
-    double fm = horner_n(c, n, mid);
-    if (is_zero(fm)) return mid;
-    if (is_neg(fm) == is_neg(flo)) { lo = mid; flo = fm; }
+    bool ok;
+    double mid = mid_rn(lo, hi, ok);
+    if (!ok) mid = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+    long long bm = __double_as_longlong(mid);   // lo, mid, hi >= 0: bit patterns order them
+    if (!(bm > __double_as_longlong(lo) && bm < __double_as_longlong(hi))) break;
+    flops += 2 + 2 * N;
+    float m = trunc_f32(mid);
+    float fs = fc[N];
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) fs = fmaf(fs, m, fc[i]);
+    bool neg;
+    dflt md;
+    bool done = fabsf(fs) > E;
+    if (done) {
+      neg = fs < 0.0f;
+    } else if (use_df && df_of_unit(mid, md)) {
+      dflt v = cd[N];
+#pragma unroll
+      for (int i = N - 1; i >= 0; --i) v = df_add(df_mul(v, md), cd[i]);
+      float vv = v.h + v.l;
+      neg = vv < 0.0f;
+      done = fabsf(vv) > Edf;
+    }
+    if (!done) {
+      double fm = horner_n(c, N, mid);
+      if (is_zero(fm)) return mid;
+      neg = is_neg(fm);
+    }
+    if (neg == neg_lo) lo = mid;
     else hi = mid;
   }
   return lo;
 }
 
+__device__ __forceinline__ double bisect_n(const double* c, int n, double lo, double hi, double flo,
+                                           long long& flops) {
+  switch (n) {
+    case 2: return bisect_tn<2>(c, lo, hi, flo, flops);
+    case 3: return bisect_tn<3>(c, lo, hi, flo, flops);
+    case 4: return bisect_tn<4>(c, lo, hi, flo, flops);
+    case 5: return bisect_tn<5>(c, lo, hi, flo, flops);
+    default: return bisect_tn<6>(c, lo, hi, flo, flops);
+  }
+}
+
 __device__ __noinline__ int ccd64_dm(int kind, const d3* X0, const d3* D, double dm, double& tau, double& w1,
-                                     double& w2) {
+                                     double& w2, long long& flops) {
   d3 a, b, c, da, db, dc;
   if (kind == KIND_VF) {
     a = d3_sub(X0[2], X0[1]); b = d3_sub(X0[3], X0[1]); c = d3_sub(X0[0], X0[1]);
@@ -913,6 +985,8 @@ __device__ __noinline__ int ccd64_dm(int kind, const d3* X0, const d3* D, double
   C[0][4] = __dsub_rn(__dadd_rn(__dmul_rn(2.0, __dmul_rn(k1, k3)), __dmul_rn(k2, k2)), __dmul_rn(dd, q4));
   C[0][5] = __dmul_rn(2.0, __dmul_rn(k2, k3));
   C[0][6] = __dmul_rn(k3, k3);
+  // differences 18, normals 39, cubic 32, |m|^2 34, d_m^2 1, sextic 28, derivatives 20
+  flops += 18 + 39 + 32 + 34 + 1 + 28 + 20;
   bool allz = true;
   for (int i = 0; i <= 6; ++i) allz = allz && is_zero(C[0][i]);
   if (allz) return 2;
@@ -923,6 +997,7 @@ __device__ __noinline__ int ccd64_dm(int kind, const d3* X0, const d3* D, double
   int nr = 0;
   if (!is_zero(C[5][1])) {
     double t = __ddiv_rn(-C[5][0], C[5][1]);
+    flops += 1;
     if (t > 0.0 && t < 1.0) rts[nr++] = t;
   }
   for (int k = 4; k >= 1; --k) {
@@ -930,9 +1005,10 @@ __device__ __noinline__ int ccd64_dm(int kind, const d3* X0, const d3* D, double
     for (int sgi = 0; sgi <= nr; ++sgi) {
       double l = sgi == 0 ? 0.0 : rts[sgi - 1], r = sgi == nr ? 1.0 : rts[sgi];
       double fl = horner_n(C[k], n, l), fr = horner_n(C[k], n, r), t;
+      flops += 4 * n;
       if (is_zero(fl)) t = l;
       else if (is_zero(fr)) t = r;
-      else if (is_neg(fl) != is_neg(fr)) t = bisect_n(C[k], n, l, r, fl);
+      else if (is_neg(fl) != is_neg(fr)) t = bisect_n(C[k], n, l, r, fl, flops);
       else continue;
       if (t > 0.0 && t < 1.0 && (nn == 0 || t > nrt[nn - 1])) nrt[nn++] = t;
     }
@@ -943,15 +1019,18 @@ __device__ __noinline__ int ccd64_dm(int kind, const d3* X0, const d3* D, double
   for (int sgi = 0; sgi <= nr; ++sgi) {
     double l = sgi == 0 ? 0.0 : rts[sgi - 1], r = sgi == nr ? 1.0 : rts[sgi];
     double gl = horner_n(C[0], 6, l), gr = horner_n(C[0], 6, r), t;
+    flops += 24;
     if (sgi == 0 && (is_neg(gl) || is_zero(gl))) t = l;
     else if (is_zero(gl)) t = l;
     else if (is_zero(gr)) t = r;
-    else if (is_neg(gl) != is_neg(gr)) t = bisect_n(C[0], 6, l, r, gl);
+    else if (is_neg(gl) != is_neg(gr)) t = bisect_n(C[0], 6, l, r, gl, flops);
     else continue;
+    flops += 24 + 9 + 25 + 3;  // positions, differences, dot products, determinant
     d3 Y[4];
     for (int q = 0; q < 4; ++q) Y[q] = d3_at(X0[q], t, D[q]);
     double u1 = 0.0, u2 = 0.0;
     int in = inside64(kind, Y, u1, u2);
+    if (in >= 0) flops += kind == KIND_VF ? 10 : 8;  // numerators, divisions (and 1 - b1 - b2)
     if (in < 0) { degen = true; continue; }
     if (in == 1) { tau = t; w1 = u1; w2 = u2; return 1; }
   }
@@ -1376,7 +1455,7 @@ __global__ void __launch_bounds__(128) fp64_kernel(narrow_args a) {
         D[q] = {__dsub_rn(p1[0], p0[0]), __dsub_rn(p1[1], p0[1]), __dsub_rn(p1[2], p0[2])};
       }
       flops += 12;  // displacements
-      int st = DM ? ccd64_dm(ty == 2 ? KIND_EE : KIND_VF, X0, D, a.dm, tau, w1, w2)
+      int st = DM ? ccd64_dm(ty == 2 ? KIND_EE : KIND_VF, X0, D, a.dm, tau, w1, w2, flops)
                   : ccd64(ty == 2 ? KIND_EE : KIND_VF, X0, D, tau, w1, w2, flops);
       if (st == 1) {
         type = ty;

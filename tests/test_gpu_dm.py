@@ -83,4 +83,8 @@ def test_dm_band_filter_is_exact(precision):
     for c in (S.C_PAIRS, S.C_PRIM, S.C_VF, S.C_EE, S.C_CPAIRS, S.C_DEGEN):
         assert f["counts"][c] == x["counts"][c], c
     assert f["counts"][S.C_EXACT] < 0.2 * x["counts"][S.C_EXACT]
+    # the operation count: every pair that reaches the degree-six test costs at
+    # least its set-up (displacements 12, coefficients and derivatives 172)
+    for r in (f, x):
+        assert r["counts"][S.C_FLOPS] >= 184 * r["counts"][S.C_EXACT] > 0
     print(f"band filter: {f['counts'][S.C_EXACT]} of {x['counts'][S.C_EXACT]} pairs reach the FP64 test")
