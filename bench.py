@@ -161,16 +161,16 @@ def fid_flops(p: int, factor: int) -> int:
     """FP64 flops of the mesh-fidelity estimate for one (vesicle, time), as
     the kernel's loops run them (mul, add = 1, fma = 2), per fine ring:
     the Legendre column recurrences (4 per (n, m)), the ring sums (an FMA
-    per coefficient and field), per longitude quadruple the odd and even
-    partial Fourier sums (2 FMAs per order m and field) and their 8
-    combinations per field, and per fine point the mesh's bilinear value,
-    the difference and the squared distance (9 per field, 1 for the
-    longitude fraction)."""
+    per coefficient and field), the mesh's two lines per longitude cell and
+    field (8), per longitude quadruple the odd and even partial Fourier sums
+    (2 FMAs per order m and field) and their 8 combinations per field, and
+    per fine point the mesh value, the difference and the squared distance
+    (5 per field)."""
     P = 2 * p
     Pf = factor * P
     nl = (p + 1) * (p + 2) // 2
     nq = Pf // 2 + 1
-    per_ring = 4 * nl + 6 * (p + 1) ** 2 + nq * (12 * p + 24) + 2 * Pf * 28
+    per_ring = 4 * nl + 6 * (p + 1) ** 2 + 24 * 2 * P + nq * (12 * p + 24) + 2 * Pf * 15
     return (Pf + 1) * per_ring
 
 

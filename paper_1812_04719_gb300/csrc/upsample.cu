@@ -265,24 +265,34 @@ __host__ __device__ inline int fid_rings(int p, int factor) {
 __host__ __device__ inline size_t fid_smem_doubles(int p, int factor) {
   int P = 2 * p, Pf = factor * P, nl = (p + 1) * (p + 2) / 2, FR = fid_rings(p, factor);
   return (size_t)3 * (p + 1) * (p + 1) + (P + 1) + (Pf + 1) + (size_t)FR * nl + (size_t)FR * 3 * (2 * p + 1) +
-         (size_t)(Pf / 2 + 1) * 2 * (p + 1) + (Pf + 1) + 2 * (size_t)nl + 2 * (size_t)(p + 1);
+         (size_t)(Pf / 2 + 1) * 2 * (p + 1) + (Pf + 1) + 2 * (size_t)nl + 2 * (size_t)(p + 1) +
+         (size_t)FR * 3 * (2 * P) * 4;
 }
 
-// The mesh's value for coordinate field o at a fine point: ring zone / cell
-// (i, a_) or pole fraction tp; longitude cell j, j1 = j + 1 (mod 2P), b.
-__device__ __forceinline__ double mesh_value(const fid_args& a, size_t o, int P, int W, int zone, int i, double a_,
-                                             double tp, int j, int j1, double b) {
-  if (zone == 0) {
-    double N = vert_at(a, o + 2 * (size_t)P * (P + 1));
-    return N + tp * ((1.0 - b) * vert_at(a, o + j) + b * vert_at(a, o + j1) - N);
-  }
-  if (zone == 2) {
-    double S = vert_at(a, o + 2 * (size_t)P * (P + 1) + 1);
-    return S + tp * ((1.0 - b) * vert_at(a, o + (size_t)P * W + j) + b * vert_at(a, o + (size_t)P * W + j1) - S);
+// The mesh along one fine ring, per coordinate field and longitude cell j
+// (j1 = j + 1 mod 2P), as two lines in the cell fraction b:
+//   A + b dA on the triangle (i, j), (i+1, j), (i+1, j+1)  (taken when a_ >= b),
+//   B + b dB on the triangle (i, j), (i+1, j+1), (i, j+1)  (when a_ < b),
+// with a_ the ring's fraction between mesh rings i and i+1; in the pole caps
+// (zone 0 north, 2 south; tp the fraction from the pole to the first ring)
+// both lines are the fan triangle's.  out: A, dA, B, dB.
+__device__ __forceinline__ void mesh_lines(const fid_args& a, size_t o, int P, int W, int zone, int i, double a_,
+                                           double tp, int j, double* out) {
+  int j1 = j + 1 == W ? 0 : j + 1;
+  if (zone != 1) {
+    size_t pole = o + 2 * (size_t)P * (P + 1) + (zone == 2 ? 1 : 0);
+    size_t ring = o + (zone == 2 ? (size_t)P * W : 0);
+    double N = vert_at(a, pole), x0 = vert_at(a, ring + j), x1 = vert_at(a, ring + j1);
+    out[0] = out[2] = fma(tp, x0 - N, N);
+    out[1] = out[3] = tp * (x1 - x0);
+    return;
   }
   double q = vert_at(a, o + (size_t)i * W + j), rr = vert_at(a, o + (size_t)(i + 1) * W + j);
   double s3 = vert_at(a, o + (size_t)(i + 1) * W + j1), u = vert_at(a, o + (size_t)i * W + j1);
-  return a_ >= b ? q + a_ * (rr - q) + b * (s3 - rr) : q + b * (u - q) + a_ * (s3 - u);
+  out[0] = fma(a_, rr - q, q);
+  out[1] = s3 - rr;
+  out[2] = fma(a_, s3 - u, q);
+  out[3] = u - q;
 }
 
 // One CTA per (vesicle, time level), FR fine rings per pass.  The series is
@@ -312,6 +322,10 @@ __global__ void __launch_bounds__(256) fidelity_kernel(fid_args a) {
   double* rb = ra + nl;             // [nl]
   double* dg = rb + nl;             // [p+1]
   double* sd = dg + (p + 1);        // [p+1]
+  double* ML = sd + (p + 1);        // [FR][3][W][4] mesh lines of the current rings (mesh_lines)
+  __shared__ int rzone[FRMAX], rcell[FRMAX], rtri[FRMAX];   // per current ring: zone, cell, triangle mask
+  __shared__ double ra_[FRMAX], rtp[FRMAX], btab[8];
+  if (threadIdx.x < a.factor) btab[threadIdx.x] = (double)threadIdx.x / a.factor;
   const double* coef = a.coef + a.coef_off[v] + (size_t)t * 3 * nc;
   for (int k = threadIdx.x; k < 3 * nc; k += blockDim.x) C[k] = coef[k];
   for (int i = threadIdx.x; i <= P; i += blockDim.x) thc[i] = a.theta[p][i];
@@ -345,7 +359,7 @@ __global__ void __launch_bounds__(256) fidelity_kernel(fid_args a) {
   }
   __syncthreads();
   size_t base = a.vert_off[v] + (size_t)t * 3 * nv;
-  double worst2 = 0.0, inv_factor = 1.0 / a.factor;
+  double worst2 = 0.0;
   for (int r0 = 0; r0 <= Pf; r0 += FR) {
     int nr = Pf + 1 - r0 < FR ? Pf + 1 - r0 : FR;
     if (threadIdx.x < nr * (p + 1)) {
@@ -353,27 +367,40 @@ __global__ void __launch_bounds__(256) fidelity_kernel(fid_args a) {
       double x = xf[r0 + rr];
       legendre_column_tab(p, m, x, sqrt((1.0 - x) * (1.0 + x)), dg, sd, ra, rb, L + rr * nl);
     }
-    __syncthreads();
-    for (int task = threadIdx.x; task < nr * 3 * ns; task += blockDim.x) {
-      int rr = task / (3 * ns), rem = task % (3 * ns), f = rem / ns, sl = rem % ns, m = (sl + 1) >> 1;
-      int sgn = sl == 0 ? 0 : ((sl & 1) ? 1 : -1);
-      const double* Lr = L + rr * nl;
-      double acc = 0.0;
-      for (int n = m; n <= p; ++n) acc = fma(C[f * nc + n * n + n + sgn * m], Lr[n * (n + 1) / 2 + m], acc);
-      G[(rr * 3 + f) * ns + sl] = acc;
-    }
-    __syncthreads();
-    for (int task = threadIdx.x; task < nr * nq; task += blockDim.x) {
-      int rr = task / nq, q = task % nq;
+    if (threadIdx.x >= blockDim.x - nr) {   // where each ring lies on the mesh
+      int rr = threadIdx.x - (blockDim.x - nr);
       double theta = thf[r0 + rr];
       int zone = 1, i = 0;
-      double a_ = 0.0, tp = 0.0;
+      double al = 0.0, tp = 0.0;
       if (theta < thc[0]) { zone = 0; tp = theta / thc[0]; }
       else if (theta > thc[P]) { zone = 2; tp = (kPi - theta) / (kPi - thc[P]); }
       else {
         while (i + 1 < P && thc[i + 1] <= theta) ++i;
-        a_ = (theta - thc[i]) / (thc[i + 1] - thc[i]);
+        al = (theta - thc[i]) / (thc[i + 1] - thc[i]);
       }
+      int mask = 0;
+      for (int sb = 0; sb < a.factor; ++sb) mask |= (al >= (double)sb / a.factor) << sb;
+      rzone[rr] = zone; rcell[rr] = i; rtri[rr] = mask; ra_[rr] = al; rtp[rr] = tp;
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < nr * 3 * (ns + W); task += blockDim.x) {
+      if (task < nr * 3 * ns) {   // ring sums
+        int rr = task / (3 * ns), rem = task % (3 * ns), f = rem / ns, sl = rem % ns, m = (sl + 1) >> 1;
+        int sgn = sl == 0 ? 0 : ((sl & 1) ? 1 : -1);
+        const double* Lr = L + rr * nl;
+        double acc = 0.0;
+        for (int n = m; n <= p; ++n) acc = fma(C[f * nc + n * n + n + sgn * m], Lr[n * (n + 1) / 2 + m], acc);
+        G[(rr * 3 + f) * ns + sl] = acc;
+      } else {                    // mesh lines
+        int k2 = task - nr * 3 * ns, rr = k2 / (3 * W), rem = k2 % (3 * W), f = rem / W, j = rem % W;
+        mesh_lines(a, base + (size_t)f * nv, P, W, rzone[rr], rcell[rr], ra_[rr], rtp[rr], j,
+                   ML + ((size_t)(rr * 3 + f) * W + j) * 4);
+      }
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < nr * nq; task += blockDim.x) {
+      int rr = task / nq, q = task % nq;
+      int tri = rtri[rr];
       const double* cs = T + (size_t)q * 2 * (p + 1);
       const double* sn = cs + (p + 1);
       int kq[4] = {q, Pf - q, Pf + q, (2 * Pf - q) % (2 * Pf)};
@@ -395,13 +422,15 @@ __global__ void __launch_bounds__(256) fidelity_kernel(fid_args a) {
         bool dup = (w == 1 && k == kq[0]) || (w == 2 && (k == kq[1] || k >= 2 * Pf)) ||
                    (w == 3 && (k == kq[0] || k == kq[2]));
         if (dup) continue;
-        int j = k / a.factor, j1 = (j + 1) % W;
-        double b = (double)(k % a.factor) * inv_factor;
+        int j = k / a.factor, sb = k % a.factor;
+        double b = btab[sb];
+        int side = (tri >> sb) & 1 ? 0 : 2;
         double d2 = 0.0;
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-          double e = mesh_value(a, base + (size_t)f * nv, P, W, zone, i, a_, tp, j, j1, b) - val[w][f];
-          d2 += e * e;
+          const double* l = ML + ((size_t)(rr * 3 + f) * W + j) * 4 + side;
+          double e = fma(b, l[1], l[0]) - val[w][f];
+          d2 = fma(e, e, d2);
         }
         worst2 = fmax(worst2, d2);   // squared distance; one square root at the end
       }
