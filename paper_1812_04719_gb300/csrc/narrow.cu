@@ -229,6 +229,14 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
   }
 }
 
+// Order-preserving int image of a float (-0 just below +0) and its inverse:
+// the warp's integer min / max reductions then give the float min / max.
+__device__ __forceinline__ int fkey32(float f) {
+  int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float fkey_val(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7FFFFFFF); }
+
 // Stage the two patches of a patch pair (A: patch pa of vesicle i, unshifted;
 // B: patch pb of vesicle j at its periodic image), lanes over slots, both
 // patches' loads in flight together; patch boxes by warp reduction.
@@ -258,14 +266,11 @@ __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const 
                       a.dm, __double2float_ru(a.dm));
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      bA[c] = fminf(bA[c], __shfl_xor_sync(0xffffffffu, bA[c], off));
-      bA[3 + c] = fmaxf(bA[3 + c], __shfl_xor_sync(0xffffffffu, bA[3 + c], off));
-      bB[c] = fminf(bB[c], __shfl_xor_sync(0xffffffffu, bB[c], off));
-      bB[3 + c] = fmaxf(bB[3 + c], __shfl_xor_sync(0xffffffffu, bB[3 + c], off));
-    }
+  for (int c = 0; c < 3; ++c) {
+    bA[c] = fkey_val(__reduce_min_sync(0xffffffffu, fkey32(bA[c])));
+    bA[3 + c] = fkey_val(__reduce_max_sync(0xffffffffu, fkey32(bA[3 + c])));
+    bB[c] = fkey_val(__reduce_min_sync(0xffffffffu, fkey32(bB[c])));
+    bB[3 + c] = fkey_val(__reduce_max_sync(0xffffffffu, fkey32(bB[3 + c])));
   }
   if (lane < 6) { ws.A.box[lane] = bA[lane]; ws.B.box[lane] = bB[lane]; }
   if (lane == 0) {
@@ -321,8 +326,21 @@ __device__ __forceinline__ bool fbox_hit(const float* a, const float* b) {
 
 // Compact the primitives of S whose FP32 boxes overlap box ob; the boxes of
 // the kept vertices (and of the kept edges, if elo is given) are stored in
-// the compacted order for the stage-1 loops.
+// the compacted order for the stage-1 loops.  A primitive's box (the min and
+// max of its slots' boxes) misses ob on an axis exactly when all its slots
+// lie above ob there (every lo > ob's hi) or all below (every hi < ob's lo),
+// so the test reads per-slot bit masks instead of merging boxes.
 __device__ void filter_patch(PatchSm& S, const float* ob, int lane, float4* elo, float4* ehi) {
+  unsigned above[3], below[3];
+  {
+    bool in = lane < NS;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float lo = in ? S.lo[c][lane] : 0.0f, hi = in ? S.hi[c][lane] : 0.0f;
+      above[c] = __ballot_sync(0xffffffffu, in && lo > ob[3 + c]);
+      below[c] = __ballot_sync(0xffffffffu, in && hi < ob[c]);
+    }
+  }
 #pragma unroll 1
   for (int kind = 0; kind < 3; ++kind) {
     int n = kind == 0 ? S.nv : kind == 1 ? S.nt : S.ne;
@@ -331,19 +349,36 @@ __device__ void filter_patch(PatchSm& S, const float* ob, int lane, float4* elo,
     for (int k0 = 0; k0 < n; k0 += 32) {
       int k = k0 + lane;
       bool hit = false;
-      float b[6];
+      unsigned sm = 0;
       if (k < n) {
-        if (kind == 0) slot_box(S, S.tp->v_slot[k], b);
-        else if (kind == 1) tri_box(S, k, b);
-        else edge_box(S, k, b);
-        hit = fbox_hit(b, ob);
+        if (kind == 0) {
+          sm = 1u << S.tp->v_slot[k];
+        } else if (kind == 1) {
+          int t = S.tp->t_slots[k];
+          sm = (1u << (t & 63)) | (1u << ((t >> 6) & 63)) | (1u << ((t >> 12) & 63));
+        } else {
+          int e = S.tp->e_slots[k];
+          sm = (1u << (e & 63)) | (1u << ((e >> 6) & 63));
+        }
+        hit = (above[0] & sm) != sm && (below[0] & sm) != sm && (above[1] & sm) != sm && (below[1] & sm) != sm &&
+              (above[2] & sm) != sm && (below[2] & sm) != sm;
       }
       unsigned m = __ballot_sync(0xffffffffu, hit);
       if (hit) {
         int pos = base + __popc(m & ((1u << lane) - 1u));
         out[pos] = (unsigned char)k;
-        if (kind == 0) { S.vlo[pos] = make_float4(b[0], b[1], b[2], 0.f); S.vhi[pos] = make_float4(b[3], b[4], b[5], 0.f); }
-        if (kind == 2 && elo) { elo[pos] = make_float4(b[0], b[1], b[2], 0.f); ehi[pos] = make_float4(b[3], b[4], b[5], 0.f); }
+        if (kind == 0) {
+          float b[6];
+          slot_box(S, S.tp->v_slot[k], b);
+          S.vlo[pos] = make_float4(b[0], b[1], b[2], 0.f);
+          S.vhi[pos] = make_float4(b[3], b[4], b[5], 0.f);
+        }
+        if (kind == 2 && elo) {
+          float b[6];
+          edge_box(S, k, b);
+          elo[pos] = make_float4(b[0], b[1], b[2], 0.f);
+          ehi[pos] = make_float4(b[3], b[4], b[5], 0.f);
+        }
       }
       base += __popc(m);
     }
