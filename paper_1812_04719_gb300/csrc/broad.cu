@@ -113,9 +113,19 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
     for (int c = 0; c < 3; ++c) R = fmax(R, fmax(red[3 + c][0] - (double)sorg[c], (double)sorg[c] - red[c][0]));
     vorg[4 * v + 3] = __double2float_ru(R);
   }
-  // per-vertex FP32 data (two float4): position at t_n relative to the
-  // origin, displacement X1 - X0
+  // per-vertex FP32 data (two float4).  FP32 vertices: X0 and X1 as stored,
+  // from which the narrow phase takes both the exact keys and the frame
+  // coordinates.  FP64 vertices: position at t_n relative to the origin and
+  // the displacement X1 - X0, each rounded once.
   float4* f4 = (float4*)(fprep + (size_t)v * fstride);
+  if (MIXED) {
+    const float* Xf = (const float*)X;
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+      f4[2 * k] = make_float4(Xf[base + k], Xf[base + (size_t)nv + k], Xf[base + (size_t)2 * nv + k], 0.f);
+      f4[2 * k + 1] = make_float4(Xf[base + (size_t)3 * nv + k], Xf[base + (size_t)4 * nv + k],
+                                  Xf[base + (size_t)5 * nv + k], 0.f);
+    }
+  } else
   for (int k = threadIdx.x; k < nv; k += blockDim.x) {
     float xo[3], dd[3];
     for (int c = 0; c < 3; ++c) {

@@ -191,17 +191,30 @@ __device__ __forceinline__ int slot_vid(int k, int r0, int c0, int W, int P, boo
 template <bool MIXED, bool DM>
 __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int64_t base, const float* fp, int nv,
                                            int vid, int k, const int* s, const double* sh, const float* off, float dx,
-                                           float* b, double pad, float padf) {
+                                           float* b, double pad, float padf, const float* org) {
   int v = vid >= 0 ? vid : 0;
   S.vid[k] = vid;
   double x0[3], x1[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    x0[c] = vtx<MIXED>(a.X, (size_t)base + (size_t)c * nv + v);
-    x1[c] = vtx<MIXED>(a.X, (size_t)base + (size_t)(3 + c) * nv + v);
-  }
   float4 fx = ((const float4*)fp)[2 * v], fd = ((const float4*)fp)[2 * v + 1];
-  float xf[3] = {fx.x, fx.y, fx.z}, df[3] = {fd.x, fd.y, fd.z};
+  float xf[3], df[3];
+  if (MIXED) {   // the staging holds the FP32 vertices themselves
+    float f0[3] = {fx.x, fx.y, fx.z}, f1[3] = {fd.x, fd.y, fd.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x0[c] = (double)f0[c];
+      x1[c] = (double)f1[c];
+      xf[c] = f0[c] - org[c];   // one rounding, as the FP64 form's staging
+      df[c] = f1[c] - f0[c];
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      x0[c] = vtx<MIXED>(a.X, (size_t)base + (size_t)c * nv + v);
+      x1[c] = vtx<MIXED>(a.X, (size_t)base + (size_t)(3 + c) * nv + v);
+      xf[c] = c == 0 ? fx.x : c == 1 ? fx.y : fx.z;
+      df[c] = c == 0 ? fd.x : c == 1 ? fd.y : fd.z;
+    }
+  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     double p0 = x0[c], p1 = x1[c];
@@ -257,13 +270,19 @@ __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const 
   bool fA = IA == 0, lA = IA == stiv_nband_blocks(PA) - 1, fB = IB == 0, lB = IB == stiv_nband_blocks(PB) - 1;
   float bA[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
   float bB[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  float orgA[3] = {0.f, 0.f, 0.f}, orgB[3] = {0.f, 0.f, 0.f};
+  if (MIXED) {
+    float4 oa = ((const float4*)a.vorg)[vi], ob = ((const float4*)a.vorg)[vj];
+    orgA[0] = oa.x; orgA[1] = oa.y; orgA[2] = oa.z;
+    orgB[0] = ob.x; orgB[1] = ob.y; orgB[2] = ob.z;
+  }
   if (lane < NS) {
     int vidA = slot_vid(lane, IA * STIV_BR, JA * STIV_BC, WA, PA, fA, lA);
     int vidB = slot_vid(lane, IB * STIV_BR, JB * STIV_BC, WB, PB, fB, lB);
     stage_slot<MIXED, DM>(ws.A, a, pi.voff_i, a.fprep + (size_t)vi * a.fstride, nvA, vidA, lane, s0, sh0, offA, dx, bA,
-                      0.0, 0.0f);
+                          0.0, 0.0f, orgA);
     stage_slot<MIXED, DM>(ws.B, a, pi.voff_j, a.fprep + (size_t)vj * a.fstride, nvB, vidB, lane, s1, sh1, offB, dx, bB,
-                      a.dm, __double2float_ru(a.dm));
+                          a.dm, __double2float_ru(a.dm), orgB);
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -1127,8 +1146,14 @@ __device__ __forceinline__ void desc_points_f32(const narrow_args& a, ulonglong2
   ep = fr.w;
   kind = ty == 2 ? 1 : 0;
   for (int q = 0; q < 4; ++q) {
-    const float4* fp = (const float4*)(a.fprep + (size_t)(onj[q] ? vj : vi) * a.fstride) + 2 * (size_t)vid[q];
+    int v = onj[q] ? vj : vi;
+    const float4* fp = (const float4*)(a.fprep + (size_t)v * a.fstride) + 2 * (size_t)vid[q];
     float4 x = fp[0], d = fp[1];
+    if (a.mixed) {   // FP32 vertices as stored: relative position and displacement, one rounding each
+      float4 o = ((const float4*)a.vorg)[v];
+      d = make_float4(d.x - x.x, d.y - x.y, d.z - x.z, 0.f);
+      x = make_float4(x.x - o.x, x.y - o.y, x.z - o.z, 0.f);
+    }
     float o0 = onj[q] ? fr.x : 0.f, o1 = onj[q] ? fr.y : 0.f, o2 = onj[q] ? fr.z : 0.f;
     xq[q] = {x.x + o0, x.y + o1, x.z + o2};
     dq[q] = {d.x, d.y, d.z};

@@ -101,7 +101,8 @@ struct detect_ws {
   float* pbox;           // [N][pstride][6]
   int pstride;           // patches per vesicle at the largest order
   float* vorg;           // [N][4]  FP32 frame origin of each vesicle, and R = max |X - origin|
-  float* fprep;          // [N][fstride]  per vertex 8 floats: X0 - origin (xyz, 0), X1 - X0 (xyz, 0)
+  float* fprep;          // [N][fstride]  per vertex 8 floats: FP32 vertices X0 (xyz, 0), X1 (xyz, 0);
+                         // FP64 vertices X0 - origin (xyz, 0), X1 - X0 (xyz, 0), rounded to FP32
   int64_t fstride;
   double* grid;          // [16]  h, origin xyz, cell sizes, G
   int32_t* cell_count;   // [N+1]
