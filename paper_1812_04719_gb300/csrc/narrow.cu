@@ -184,6 +184,14 @@ __device__ __forceinline__ int slot_vid(int k, int r0, int c0, int W, int P, boo
   return last ? W * (P + 1) + 1 : -1;
 }
 
+// Order-preserving int image of a float (-0 just below +0) and its inverse:
+// the warp's integer min / max reductions then give the float min / max.
+__device__ __forceinline__ int fkey32(float f) {
+  int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float fkey_val(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7FFFFFFF); }
+
 // One vertex slot: exact FP64 swept-box keys, FP32 frame coordinates and the
 // slot's conservative FP32 swept box (also returned in b).  s: periodic image
 // of the vesicle (applied to both time levels in FP64, as the contact test
@@ -191,18 +199,16 @@ __device__ __forceinline__ int slot_vid(int k, int r0, int c0, int W, int P, boo
 template <bool MIXED, bool DM>
 __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int64_t base, const float* fp, int nv,
                                            int vid, int k, const int* s, const double* sh, const float* off, float dx,
-                                           float* b, double pad, float padf, const float* org) {
+                                           float* b, double pad, float padf, const float* org, bool f32keys) {
   int v = vid >= 0 ? vid : 0;
   S.vid[k] = vid;
   double x0[3], x1[3];
   float4 fx = ((const float4*)fp)[2 * v], fd = ((const float4*)fp)[2 * v + 1];
   float xf[3], df[3];
+  float f0[3] = {fx.x, fx.y, fx.z}, f1[3] = {fd.x, fd.y, fd.z};
   if (MIXED) {   // the staging holds the FP32 vertices themselves
-    float f0[3] = {fx.x, fx.y, fx.z}, f1[3] = {fd.x, fd.y, fd.z};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      x0[c] = (double)f0[c];
-      x1[c] = (double)f1[c];
       xf[c] = f0[c] - org[c];   // one rounding, as the FP64 form's staging
       df[c] = f1[c] - f0[c];
     }
@@ -217,7 +223,14 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    double p0 = x0[c], p1 = x1[c];
+    if (MIXED && f32keys) {
+      // FP32 vertices, no periodic image and no widening on either side: the
+      // exact box ends are FP32 values, ordered by their int images (the
+      // FP64 keys order the same values the same way)
+      S.key[c][k] = fkey32(fminf(f0[c], f1[c]));
+      S.key[3 + c][k] = fkey32(fmaxf(f0[c], f1[c]));
+    } else {
+    double p0 = MIXED ? (double)f0[c] : x0[c], p1 = MIXED ? (double)f1[c] : x1[c];
     if (s[c] != 0) { p0 = p0 + sh[c]; p1 = p1 + sh[c]; }
     long long k0 = dkey(p0), k1 = dkey(p1);
     if (DM && pad > 0.0) {   // d_m > 0: this side's boxes widened by d_m (FP64, as computed)
@@ -227,6 +240,7 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
     } else {
       S.key[c][k] = k0 < k1 ? k0 : k1;
       S.key[3 + c][k] = k0 < k1 ? k1 : k0;
+    }
     }
     float x = xf[c] + off[c], d = df[c];
     S.x[c][k] = x;
@@ -241,14 +255,6 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
     b[3 + c] = hi;
   }
 }
-
-// Order-preserving int image of a float (-0 just below +0) and its inverse:
-// the warp's integer min / max reductions then give the float min / max.
-__device__ __forceinline__ int fkey32(float f) {
-  int i = __float_as_int(f);
-  return i >= 0 ? i : i ^ 0x7FFFFFFF;
-}
-__device__ __forceinline__ float fkey_val(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7FFFFFFF); }
 
 // Stage the two patches of a patch pair (A: patch pa of vesicle i, unshifted;
 // B: patch pb of vesicle j at its periodic image), lanes over slots, both
@@ -271,6 +277,7 @@ __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const 
   float bA[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
   float bB[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
   float orgA[3] = {0.f, 0.f, 0.f}, orgB[3] = {0.f, 0.f, 0.f};
+  bool f32keys = MIXED && !DM && code == 13;   // both patches in one key space: unshifted, unwidened
   if (MIXED) {
     float4 oa = ((const float4*)a.vorg)[vi], ob = ((const float4*)a.vorg)[vj];
     orgA[0] = oa.x; orgA[1] = oa.y; orgA[2] = oa.z;
@@ -280,9 +287,9 @@ __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const 
     int vidA = slot_vid(lane, IA * STIV_BR, JA * STIV_BC, WA, PA, fA, lA);
     int vidB = slot_vid(lane, IB * STIV_BR, JB * STIV_BC, WB, PB, fB, lB);
     stage_slot<MIXED, DM>(ws.A, a, pi.voff_i, a.fprep + (size_t)vi * a.fstride, nvA, vidA, lane, s0, sh0, offA, dx, bA,
-                          0.0, 0.0f, orgA);
+                          0.0, 0.0f, orgA, f32keys);
     stage_slot<MIXED, DM>(ws.B, a, pi.voff_j, a.fprep + (size_t)vj * a.fstride, nvB, vidB, lane, s1, sh1, offB, dx, bB,
-                          a.dm, __double2float_ru(a.dm), orgB);
+                          a.dm, __double2float_ru(a.dm), orgB, f32keys);
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
