@@ -1434,7 +1434,9 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
 #pragma unroll 1
       for (int t0 = 0; t0 < total; t0 += 32) {
         int t = t0 + lane;
-        if (t < total) {
+        // a descriptor already bound for the FP64 test needs none of its
+        // other pieces decided
+        if (t < total && !W.fail[cur[t] >> 10]) {
           int owner = cur[t] >> 10, idx = cur[t] & 1023;
           float tl = idx * w;
           bool may_root = true;
