@@ -44,9 +44,9 @@ NARROW_STAGES = ("patch_pairs", "narrow", "pieces", "fp64")
 # is scaled to a launch by the pairs the launch processes.  The figure belongs
 # to the kernels as captured: if csrc/narrow.cu differs from the captured
 # source (its SHA-256 prefix below), the traffic is reported as null.
-NARROW_TRAFFIC_BYTES_144 = 34450688.0
+NARROW_TRAFFIC_BYTES_144 = 34397184.0
 NARROW_TRAFFIC_PAIRS_144 = 1877492.0
-NARROW_TRAFFIC_SRC_SHA256 = "fe189a2e8b75c0fc"
+NARROW_TRAFFIC_SRC_SHA256 = "11cff625e6f52182"
 METRIC = "vesicle-steps/s of detect+V+∇V at p=16→32, 58% vf; % of roofline vs FP64 form"
 UNIT = "vesicle-steps/s"
 
