@@ -70,10 +70,11 @@ __device__ double stiv_one(const contact_in& c, double e2, int vabs, double dm2,
     d3 Dr = vabs ? D[0] : D[0] - (b0 * D[1] + b1 * D[2] + b2 * D[3]);
     double dm = dot(Dr, m);
     double Q = e2 * dot(m, m) + dm * dm;
-    double S = sqrt(Q);
+    double rS = rsqrt(Q);                  // 1 / sqrt(Q): no division in the adjoint below
+    double S = Q > 0.0 ? Q * rS : 0.0;
     V = 0.5 * (1.0 - tau) * S;
     if (!g && !g0) return V;
-    double Qb = 0.5 * (1.0 - tau) / (2.0 * S);
+    double Qb = 0.25 * (1.0 - tau) * rS;   // dV/dQ
     d3 mb = (2.0 * Qb) * (e2 * m + dm * Dr);
     d3 Drb = (2.0 * Qb * dm) * m;
     taub = -0.5 * S;
@@ -115,10 +116,11 @@ __device__ double stiv_one(const contact_in& c, double e2, int vabs, double dm2,
     d3 Dr = vabs ? Dp : ((1.0 - u) * D[2] + u * D[3]) - Dp;
     double dm = dot(Dr, m);
     double Q = e2 * dot(m, m) + dm * dm;
-    double S = sqrt(Q);
+    double rS = rsqrt(Q);                  // 1 / sqrt(Q): no division in the adjoint below
+    double S = Q > 0.0 ? Q * rS : 0.0;
     V = 0.5 * (1.0 - tau) * S;
     if (!g && !g0) return V;
-    double Qb = 0.5 * (1.0 - tau) / (2.0 * S);
+    double Qb = 0.25 * (1.0 - tau) * rS;   // dV/dQ
     d3 mb = (2.0 * Qb) * (e2 * m + dm * Dr);
     d3 Drb = (2.0 * Qb * dm) * m;
     taub = -0.5 * S;
