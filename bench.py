@@ -200,20 +200,21 @@ class OracleScene:
         boxes = np.stack([O.vesicle_box(X, sc.d_m) for X in self.X])
         self.pairs = O.candidate_pairs(boxes, sc.L)
 
-    def sample(self, n_s: int, seed: int):
+    def sample(self, n_s: int, seed: int, threads: int = 0):
         """Time the oracle on n_s random vesicles: their SH synthesis plus every
         candidate pair they own (pair (i, j), i < j, is owned by i), i.e. the
         vertex-triangle and edge-edge tests, V and dV/dX1 of those pairs.
         Summed over all vesicles this is exactly one step of the scene."""
         from concurrent.futures import ThreadPoolExecutor
         O, sc = self.O, self.sc
+        threads = threads or self.threads
         rng = np.random.default_rng(seed)
         S = np.sort(rng.choice(sc.n, size=min(n_s, sc.n), replace=False))
         own = self.pairs[np.isin(self.pairs[:, 0], S)]
         t0 = time.perf_counter()
-        with ThreadPoolExecutor(self.threads) as ex:
+        with ThreadPoolExecutor(threads) as ex:
             list(ex.map(lambda v: O.synth_vesicle(int(sc.p[v]), int(sc.P[v]), sc.coef_of(v)), S.tolist()))
-        O.contacts(sc.P, self.X, own, sc.L, sc.eps * sc.dt, nthreads=self.threads)
+        O.contacts(sc.P, self.X, own, sc.L, sc.eps * sc.dt, nthreads=threads)
         secs = time.perf_counter() - t0
         desc = (f"{len(S)} random vesicles of the {sc.n}-vesicle scene: oracle SH synthesis of X0/X1 plus "
                 f"the {len(own)} candidate pairs they own (vertex-triangle and edge-edge tests, V, dV/dX1)")
@@ -226,11 +227,15 @@ class OracleScene:
 
 def oracle_sample(sc, target_s: float, rng_seed: int = 0):
     """(vesicles, seconds, threads, description) of one timed oracle sample of
-    about target_s seconds."""
+    about target_s seconds on all host cores, and (vesicles, seconds,
+    description) of a smaller one on a single core."""
     osc = OracleScene(sc)
     n_s = osc.sized(target_s, rng_seed)
     nv, secs, desc = osc.sample(n_s, rng_seed + 1)
-    return nv, secs, osc.threads, desc
+    # one core: about a third of the budget, scaled from the all-core rate
+    n_1 = int(max(2, min(sc.n, (target_s / 3) * nv / secs / max(osc.threads, 1))))
+    nv1, secs1, desc1 = osc.sample(n_1, rng_seed + 2, threads=1)
+    return nv, secs, osc.threads, desc, (nv1, secs1, desc1)
 
 
 def make_scene(args, seed):
@@ -645,8 +650,9 @@ def run_ours(args, rank, world, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        nv, secs, threads, desc = oracle_sample(sc, args.cpu_seconds)
-        cpu = {"value": nv / secs, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc}
+        nv, secs, threads, desc, one = oracle_sample(sc, args.cpu_seconds)
+        cpu = {"value": nv / secs, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+               "single_core": {"value": one[0] / one[1], "unit": UNIT, "cores": 1, "sample": one[2]}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
