@@ -51,3 +51,16 @@ def test_dist_env_defaults(monkeypatch):
     assert bench.dist_env() == (0, 1, 0)
     monkeypatch.setenv("RANK", "1"); monkeypatch.setenv("WORLD_SIZE", "2"); monkeypatch.setenv("LOCAL_RANK", "1")
     assert bench.dist_env() == (1, 2, 1)
+
+
+def test_oracle_baseline_sample():
+    """The CPU baseline's samples (all host cores and one core): bounded, the
+    vesicles they report timed, and the one-core rate the slower."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1812_04719_gb300 import scenegen as G
+    sc = G.scene_small((2, 2, 1), p=4, seed=3)
+    nv, secs, threads, desc, one = bench.oracle_sample(sc, 0.5)
+    assert 1 <= nv <= sc.n and secs > 0 and threads >= 1 and "random vesicles" in desc
+    nv1, secs1, desc1 = one
+    assert 1 <= nv1 <= sc.n and secs1 > 0 and "random vesicles" in desc1
