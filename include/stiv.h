@@ -363,6 +363,18 @@ int stiv_set_tuning(stiv_handle* h, const int32_t* values);
  * usable.  STIV_ERR_ARG for a limit out of range. */
 int stiv_wait_selftest(void* stream, int64_t limit_cycles, int32_t* status_dev);
 
+/* Arithmetic-rate probe (not a step of the method; the paper has no
+ * counterpart): the measured denominator of the FP64 and FP32 rooflines that
+ * the benchmark reports.  Launches, on the current device, 8 blocks of 256
+ * threads per SM; each thread runs 8 independent fused multiply-add chains of
+ * `iters` steps in FP64 (kind 0) or FP32 (kind 1).  *flops_out (host) is set
+ * to the operations the launch performs, 2 * 8 * iters * threads; time the
+ * launch with events on `stream` to get the rate.  sink_dev: one device
+ * double the kernel may write (it never does for the built-in constants; the
+ * write only keeps the chains alive).  STIV_ERR_ARG for kind outside {0, 1},
+ * iters outside [1, 2^32] or a null pointer. */
+int stiv_peak_probe(void* stream, int32_t kind, int64_t iters, double* sink_dev, double* flops_out);
+
 /* Stable LSD radix sort of (key, value) pairs on the low key_bits bits of the
  * 64-bit keys (Alg. 1's check-point sort, on one GPU).  scratch:
  * at least stiv_sort_scratch_bytes(n) bytes of device memory. */
@@ -383,8 +395,9 @@ int stiv_sort_pairs(void* stream, int64_t n, int32_t key_bits, const uint64_t* k
  *   - n <= STIV_SORT_STATIC_MAX, else STIV_ERR_ARG (nothing is launched);
  *   - keys_in/vals_in are left intact; keys_out/vals_out receive the result;
  *   - calls no cudaMalloc, cudaFree or allocating library routine;
- *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
+ *   - every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress); the first call on a device also makes the
+ *     runtime load the library's device code there, so make that first call
  *     before any stream capture on the device;
  *   - all calls on a device share the one array, which keeps the previous
  *     call's contents: calls that overlap on the GPU (different streams, or

@@ -16,8 +16,6 @@
 // start at zero.
 #include "stiv_internal.cuh"
 
-#include <mutex>
-
 namespace {
 
 constexpr int64_t kMaxPairs = STIV_SORT_STATIC_MAX;
@@ -30,22 +28,15 @@ constexpr size_t kScratchBytes = kHistBytes + kKeyBytes + kValBytes;  // 13.6 MB
 // device address comes from cudaGetSymbolAddress (below).
 static __device__ __align__(256) unsigned char g_sort_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 128;
-std::mutex g_mu;
-unsigned char* g_addr[kMaxDevices] = {};
-
-// Device address of g_sort_scratch on the current device, looked up once per
-// device (the first call on a device does this set-up).
+// Device address of g_sort_scratch on the current device, looked up on every
+// call with that device current.  The lookup is a host-side table read once
+// the library's device code is loaded on the device; the first call on a
+// device is the one that loads it.  Not caching the address keeps it valid
+// across a device reset or a new context, where the array may move.
 int scratch_address(unsigned char** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return STIV_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return STIV_ERR_CUDA;
-    g_addr[dev] = (unsigned char*)p;
-  }
-  *out = g_addr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_sort_scratch) != cudaSuccess || !p) return STIV_ERR_CUDA;
+  *out = (unsigned char*)p;
   return STIV_OK;
 }
 

@@ -52,6 +52,34 @@ def test_static_sort_matches_scratch_sort_twice():
         assert np.array_equal(vo_s.cpu().numpy(), order.astype(np.int32))
 
 
+def test_static_sort_allocates_nothing():
+    """After a first call (which loads the library's device code on the
+    device), a call leaves the device's free memory and torch's allocator
+    statistics unchanged: nothing is allocated or freed."""
+    from paper_1812_04719_gb300 import stiv as S
+    rng = np.random.default_rng(7)
+    n = 200_003
+    keys = torch.from_numpy(rng.integers(0, 1 << 40, size=n, dtype=np.int64)).cuda()
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    ko = torch.empty_like(keys)
+    vo = torch.empty_like(vals)
+    st = torch.cuda.current_stream().cuda_stream
+    S.stiv_sort_pairs_static(st, n, 40, keys.data_ptr(), vals.data_ptr(), ko.data_ptr(), vo.data_ptr())
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    S.stiv_sort_pairs_static(st, n, 40, keys.data_ptr(), vals.data_ptr(), ko.data_ptr(), vo.data_ptr())
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    for k in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current",
+              "allocated_bytes.all.current"):
+        assert stats1.get(k, 0) == stats0.get(k, 0), k
+    order = np.argsort(keys.cpu().numpy(), kind="stable")
+    assert np.array_equal(vo.cpu().numpy(), order.astype(np.int32))
+
+
 def test_static_sort_rejects_oversize():
     from paper_1812_04719_gb300 import stiv as S
     n = S.SORT_STATIC_MAX + 1
