@@ -52,6 +52,7 @@ constexpr int BLK_FLOATS = 8 * TM * 4;  // one hi or lo block: 4096 floats = 16 
 constexpr int BLK_BYTES = 2 * BLK_FLOATS * 4;  // hi + lo = 32 KB
 constexpr int STAGE_BYTES = 2 * BLK_BYTES;     // A + B
 constexpr long long WAIT_CYCLES = 2000000000LL; // bound of every mbarrier wait (SM clocks)
+constexpr long long DRAIN_CYCLES = 200000000LL;  // bound of the final drains (about 0.1 s)
 constexpr double Y00 = 0.28209479177387814347;  // 1 / sqrt(4 pi)
 
 __host__ __device__ inline int tc_mtiles(int p) { return (stiv_nverts(2 * p) + TM - 1) / TM; }
@@ -403,8 +404,8 @@ template <typename OUT>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(gemm_args a) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   __shared__ tc_group G[STIV_MAX_P + 1];
-  // full[NSTAGE], empty[NSTAGE], acc_full[NACC], acc_empty[NACC]
-  __shared__ __align__(8) unsigned long long bars[2 * NSTAGE + 2 * NACC];
+  // full[NSTAGE], empty[NSTAGE], acc_full[NACC], acc_empty[NACC], drain
+  __shared__ __align__(8) unsigned long long bars[2 * NSTAGE + 2 * NACC + 1];
   __shared__ unsigned tmem_base;
   int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char* sm = (unsigned char*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
@@ -415,6 +416,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(gemm_args a) {
       mbar_init(smem_u32(&bars[2 * NSTAGE + b]), 1);
       mbar_init(smem_u32(&bars[2 * NSTAGE + NACC + b]), 4);   // one arrival per epilogue warp
     }
+    mbar_init(smem_u32(&bars[2 * NSTAGE + 2 * NACC]), 1);     // the MMA warp's final drain
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -431,6 +433,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(gemm_args a) {
   auto empty = [&](int s) { return smem_u32(&bars[NSTAGE + s]); };
   auto acc_full = [&](int b) { return smem_u32(&bars[2 * NSTAGE + b]); };
   auto acc_empty = [&](int b) { return smem_u32(&bars[2 * NSTAGE + NACC + b]); };
+  const unsigned drain = smem_u32(&bars[2 * NSTAGE + 2 * NACC]);
   int ntiles = *a.ntiles;
   bool ok = true;
   if (warp == 0) {
@@ -454,6 +457,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(gemm_args a) {
           bulk_g2s(smem_u32(dst + BLK_BYTES), bsrc + (size_t)kb * BLK_BYTES, BLK_BYTES, full(s));
         }
       }
+      // before the shared memory is left: the copies of the last stages
+      // issued have landed (already true unless another warp gave up early;
+      // the wait is bounded either way)
+      for (unsigned k = it > NSTAGE ? it - NSTAGE : 0; k < it; ++k)
+        if (!mbar_wait(full(k % NSTAGE), (k / NSTAGE) & 1, DRAIN_CYCLES)) ok = false;
     }
   } else if (warp == 1) {
     // MMA issuer: one lane; accumulator b = (tile count) % NACC
@@ -487,6 +495,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_kernel(gemm_args a) {
         }
         if (!ok) break;
         mma_commit(acc_full(b));     // accumulator b holds the finished tile
+      }
+      // before TMEM is freed: every MMA this thread issued has completed
+      // (a gave-up wait above may have left some in flight)
+      if (it > 0) {
+        mma_commit(drain);
+        if (!mbar_wait(drain, 0, DRAIN_CYCLES)) ok = false;
       }
     }
   } else {
