@@ -256,47 +256,78 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
   }
 }
 
+// Lane -> slot of the packed staging and culling: lanes 0-14 hold the 15 grid
+// slots of patch A, lanes 15-29 those of patch B, lane 30 A's pole slot and
+// lane 31 B's (a patch touches at most one pole, except at P = 2, where the
+// south-pole slots of a patch that has both take a second pass).  Returns
+// the slot (-1: none) and whether it belongs to B.
+__device__ __forceinline__ int packed_slot(int lane, bool fA, bool lA, bool fB, bool lB, bool& onB) {
+  if (lane < 30) {
+    onB = lane >= 15;
+    return onB ? lane - 15 : lane;
+  }
+  onB = lane == 31;
+  bool f = onB ? fB : fA, l = onB ? lB : lA;
+  return f ? SN : (l ? SS : -1);
+}
+
 // Stage the two patches of a patch pair (A: patch pa of vesicle i, unshifted;
-// B: patch pb of vesicle j at its periodic image), lanes over slots, both
-// patches' loads in flight together; patch boxes by warp reduction.
+// B: patch pb of vesicle j at its periodic image) in one pass over the lanes
+// (packed_slot), both patches' loads in flight together; patch boxes by warp
+// reduction.
 template <bool MIXED, bool DM>
 __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const PatchTopo* topo,
                                         const stiv_pair_info& pi, int pa, int pb, int lane) {
   int vi = pi.vi, vj = pi.vj, code = pi.code;
-  int s0[3] = {0, 0, 0};
   int s1[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
-  double sh0[3] = {0.0, 0.0, 0.0};
-  double sh1[3] = {s1[0] * a.L[0], s1[1] * a.L[1], s1[2] * a.L[2]};
-  float offA[3] = {0.f, 0.f, 0.f}, offB[3] = {pi.frame.x, pi.frame.y, pi.frame.z};
   float dx = pi.frame.w;
   int PA = pi.Pij & 0xFFFF, PB = pi.Pij >> 16;
-  int WA = 2 * PA, WB = 2 * PB, nvA = stiv_nverts(PA), nvB = stiv_nverts(PB);
   int nbcA = stiv_ncol_blocks(PA), nbcB = stiv_ncol_blocks(PB);
   int IA = pa / nbcA, JA = pa % nbcA, IB = pb / nbcB, JB = pb % nbcB;
   bool fA = IA == 0, lA = IA == stiv_nband_blocks(PA) - 1, fB = IB == 0, lB = IB == stiv_nband_blocks(PB) - 1;
-  float bA[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-  float bB[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-  float orgA[3] = {0.f, 0.f, 0.f}, orgB[3] = {0.f, 0.f, 0.f};
   bool f32keys = MIXED && !DM && code == 13;   // both patches in one key space: unshifted, unwidened
-  if (MIXED) {
-    float4 oa = ((const float4*)a.vorg)[vi], ob = ((const float4*)a.vorg)[vj];
-    orgA[0] = oa.x; orgA[1] = oa.y; orgA[2] = oa.z;
-    orgB[0] = ob.x; orgB[1] = ob.y; orgB[2] = ob.z;
+  // this lane's side: shift, frame offset, widening and origin of its vesicle
+  auto stage_one = [&](bool onB, int k, float* b) {
+    int P = onB ? PB : PA, I = onB ? IB : IA, J = onB ? JB : JA;
+    int v = onB ? vj : vi;
+    int sh[3] = {onB ? s1[0] : 0, onB ? s1[1] : 0, onB ? s1[2] : 0};
+    double shd[3] = {sh[0] * a.L[0], sh[1] * a.L[1], sh[2] * a.L[2]};
+    float off[3] = {onB ? pi.frame.x : 0.f, onB ? pi.frame.y : 0.f, onB ? pi.frame.z : 0.f};
+    float org[3] = {0.f, 0.f, 0.f};
+    if (MIXED) {
+      float4 o = ((const float4*)a.vorg)[v];
+      org[0] = o.x; org[1] = o.y; org[2] = o.z;
+    }
+    bool f = onB ? fB : fA, l = onB ? lB : lA;
+    int vid = slot_vid(k, I * STIV_BR, J * STIV_BC, 2 * P, P, f, l);
+    stage_slot<MIXED, DM>(onB ? ws.B : ws.A, a, onB ? pi.voff_j : pi.voff_i, a.fprep + (size_t)v * a.fstride,
+                          stiv_nverts(P), vid, k, sh, shd, off, dx, b, onB ? a.dm : 0.0,
+                          onB ? __double2float_ru(a.dm) : 0.0f, org, f32keys);
+  };
+  float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  bool onB;
+  int k = packed_slot(lane, fA, lA, fB, lB, onB);
+  if (k >= 0) stage_one(onB, k, b);
+  if ((fA && lA) || (fB && lB)) {
+    // P = 2: a patch with both poles; its south-pole slot (lane 0 for A,
+    // lane 15 for B, each on its own side)
+    bool two = lane == 0 ? (fA && lA) : lane == 15 ? (fB && lB) : false;
+    if (two) {
+      float b2[6];
+      stage_one(lane == 15, SS, b2);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { b[c] = fminf(b[c], b2[c]); b[3 + c] = fmaxf(b[3 + c], b2[3 + c]); }
+    }
   }
-  if (lane < NS) {
-    int vidA = slot_vid(lane, IA * STIV_BR, JA * STIV_BC, WA, PA, fA, lA);
-    int vidB = slot_vid(lane, IB * STIV_BR, JB * STIV_BC, WB, PB, fB, lB);
-    stage_slot<MIXED, DM>(ws.A, a, pi.voff_i, a.fprep + (size_t)vi * a.fstride, nvA, vidA, lane, s0, sh0, offA, dx, bA,
-                          0.0, 0.0f, orgA, f32keys);
-    stage_slot<MIXED, DM>(ws.B, a, pi.voff_j, a.fprep + (size_t)vj * a.fstride, nvB, vidB, lane, s1, sh1, offB, dx, bB,
-                          a.dm, __double2float_ru(a.dm), orgB, f32keys);
-  }
+  float bA[6], bB[6];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    bA[c] = fkey_val(__reduce_min_sync(0xffffffffu, fkey32(bA[c])));
-    bA[3 + c] = fkey_val(__reduce_max_sync(0xffffffffu, fkey32(bA[3 + c])));
-    bB[c] = fkey_val(__reduce_min_sync(0xffffffffu, fkey32(bB[c])));
-    bB[3 + c] = fkey_val(__reduce_max_sync(0xffffffffu, fkey32(bB[3 + c])));
+    float la = onB ? INFINITY : b[c], ha = onB ? -INFINITY : b[3 + c];
+    float lb = onB ? b[c] : INFINITY, hb = onB ? b[3 + c] : -INFINITY;
+    bA[c] = fkey_val(__reduce_min_sync(0xffffffffu, fkey32(la)));
+    bA[3 + c] = fkey_val(__reduce_max_sync(0xffffffffu, fkey32(ha)));
+    bB[c] = fkey_val(__reduce_min_sync(0xffffffffu, fkey32(lb)));
+    bB[3 + c] = fkey_val(__reduce_max_sync(0xffffffffu, fkey32(hb)));
   }
   if (lane < 6) { ws.A.box[lane] = bA[lane]; ws.B.box[lane] = bB[lane]; }
   if (lane == 0) {
@@ -350,33 +381,66 @@ __device__ __forceinline__ bool fbox_hit(const float* a, const float* b) {
   return a[0] <= b[3] && b[0] <= a[3] && a[1] <= b[4] && b[1] <= a[4] && a[2] <= b[5] && b[2] <= a[5];
 }
 
-// Compact the primitives of S whose FP32 boxes overlap box ob; the boxes of
-// the kept vertices (and of the kept edges, if elo is given) are stored in
-// the compacted order for the stage-1 loops.  A primitive's box (the min and
-// max of its slots' boxes) misses ob on an axis exactly when all its slots
-// lie above ob there (every lo > ob's hi) or all below (every hi < ob's lo),
-// so the test reads per-slot bit masks instead of merging boxes.
-__device__ void filter_patch(PatchSm& S, const float* ob, int lane, float4* elo, float4* ehi) {
-  unsigned above[3], below[3];
+// Compact the primitives of both staged patches whose FP32 boxes overlap the
+// other patch's box (A's against B's box, B's against A's); the boxes of the
+// kept vertices (and of A's kept edges) are stored in the compacted order for
+// the stage-1 loops.  A primitive's box (the min and max of its slots' boxes)
+// misses a box on an axis exactly when all its slots lie above it there
+// (every lo > its hi) or all below (every hi < its lo), so the test reads
+// per-slot bit masks instead of merging boxes.  Both patches share each pass
+// over the lanes: the slot masks come from the packed slot layout of the
+// staging, and the primitive lists of A and B are concatenated.
+__device__ void filter_pair(WarpSm& ws, int lane) {
+  PatchSm& A = ws.A;
+  PatchSm& B = ws.B;
+  bool fA = A.I == 0, lA = A.I == stiv_nband_blocks(A.P) - 1;
+  bool fB = B.I == 0, lB = B.I == stiv_nband_blocks(B.P) - 1;
+  unsigned abA[3], blA[3], abB[3], blB[3];
   {
-    bool in = lane < NS;
+    bool onB;
+    int k = packed_slot(lane, fA, lA, fB, lB, onB);
+    bool in = k >= 0;
+    const PatchSm& S = onB ? B : A;
+    const float* ob = onB ? A.box : B.box;
+    int poleA = fA ? SN : SS, poleB = fB ? SN : SS;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float lo = in ? S.lo[c][lane] : 0.0f, hi = in ? S.hi[c][lane] : 0.0f;
-      above[c] = __ballot_sync(0xffffffffu, in && lo > ob[3 + c]);
-      below[c] = __ballot_sync(0xffffffffu, in && hi < ob[c]);
+      float lo = in ? S.lo[c][k] : 0.0f, hi = in ? S.hi[c][k] : 0.0f;
+      unsigned ma = __ballot_sync(0xffffffffu, in && lo > ob[3 + c]);
+      unsigned mb = __ballot_sync(0xffffffffu, in && hi < ob[c]);
+      abA[c] = (ma & 0x7FFFu) | (((ma >> 30) & 1u) << poleA);
+      abB[c] = ((ma >> 15) & 0x7FFFu) | (((ma >> 31) & 1u) << poleB);
+      blA[c] = (mb & 0x7FFFu) | (((mb >> 30) & 1u) << poleA);
+      blB[c] = ((mb >> 15) & 0x7FFFu) | (((mb >> 31) & 1u) << poleB);
+    }
+    if ((fA && lA) || (fB && lB)) {   // P = 2: the south-pole slots of two-pole patches
+      bool two = lane == 0 ? (fA && lA) : lane == 15 ? (fB && lB) : false;
+      const PatchSm& S2 = lane == 15 ? B : A;
+      const float* ob2 = lane == 15 ? A.box : B.box;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float lo = two ? S2.lo[c][SS] : 0.0f, hi = two ? S2.hi[c][SS] : 0.0f;
+        unsigned ma = __ballot_sync(0xffffffffu, two && lo > ob2[3 + c]);
+        unsigned mb = __ballot_sync(0xffffffffu, two && hi < ob2[c]);
+        abA[c] |= (ma & 1u) << SS; abB[c] |= ((ma >> 15) & 1u) << SS;
+        blA[c] |= (mb & 1u) << SS; blB[c] |= ((mb >> 15) & 1u) << SS;
+      }
     }
   }
+  const unsigned lower = (1u << lane) - 1u;
 #pragma unroll 1
   for (int kind = 0; kind < 3; ++kind) {
-    int n = kind == 0 ? S.nv : kind == 1 ? S.nt : S.ne;
-    unsigned char* out = kind == 0 ? S.vf : kind == 1 ? S.tf : S.ef;
-    int base = 0;
+    int nA = kind == 0 ? A.nv : kind == 1 ? A.nt : A.ne;
+    int nB = kind == 0 ? B.nv : kind == 1 ? B.nt : B.ne;
+    int n = nA + nB, baseA = 0, baseB = 0;
     for (int k0 = 0; k0 < n; k0 += 32) {
-      int k = k0 + lane;
+      int kk = k0 + lane;
+      bool valid = kk < n, isB = kk >= nA;
+      int k = isB ? kk - nA : kk;
+      PatchSm& S = isB ? B : A;
       bool hit = false;
       unsigned sm = 0;
-      if (k < n) {
+      if (valid) {
         if (kind == 0) {
           sm = 1u << S.tp->v_slot[k];
         } else if (kind == 1) {
@@ -386,12 +450,16 @@ __device__ void filter_patch(PatchSm& S, const float* ob, int lane, float4* elo,
           int e = S.tp->e_slots[k];
           sm = (1u << (e & 63)) | (1u << ((e >> 6) & 63));
         }
-        hit = (above[0] & sm) != sm && (below[0] & sm) != sm && (above[1] & sm) != sm && (below[1] & sm) != sm &&
-              (above[2] & sm) != sm && (below[2] & sm) != sm;
+        unsigned a0 = isB ? abB[0] : abA[0], a1 = isB ? abB[1] : abA[1], a2 = isB ? abB[2] : abA[2];
+        unsigned b0 = isB ? blB[0] : blA[0], b1 = isB ? blB[1] : blA[1], b2 = isB ? blB[2] : blA[2];
+        hit = (a0 & sm) != sm && (b0 & sm) != sm && (a1 & sm) != sm && (b1 & sm) != sm && (a2 & sm) != sm &&
+              (b2 & sm) != sm;
       }
       unsigned m = __ballot_sync(0xffffffffu, hit);
+      unsigned mB = __ballot_sync(0xffffffffu, valid && isB);
       if (hit) {
-        int pos = base + __popc(m & ((1u << lane) - 1u));
+        int pos = isB ? baseB + __popc(m & mB & lower) : baseA + __popc(m & ~mB & lower);
+        unsigned char* out = kind == 0 ? S.vf : kind == 1 ? S.tf : S.ef;
         out[pos] = (unsigned char)k;
         if (kind == 0) {
           float b[6];
@@ -399,16 +467,21 @@ __device__ void filter_patch(PatchSm& S, const float* ob, int lane, float4* elo,
           S.vlo[pos] = make_float4(b[0], b[1], b[2], 0.f);
           S.vhi[pos] = make_float4(b[3], b[4], b[5], 0.f);
         }
-        if (kind == 2 && elo) {
+        if (kind == 2 && !isB) {
           float b[6];
-          edge_box(S, k, b);
-          elo[pos] = make_float4(b[0], b[1], b[2], 0.f);
-          ehi[pos] = make_float4(b[3], b[4], b[5], 0.f);
+          edge_box(A, k, b);
+          ws.elo[pos] = make_float4(b[0], b[1], b[2], 0.f);
+          ws.ehi[pos] = make_float4(b[3], b[4], b[5], 0.f);
         }
       }
-      base += __popc(m);
+      baseA += __popc(m & ~mB);
+      baseB += __popc(m & mB);
     }
-    if (lane == 0) { if (kind == 0) S.nvf = base; else if (kind == 1) S.ntf = base; else S.nef = base; }
+    if (lane == 0) {
+      if (kind == 0) { A.nvf = baseA; B.nvf = baseB; }
+      else if (kind == 1) { A.ntf = baseA; B.ntf = baseB; }
+      else { A.nef = baseA; B.nef = baseB; }
+    }
   }
   __syncwarp();
 }
@@ -1292,8 +1365,7 @@ __global__ void __launch_bounds__(NW * 32, 3) narrow_kernel(narrow_args a) {
     int r = (int)(w >> 32), pa = (int)((w >> 16) & 0xFFFF), pb = (int)(w & 0xFFFF);
     stiv_pair_info pi = a.pinfo[r];
     stage_pair<MIXED, DM>(ws, a, topo, pi, pa, pb, lane);
-    filter_patch(ws.A, ws.B.box, lane, ws.elo, ws.ehi);
-    filter_patch(ws.B, ws.A.box, lane, nullptr, nullptr);
+    filter_pair(ws, lane);
     int n1 = 0;
     // stage 1: FP32 boxes.  VF: vertices of A vs triangles of B (0), vertices of B vs triangles of A (1)
 #pragma unroll 1
