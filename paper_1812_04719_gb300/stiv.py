@@ -38,7 +38,7 @@ EXPORTS = ["stiv_create", "stiv_destroy", "stiv_status_string", "stiv_last_cuda_
            "stiv_grad_to_coef", "stiv_step", "stiv_sync_counts", "stiv_sort_scratch_bytes", "stiv_sort_pairs",
            "stiv_profile", "stiv_profile_read", "stiv_sort_pairs_static", "stiv_autotune", "stiv_set_tuning",
            "stiv_wait_selftest", "stiv_lcp_matrix", "stiv_lcp_solve",
-           "stiv_mesh_fidelity", "stiv_stiv_grad_x0"]
+           "stiv_mesh_fidelity", "stiv_stiv_grad_x0", "stiv_peak_probe"]
 TUNE_NAMES = ("narrow_ctas_per_sm", "pieces_ctas_per_sm", "fp64_blocks_per_sm", "patch_blocks_per_sm",
               "piece_levels")
 SORT_STATIC_MAX = 1 << 20
@@ -113,6 +113,7 @@ def lib() -> ctypes.CDLL:
     L.stiv_stiv_grad_x0.argtypes = [vp, vp, i32, vp, vp, vp, P(StivPairs), P(StivContacts), vp, vp]
     L.stiv_mesh_fidelity.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, i32, vp]
     L.stiv_lcp_solve.argtypes = [vp, vp, P(StivLcp), ctypes.c_double, i32, i32, vp, vp]
+    L.stiv_peak_probe.argtypes = [vp, i32, i64, vp, P(ctypes.c_double)]
     L.stiv_profile.argtypes = [vp, i32]
     L.stiv_profile_read.argtypes = [vp, i32, vp, vp, vp, vp]
     _lib = L
@@ -221,6 +222,14 @@ def stiv_sort_pairs_static(stream, n, key_bits, keys_in_ptr, vals_in_ptr, keys_o
     that cannot allocate device memory; calls that overlap on the GPU race."""
     _check(lib().stiv_sort_pairs_static(stream, n, key_bits, keys_in_ptr, vals_in_ptr, keys_out_ptr,
                                         vals_out_ptr), "stiv_sort_pairs_static")
+
+
+def stiv_peak_probe(stream, kind: int, iters: int, sink_ptr: int) -> float:
+    """Launch the FMA-rate probe (kind 0 FP64, 1 FP32); returns the FLOPs the
+    launch performs (time it with events on the same stream)."""
+    fl = ctypes.c_double(0.0)
+    _check(lib().stiv_peak_probe(stream, int(kind), int(iters), sink_ptr, ctypes.byref(fl)), "stiv_peak_probe")
+    return fl.value
 
 
 def stiv_profile(h: int, enable: bool):

@@ -1,0 +1,145 @@
+"""Whole-list parity on the benchmark's workload: 1440 prolate vesicles at 58%
+volume fraction on the staggered lattice, p = 16 -> 32, in the launch
+configuration the benchmark times (autotuned launch shapes, CUDA-graph
+replay of the whole step).
+
+- FP64 form, on the oracle's own FP64 synthesis: every candidate pair, every
+  contact (pair, type, primitive ids; contact time and inside-test weights
+  bit for bit), V per contact and per pair within 1e-10 relative, every
+  gradient row within 1e-9 of its row's largest entry, against the oracle's
+  all-pairs Alg. 2 over the whole scene (Eq. 3.1, Eq. 3.2, Alg. 2
+  checkContact).
+- MIXED form end to end: the tensor-core synthesis writes the FP32
+  vertices, and the oracle recomputes the whole scene on exactly those
+  vertices (widened to FP64), with the same bars.
+- The certified FP32 rejection stages are checked against the exact path
+  (stiv_params.exact_only = 1: every exact-box pair through the FP64 test)
+  at this size, in both forms, GPU against GPU.
+
+The oracle runs each whole scene on the host cores (about a minute on 16
+cores per form)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1812_04719_gb300 import scenegen as G
+from paper_1812_04719_gb300 import stiv as S
+from tests.gpu_run import gpu_pairs_rows, verts_list
+from tests.oracle_pool import oracle_vertices
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def bits(x):
+    return np.ascontiguousarray(x, dtype=np.float64).view(np.int64)
+
+
+@pytest.fixture(scope="module")
+def scene():
+    sc = G.scene_1440()
+    return sc, oracle_vertices(sc)
+
+
+def bench_engine(sc, prec, exact_only=False):
+    """An engine set up as the benchmark sets it up: buffers sized by a first
+    step, launch shapes picked by the autotuner."""
+    eng = S.Stiv.for_scene(sc, precision=prec, pair_cap=8192, contact_cap=1 << 20, exact_only=exact_only)
+    ds = S.DeviceScene.from_scene(sc, precision=prec)
+    eng.step(ds, grad=True)
+    eng.autotune(ds)
+    return eng, ds
+
+
+def replay(eng, ds, upsample, replays=3):
+    """Graph replays of the whole step; the last one's outputs on the host."""
+    for _ in range(replays):
+        r = eng.step(ds, grad=True, upsample=upsample, use_graph=True)
+    torch.cuda.synchronize()
+    out = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
+    out["verts"] = ds.verts.double().cpu().numpy()
+    return out
+
+
+def oracle_scene(orc, sc, flat, grad_wrt="X1"):
+    Xs = verts_list(sc, flat)
+    boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
+    pairs = orc.candidate_pairs(boxes, sc.L)
+    c = orc.contacts(sc.P, Xs, pairs, sc.L, sc.eps * sc.dt, grad=True, grad_wrt=grad_wrt)
+    c["pairs"] = pairs
+    return c
+
+
+def assert_whole_list(g, c):
+    assert g["counts"][S.C_STATUS] == 0
+    assert np.array_equal(gpu_pairs_rows(g), c["pairs"])
+    n = len(c["pair"])
+    assert n > 500_000 and len(g["pair"]) == n
+    for k in ("pair", "type", "a", "b"):
+        assert np.array_equal(g[k], c[k]), k
+    assert np.array_equal(bits(g["tau"]), bits(c["tau"]))
+    assert np.array_equal(bits(g["w"]), bits(c["w"]))
+    assert np.all(np.abs(g["V"] - c["V"]) <= 1e-10 * np.abs(c["V"]))
+    assert np.all(np.abs(g["V_pair"] - c["V_pair"]) <= 1e-10 * np.abs(c["V_pair"]))
+    scale = np.abs(c["grad"]).reshape(n, -1).max(axis=1)
+    err = np.abs(g["grad"] - c["grad"]).reshape(n, -1).max(axis=1)
+    assert np.all(err <= 1e-9 * scale)
+    assert np.array_equal(g["gves"], c["gves"]) and np.array_equal(g["gvid"], c["gvid"])
+    assert g["counts"][S.C_PRIM] == c["counts"][1]
+    assert g["counts"][S.C_DEGEN] == c["counts"][2]
+
+
+@pytest.fixture(scope="module")
+def fp64_run(scene):
+    sc, Xo = scene
+    eng, ds = bench_engine(sc, S.STIV_FP64)
+    ds.verts.copy_(torch.from_numpy(Xo))
+    g = replay(eng, ds, upsample=False)
+    eng.close()
+    return g
+
+
+@pytest.fixture(scope="module")
+def oracle_fp64(orc, scene):
+    sc, Xo = scene
+    return oracle_scene(orc, sc, Xo)
+
+
+def test_fp64_form_whole_list(fp64_run, oracle_fp64):
+    assert_whole_list(fp64_run, oracle_fp64)
+
+
+@pytest.fixture(scope="module")
+def mixed_run(scene):
+    sc, _ = scene
+    eng, ds = bench_engine(sc, S.STIV_MIXED)
+    g = replay(eng, ds, upsample=True)           # the tensor-core synthesis writes the vertices
+    g["grad_x0"] = eng.grad_x0(ds).cpu().numpy()
+    eng.close()
+    return g
+
+
+def test_mixed_form_whole_list_end_to_end(orc, scene, mixed_run):
+    sc, _ = scene
+    c = oracle_scene(orc, sc, mixed_run["verts"])
+    assert_whole_list(mixed_run, c)
+
+
+@pytest.mark.parametrize("prec", [S.STIV_FP64, S.STIV_MIXED], ids=["fp64", "mixed"])
+def test_filter_cascade_equals_exact_path(scene, prec):
+    """The certified FP32 stages (Bernstein certificate, piece test) change
+    nothing: the filtered step and the exact step (every exact-box pair
+    through the FP64 contact test) give the same lists bit for bit."""
+    sc, Xo = scene
+    Xd = torch.from_numpy(np.ascontiguousarray(Xo, dtype=np.float32 if prec == S.STIV_MIXED else np.float64))
+    runs = []
+    for exact in (False, True):
+        eng, ds = bench_engine(sc, prec, exact_only=exact)
+        ds.verts.copy_(Xd)
+        runs.append(replay(eng, ds, upsample=False, replays=2))
+        eng.close()
+    f, e = runs
+    assert e["counts"][S.C_EXACT] == e["counts"][S.C_PRIM] > f["counts"][S.C_EXACT]
+    for k in ("i", "j", "shift", "pair", "type", "a", "b", "gves", "gvid"):
+        assert np.array_equal(f[k], e[k]), k
+    for k in ("tau", "w", "V", "V_pair", "grad"):
+        assert np.array_equal(bits(f[k]), bits(e[k])), k
