@@ -15,6 +15,10 @@ replay of the whole step).
 - The certified FP32 rejection stages are checked against the exact path
   (stiv_params.exact_only = 1: every exact-box pair through the FP64 test)
   at this size, in both forms, GPU against GPU.
+- The MIXED form end to end against the FP64 oracle on the oracle's own
+  synthesis: the stated accuracy bounds of the precision form
+  (paper_1812_04719_gb300/accuracy.py) on V, the contact lists and the
+  gradient rows.
 
 The oracle runs each whole scene on the host cores (about a minute on 16
 cores per form)."""
@@ -22,6 +26,7 @@ import numpy as np
 import pytest
 import torch
 
+from paper_1812_04719_gb300 import accuracy as A
 from paper_1812_04719_gb300 import scenegen as G
 from paper_1812_04719_gb300 import stiv as S
 from tests.gpu_run import gpu_pairs_rows, verts_list
@@ -143,3 +148,35 @@ def test_filter_cascade_equals_exact_path(scene, prec):
         assert np.array_equal(f[k], e[k]), k
     for k in ("tau", "w", "V", "V_pair", "grad"):
         assert np.array_equal(bits(f[k]), bits(e[k])), k
+
+
+@pytest.fixture(scope="module")
+def oracle_fp64_x0(orc, scene):
+    sc, Xo = scene
+    return oracle_scene(orc, sc, Xo, grad_wrt="X0")
+
+
+def test_mixed_form_accuracy_bounds(scene, mixed_run, oracle_fp64, oracle_fp64_x0):
+    """The precision form end to end (tensor-core synthesis, FP32 vertices,
+    FP64 detection and volumes) against the FP64 oracle on its own synthesis:
+    (1) |dV_k| <= S_k delta_k for every contact in both lists; (2) every
+    contact in one list only has decision margins below 4 delta_k; (3) every
+    gradient row of a contact in both lists within 4 kappa_k of its largest
+    entry; (4) every vesicle pair's V within the sum of its contacts' bounds
+    and of its one-list contacts' volumes.  Almost every contact is in both
+    lists."""
+    sc, Xo = scene
+    c = oracle_fp64
+    rb = dict(c)
+    pr = c["pairs"]
+    rb["i"], rb["j"] = pr[:, 0], pr[:, 1]
+    rb["shift"] = 9 * (pr[:, 2] + 1) + 3 * (pr[:, 3] + 1) + (pr[:, 4] + 1)
+    assert np.array_equal(oracle_fp64_x0["pair"], c["pair"]) and np.array_equal(oracle_fp64_x0["a"], c["a"])
+    pdelta = A.point_delta(sc.p, sc.coef_of, sc.vert_off(), Xo)
+    res = A.compare(mixed_run, mixed_run["verts"], rb, Xo, oracle_fp64_x0["grad"], pdelta, sc.vert_off(), sc.L)
+    print({k: v for k, v in res.items()})
+    assert res["contacts_both"] >= 0.999 * res["contacts_fp64"]
+    assert res["bound1_V_holds"], res["V_ratio_max"]
+    assert res["bound2_lists_hold"], res["symdiff_margin_max"]
+    assert res["bound3_grad_holds"], res["grad_ratio_max"]
+    assert res["bound4_pairs_hold"], res["pairs_exceeding_bound"]
