@@ -29,9 +29,39 @@ __device__ __forceinline__ double vload(const void* X, int mixed, size_t i) {
   return mixed ? (double)((const float*)X)[i] : ((const double*)X)[i];
 }
 
+// Order-preserving int64 image of a double (a <= b <=> okey(a) <= okey(b)
+// for non-NaN values, -0 just below +0) and its inverse (the map is its own
+// inverse): exact FP64 min / max on the integer pipe.
+__device__ __forceinline__ long long okey(double v) {
+  long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double okey_val(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFll));
+}
+
+// x rounded to float toward -inf (up = false) or +inf (up = true), on the
+// integer pipe for |x| in the normal float range: the significand truncated
+// to 23 bits rounds toward zero, and one unit in the last place more in
+// magnitude gives the other direction when bits were dropped (a carry into
+// the exponent, up to infinity, is the correct rounding).  Other values take
+// the conversion instruction.
+__device__ __forceinline__ float d2f_dir(double x, bool up) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -126 || e > 127) return up ? __double2float_ru(x) : __double2float_rd(x);
+  unsigned sgn = (unsigned)(b >> 63);
+  unsigned f = (sgn << 31) | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFF);
+  if ((b & 0x1FFFFFFFull) != 0 && (up ? sgn == 0 : sgn != 0)) f += 1;
+  return __uint_as_float(f);
+}
+
 // One CTA per vesicle.  MIXED (FP32 vertices): the min / max run in FP32,
 // which is exact, and widen exactly to FP64, so the boxes are those of the
-// FP64 reduction bit for bit without its FP64 instructions.
+// FP64 reduction bit for bit without its FP64 instructions.  FP64 vertices:
+// the min / max run on order-preserving integer images (exact), and the
+// per-vertex FP32 boxes are rounded outward on the integer pipe, so that the
+// FP64 pipe only forms the staging differences.
 template <bool MIXED>
 __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, const int64_t* voff, const void* X,
                                                     int mixed, double dm, double Lx, double Ly, double Lz,
@@ -55,7 +85,7 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
   int P = 2 * pv[v], nv = stiv_nverts(P);
   bool use_sm = (size_t)6 * nv <= vb_cap;
   const size_t base = voff[v];
-  __shared__ double red[6][256];
+  __shared__ long long red[6][256];
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   bool bad = false;
   if (MIXED) {
@@ -71,38 +101,62 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
         if (use_sm) { vbs[c * nv + k] = a; vbs[(3 + c) * nv + k] = b; }
       }
     for (int c = 0; c < 3; ++c) { lo[c] = (double)flo[c]; hi[c] = (double)fhi[c]; }
-  } else {
+  }
+  long long klo[3], khi[3];
+  for (int c = 0; c < 3; ++c) { klo[c] = okey(lo[c]); khi[c] = okey(hi[c]); }
+  if (!MIXED) {
+    const double* Xd = (const double*)X;
     for (int k = threadIdx.x; k < nv; k += blockDim.x)
       for (int c = 0; c < 3; ++c) {
-        double x0 = vload(X, mixed, base + (size_t)c * nv + k);
-        double x1 = vload(X, mixed, base + (size_t)(3 + c) * nv + k);
-        if (!finite_d(x0) || !finite_d(x1)) bad = true;
-        double a = fmin(x0, x1), b = fmax(x0, x1);
-        lo[c] = fmin(lo[c], a);
-        hi[c] = fmax(hi[c], b);
-        if (use_sm) { vbs[c * nv + k] = __double2float_rd(a); vbs[(3 + c) * nv + k] = __double2float_ru(b); }
+        double x0 = Xd[base + (size_t)c * nv + k], x1 = Xd[base + (size_t)(3 + c) * nv + k];
+        long long b0 = __double_as_longlong(x0), b1 = __double_as_longlong(x1);
+        long long k0 = okey(x0), k1 = okey(x1);
+        // finite iff the exponent field is not all ones; a NaN is ignored by
+        // the min / max, as fmin / fmax ignore it
+        if ((~b0 & 0x7FF0000000000000ll) == 0 || (~b1 & 0x7FF0000000000000ll) == 0) bad = true;
+        bool n0 = (b0 & 0x7FFFFFFFFFFFFFFFll) > 0x7FF0000000000000ll;
+        bool n1 = (b1 & 0x7FFFFFFFFFFFFFFFll) > 0x7FF0000000000000ll;
+        if (n0) k0 = k1;
+        if (n1) k1 = k0;
+        long long ka = k0 < k1 ? k0 : k1, kb = k0 < k1 ? k1 : k0;
+        if (!(n0 && n1)) {
+          klo[c] = ka < klo[c] ? ka : klo[c];
+          khi[c] = kb > khi[c] ? kb : khi[c];
+        }
+        if (use_sm) {
+          vbs[c * nv + k] = d2f_dir(okey_val(ka), false);
+          vbs[(3 + c) * nv + k] = d2f_dir(okey_val(kb), true);
+        }
       }
   }
-  for (int c = 0; c < 3; ++c) { red[c][threadIdx.x] = lo[c]; red[3 + c][threadIdx.x] = hi[c]; }
+  for (int c = 0; c < 3; ++c) { red[c][threadIdx.x] = klo[c]; red[3 + c][threadIdx.x] = khi[c]; }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_NONFINITE);
   for (int s = 128; s > 0; s >>= 1) {
     if (threadIdx.x < s)
       for (int c = 0; c < 3; ++c) {
-        red[c][threadIdx.x] = fmin(red[c][threadIdx.x], red[c][threadIdx.x + s]);
-        red[3 + c][threadIdx.x] = fmax(red[3 + c][threadIdx.x], red[3 + c][threadIdx.x + s]);
+        long long a = red[c][threadIdx.x + s], b = red[3 + c][threadIdx.x + s];
+        if (a < red[c][threadIdx.x]) red[c][threadIdx.x] = a;
+        if (b > red[3 + c][threadIdx.x]) red[3 + c][threadIdx.x] = b;
       }
     __syncthreads();
   }
   __shared__ float sorg[4];
+  __shared__ double vlo_s[3], vhi_s[3];
   if (threadIdx.x < 3) {
     int c = threadIdx.x;
-    double l = red[c][0] - dm, u = red[3 + c][0] + dm;
+    vlo_s[c] = okey_val(red[c][0]);
+    vhi_s[c] = okey_val(red[3 + c][0]);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    int c = threadIdx.x;
+    double l = vlo_s[c] - dm, u = vhi_s[c] + dm;
     vbox[6 * v + c] = l;
     vbox[6 * v + 3 + c] = u;
     double L = c == 0 ? Lx : c == 1 ? Ly : Lz;
     if (L > 0.0 && !(u - l < 0.5 * L)) atomicOr((unsigned long long*)&ctr[STIV_C_STATUS], STIV_F_BOX_TOO_SMALL);
     // FP32 frame of this vesicle: origin at the (float-rounded) box centre
-    float o = (float)(0.5 * (red[c][0] + red[3 + c][0]));
+    float o = (float)(0.5 * (vlo_s[c] + vhi_s[c]));
     sorg[c] = o;
     vorg[4 * v + c] = o;
   }
@@ -110,7 +164,7 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
   if (threadIdx.x == 0) {
     // R bounds |X - o| over the vesicle (both times), rounded up
     double R = 0.0;
-    for (int c = 0; c < 3; ++c) R = fmax(R, fmax(red[3 + c][0] - (double)sorg[c], (double)sorg[c] - red[c][0]));
+    for (int c = 0; c < 3; ++c) R = fmax(R, fmax(vhi_s[c] - (double)sorg[c], (double)sorg[c] - vlo_s[c]));
     vorg[4 * v + 3] = __double2float_ru(R);
   }
   // per-vertex FP32 data (two float4).  FP32 vertices: X0 and X1 as stored,
