@@ -74,7 +74,8 @@ enum stiv_count {
   STIV_C_PATCH = 7,    /* patch pairs examined by the narrow phase            */
   STIV_C_FLOPS = 8,    /* FP64 flops executed by the exact contact tests      */
   STIV_C_EXACT = 9,    /* primitive pairs that ran the FP64 contact test      */
-  STIV_NCOUNTS = 10
+  STIV_C_PIECE = 10,   /* primitive pairs the FP32 piece test examined        */
+  STIV_NCOUNTS = 11
 };
 
 enum stiv_flag {

@@ -39,6 +39,7 @@ __global__ void finalize_kernel(int64_t* ctr, int64_t C, int64_t* counts, int* t
     for (int k = 0; k < 8; ++k) counts[k] = ctr[k];
     counts[STIV_C_FLOPS] = ctr[12];
     counts[STIV_C_EXACT] = ctr[13];
+    counts[STIV_C_PIECE] = ctr[14];
   }
 }
 

@@ -27,8 +27,8 @@ LIB_PATH = os.path.join(HERE, "libstiv.so")
 STIV_OK, STIV_ERR_ARG, STIV_ERR_CAPACITY, STIV_ERR_TIMEOUT, STIV_ERR_CUDA, STIV_ERR_INPUT = range(6)
 STIV_FP64, STIV_MIXED = 0, 1
 STIV_VEL_RELATIVE, STIV_VEL_ABSOLUTE = 0, 1
-C_PAIRS, C_PRIM, C_VF, C_EE, C_CPAIRS, C_DEGEN, C_STATUS, C_PATCH, C_FLOPS, C_EXACT = range(10)
-NCOUNTS = 10
+C_PAIRS, C_PRIM, C_VF, C_EE, C_CPAIRS, C_DEGEN, C_STATUS, C_PATCH, C_FLOPS, C_EXACT, C_PIECE = range(11)
+NCOUNTS = 11
 F_PAIRS_OVERFLOW, F_CONTACTS_OVERFLOW, F_BOX_TOO_SMALL, F_NONFINITE, F_WORK_OVERFLOW, F_TIMEOUT = 1, 2, 4, 8, 16, 32
 F_BAD_ORDER = 64
 MAX_ORDER = 32   # largest SH order p the library accepts (mesh order 64)
