@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--no-fidelity", action="store_true", help="skip the mesh-fidelity diagnostic")
     ap.add_argument("--no-dm", action="store_true", help="skip timing the step with minimum separation d_m > 0")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip timing the 4096-vesicle (uneven orders) and 256-vesicle workloads beside the 1440 one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
@@ -306,60 +308,41 @@ def job_throughput(n_per_rank: int, world: int, ms_max: float) -> float:
     return n_per_rank * world / (ms_max * 1e-3)
 
 
-def compare_forms(S, sc, ra, rb, verts_a, verts_b):
-    """Errors of form a (the precision form) against form b (the FP64 form,
-    which the parity tests tie to the FP64 oracle bit for bit)."""
+def mixed_errors(S, sc, e_m, d_m, e_64, d_64, dev) -> dict:
+    """The precision form's errors against the FP64 form on this workload and
+    its stated bounds (paper_1812_04719_gb300/accuracy.py): one step of each
+    form on its own synthesis, compared contact by contact."""
     import torch
-    out = {}
-    xa = verts_a.double().cpu().numpy(); xb = verts_b.double().cpu().numpy()
-    out["max_abs_dX"] = float(np.abs(xa - xb).max())
-    out["max_abs_X"] = float(np.abs(xb).max())
+    from paper_1812_04719_gb300 import accuracy as A
 
-    def pair_keys(r):
-        i = r["i"].cpu().numpy().astype(np.uint64); j = r["j"].cpu().numpy().astype(np.uint64)
-        s_ = r["shift"].cpu().numpy().astype(np.uint64)
-        return (i << np.uint64(18)) | (j << np.uint64(5)) | s_
-
-    pa, pb = pair_keys(ra), pair_keys(rb)
-    va, vb = ra["V_pair"].cpu().numpy(), rb["V_pair"].cpu().numpy()
-    common, ia, ib = np.intersect1d(pa, pb, return_indices=True)
-    hit = vb[ib] > 0
-    rel = np.abs(va[ia][hit] - vb[ib][hit]) / vb[ib][hit]
-    out["V_pair_max_rel"] = float(rel.max()) if rel.size else 0.0
-    out["V_pair_median_rel"] = float(np.median(rel)) if rel.size else 0.0
-    out["V_pairs_rel_above_1e-3"] = int((rel > 1e-3).sum())
-    # volume-weighted: sum |dV| over all pairs relative to the total volume
-    out["V_sum_abs_dV_over_sum_V"] = float(np.abs(va[ia] - vb[ib]).sum() / max(vb.sum(), 1e-300))
-    out["candidate_pairs_only_in_one_form"] = int(len(pa) + len(pb) - 2 * len(common))
-
-    def contact_keys(r, pk):
-        pr = r["pair"].cpu().numpy()
-        t = r["type"].cpu().numpy().astype(np.uint64)
-        a = r["a"].cpu().numpy().astype(np.uint64); b = r["b"].cpu().numpy().astype(np.uint64)
-        return (pk[pr] << np.uint64(32)) | (t << np.uint64(30)) | (a << np.uint64(15)) | b
-
-    ca, cb = contact_keys(ra, pa), contact_keys(rb, pb)
-    cc, ja, jb = np.intersect1d(ca, cb, return_indices=True)
-    out["contacts_fp64_form"] = int(len(cb))
-    out["contacts_symmetric_difference"] = int(len(ca) + len(cb) - 2 * len(cc))
-    ga = ra["grad"].cpu().numpy().reshape(len(ca), -1)[ja]
-    gb = rb["grad"].cpu().numpy().reshape(len(cb), -1)[jb]
-    nb = np.linalg.norm(gb, axis=1)
-    ok = nb > 0
-    g_rel = np.linalg.norm(ga - gb, axis=1)[ok] / nb[ok]
-    out["grad_row_max_rel"] = float(g_rel.max()) if g_rel.size else 0.0
-    out["grad_row_median_rel"] = float(np.median(g_rel)) if g_rel.size else 0.0
+    def host(r):
+        return {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
+    ra = host(e_m.step(d_m, grad=True))
+    rb = host(e_64.step(d_64, grad=True))
+    g0b = e_64.grad_x0(d_64).cpu().numpy()
+    torch.cuda.synchronize(dev)
+    Xa = d_m.verts.double().cpu().numpy()
+    Xb = d_64.verts.cpu().numpy()
+    pdelta = A.point_delta(sc.p, sc.coef_of, sc.vert_off(), Xb)
+    res = A.compare(ra, Xa, rb, Xb, g0b, pdelta, sc.vert_off(), sc.L)
+    keep = ("contacts_fp64", "only_mixed", "only_fp64", "V_ratio_max", "grad_ratio_max", "grad_rel_max",
+            "symdiff_margin_max", "symdiff_volume", "V_pair_abs_err_sum_over_V_sum", "V_pair_rel_err_max")
+    out = {k: res[k] for k in keep}
+    out["max_abs_dX"] = float(np.abs(Xa - Xb).max())
+    out["bounds"] = "V_ratio <= 1 (|dV_k| <= S_k delta_k); symdiff_margin <= 4; grad_ratio <= 4; pairs within bound"
+    out["bounds_hold"] = bool(res["bound1_V_holds"] and res["bound2_lists_hold"] and res["bound3_grad_holds"]
+                              and res["bound4_pairs_hold"])
     return out
 
 
 def measure_fma_peak(S, stream, kind: int, dev) -> float:
     """GFLOP/s of the library's FMA-rate probe (kind 0 FP64, 1 FP32) on this
-    GPU: best of 5 launches of about 20-40 ms, timed with CUDA events on the
+    GPU: best of 5 launches of about 30-40 ms, timed with CUDA events on the
     launching stream after 2 warm-up launches."""
     import torch
     sink = torch.zeros(1, dtype=torch.float64, device=dev)
     st = int(stream.cuda_stream)
-    iters = 40_000 if kind == 0 else 2_000_000
+    iters = 8_000 if kind == 0 else 400_000
     best = 0.0
     for k in range(7):
         e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
@@ -535,13 +518,46 @@ def run_ours(args, rank, world, local):
         if rank == 0:
             e_m, e_64 = (eng, eng2) if prec == S.STIV_MIXED else (eng2, eng)
             d_m, d_64 = (ds, ds2) if prec == S.STIV_MIXED else (ds2, ds)
-            ra = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in e_m.step(d_m, grad=True).items()}
-            rb = e_64.step(d_64, grad=True)
-            torch.cuda.synchronize(dev)
-            other["mixed_errors"] = compare_forms(S, sc, ra, rb, d_m.verts, d_64.verts)
+            other["mixed_errors"] = mixed_errors(S, sc, e_m, d_m, e_64, d_64, dev)
         eng2.close()
 
     roof = kernel_roofline(S, sc, form, prec, stage_ms, counts, peaks, clk, n_sms)
+
+    # the other workloads of the paper's shapes, timed the same way (graph
+    # replay, autotuned shapes, L2 flushed): the 4096-vesicle batch of uneven
+    # orders p in {8, 12, 16} at 40% in both forms, and the 256-vesicle
+    # 50% workload (p = 12 -> 24) in the FP64 form
+    other_wl = None
+    if args.workload == "1440" and not args.cells and not args.no_other_workloads:
+        from paper_1812_04719_gb300 import scenegen as G
+        other_wl = {}
+        for name, mk, forms in (("4096", G.scene_4096, (S.STIV_FP64, S.STIV_MIXED)), ("256", G.scene_256, (S.STIV_FP64,))):
+            sco = mk(seed=default_seed(argparse.Namespace(workload=name, seed=None)) + rank)
+            rec = {"workload": sco.name}
+            for fp in forms:
+                eo = S.Stiv.for_scene(sco, precision=fp, pair_cap=1 << 15, contact_cap=1 << 21, device=dev)
+                dso = S.DeviceScene.from_scene(sco, precision=fp, device=dev)
+                eo.step(dso, grad=True)
+                if not args.no_autotune:
+                    eo.autotune(dso, stream=stream)
+                ms_o = []
+                for k in range(3 + 5):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ro = eo.step(dso, grad=True, use_graph=True, stream=stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    if k >= 3:
+                        ms_o.append(e0.elapsed_time(e1))
+                key = "fp64" if fp == S.STIV_FP64 else "mixed"
+                rec[key] = {"ms_per_step": round(float(np.mean(ms_o)), 3),
+                            "value": job_throughput(sco.n, world, float(np.mean(ms_o))),
+                            "contacts": int(ro["counts"][S.C_VF] + ro["counts"][S.C_EE]),
+                            "prim_pairs_tested": int(ro["counts"][S.C_PRIM])}
+                eo.close()
+                del dso
+            other_wl[name] = rec
 
     # stage 4 alone: the FP64 operations it executed over its time; and the
     # narrow phase's effective rate: the FP64 contact test's operations on
@@ -720,6 +736,8 @@ def run_ours(args, rank, world, local):
                "contacts_vf": int(counts[S.C_VF]), "contacts_ee": int(counts[S.C_EE]),
                "prim_pairs_tested": int(counts[S.C_PRIM]), "patch_pairs": int(counts[S.C_PATCH]),
                "prim_pairs_fp64": int(counts[S.C_EXACT])}
+        if other_wl is not None:
+            cfg["other_workloads"] = other_wl
         if other is not None:
             key = "mixed_form" if other["form"] == "mixed" else "fp64_form"
             cfg[key] = {k: v for k, v in other.items() if k not in ("form", "stage_ms")}
