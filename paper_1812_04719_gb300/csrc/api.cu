@@ -263,7 +263,7 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   size_t o_sg2 = off; off = align_up(off + sizeof(uint64_t) * (size_t)w.C);
   size_t o_ti = off; off = align_up(off + sizeof(int32_t) * 4 * (size_t)w.C);
   size_t o_tf = off; off = align_up(off + sizeof(double) * 3 * (size_t)w.C);
-  size_t o_ctr = off; off = align_up(off + sizeof(int64_t) * 16);
+  size_t o_ctr = off; off = align_up(off + sizeof(int64_t) * 32);
   size_t o_ss = off; off = align_up(off + w.sort_scratch_bytes);
   if (!carve) return stiv_ws_reserve(h, off);
   char* b = (char*)h->ws;
@@ -306,7 +306,7 @@ extern "C" int stiv_detect(stiv_handle* h, void* stream, int32_t n_ves, int32_t 
   int rc = detect_layout(h, n_ves, p_max, cand, out, w, false);
   if (rc) return rc;
   detect_layout(h, n_ves, p_max, cand, out, w, true);
-  STIV_CUDA(h, cudaMemsetAsync(w.ctr, 0, sizeof(int64_t) * 16, st));
+  STIV_CUDA(h, cudaMemsetAsync(w.ctr, 0, sizeof(int64_t) * 32, st));
   STIV_CUDA(h, cudaMemsetAsync(w.pair_cnt, 0, sizeof(int32_t) * (size_t)cand->capacity, st));
   STIV_CUDA(h, cudaMemsetAsync(w.pair_fill, 0, sizeof(int32_t) * (size_t)cand->capacity, st));
   int sms = 152;

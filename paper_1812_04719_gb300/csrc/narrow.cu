@@ -52,7 +52,10 @@ static_assert(NS <= 32, "one lane per vertex slot");
 static_assert(STIV_BR == 2 && STIV_BC % 2 == 0, "patches tile every even-order grid exactly");
 
 struct PatchSm {
-  long long key[6][NS];            // exact swept box of each slot: order keys of lo xyz, hi xyz
+  union {
+    long long key[6][NS];          // d_m > 0: exact swept box of each slot, order keys of lo xyz, hi xyz
+    float m[NS];                   // d_m = 0: bound on the FP32 error of the slot's box ends
+  };
   float x[3][NS], d[3][NS];        // FP32: X0 - origin of vesicle i, X1 - X0
   float lo[3][NS], hi[3][NS];      // FP32 conservative swept box of each slot (frame of vesicle i)
   int vid[NS];                     // global vertex id of each slot (-1: unused)
@@ -192,60 +195,58 @@ __device__ __forceinline__ int fkey32(float f) {
 }
 __device__ __forceinline__ float fkey_val(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7FFFFFFF); }
 
-// One vertex slot: exact FP64 swept-box keys, FP32 frame coordinates and the
-// slot's conservative FP32 swept box (also returned in b).  s: periodic image
-// of the vesicle (applied to both time levels in FP64, as the contact test
-// sees it); off: FP32 offset of the vesicle's frame origin in the pair frame.
+// One vertex slot: FP32 frame coordinates, the slot's conservative FP32 swept
+// box (also returned in b) and, with d_m > 0, its exact FP64 swept-box keys.
+// With d_m = 0 the exact box is not staged: the FP32 box ends are within m of
+// the exact ones (m stored per slot), which decides almost every exact box
+// test; the rare undecided pair reads the FP64 values (stage 2).  s: periodic
+// image of the vesicle (applied to both time levels in FP64, as the contact
+// test sees it); off: FP32 offset of the vesicle's frame origin in the pair
+// frame.
 template <bool MIXED, bool DM>
 __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int64_t base, const float* fp, int nv,
                                            int vid, int k, const int* s, const double* sh, const float* off, float dx,
-                                           float* b, double pad, float padf, const float* org, bool f32keys) {
+                                           float* b, double pad, float padf, const float* org) {
   int v = vid >= 0 ? vid : 0;
   S.vid[k] = vid;
-  double x0[3], x1[3];
   float4 fx = ((const float4*)fp)[2 * v], fd = ((const float4*)fp)[2 * v + 1];
   float xf[3], df[3];
   float f0[3] = {fx.x, fx.y, fx.z}, f1[3] = {fd.x, fd.y, fd.z};
-  if (MIXED) {   // the staging holds the FP32 vertices themselves
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      xf[c] = f0[c] - org[c];   // one rounding, as the FP64 form's staging
-      df[c] = f1[c] - f0[c];
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      x0[c] = vtx<MIXED>(a.X, (size_t)base + (size_t)c * nv + v);
-      x1[c] = vtx<MIXED>(a.X, (size_t)base + (size_t)(3 + c) * nv + v);
-      xf[c] = c == 0 ? fx.x : c == 1 ? fx.y : fx.z;
-      df[c] = c == 0 ? fd.x : c == 1 ? fd.y : fd.z;
-    }
-  }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    if (MIXED && f32keys) {
-      // FP32 vertices, no periodic image and no widening on either side: the
-      // exact box ends are FP32 values, ordered by their int images (the
-      // FP64 keys order the same values the same way)
-      S.key[c][k] = fkey32(fminf(f0[c], f1[c]));
-      S.key[3 + c][k] = fkey32(fmaxf(f0[c], f1[c]));
+    if (MIXED) {   // the staging holds the FP32 vertices themselves
+      xf[c] = f0[c] - org[c];   // one rounding, as the FP64 form's staging
+      df[c] = f1[c] - f0[c];
     } else {
-    double p0 = MIXED ? (double)f0[c] : x0[c], p1 = MIXED ? (double)f1[c] : x1[c];
-    if (s[c] != 0) { p0 = p0 + sh[c]; p1 = p1 + sh[c]; }
-    long long k0 = dkey(p0), k1 = dkey(p1);
-    if (DM && pad > 0.0) {   // d_m > 0: this side's boxes widened by d_m (FP64, as computed)
-      double lo = k0 < k1 ? p0 : p1, hi = k0 < k1 ? p1 : p0;
-      S.key[c][k] = dkey(__dsub_rn(lo, pad));
-      S.key[3 + c][k] = dkey(__dadd_rn(hi, pad));
-    } else {
-      S.key[c][k] = k0 < k1 ? k0 : k1;
-      S.key[3 + c][k] = k0 < k1 ? k1 : k0;
+      xf[c] = f0[c];
+      df[c] = f1[c];
     }
+  }
+  if (DM) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double p0 = MIXED ? (double)f0[c] : vtx<MIXED>(a.X, (size_t)base + (size_t)c * nv + v);
+      double p1 = MIXED ? (double)f1[c] : vtx<MIXED>(a.X, (size_t)base + (size_t)(3 + c) * nv + v);
+      if (s[c] != 0) { p0 = p0 + sh[c]; p1 = p1 + sh[c]; }
+      long long k0 = dkey(p0), k1 = dkey(p1);
+      if (pad > 0.0) {   // d_m > 0: this side's boxes widened by d_m (FP64, as computed)
+        double lo = k0 < k1 ? p0 : p1, hi = k0 < k1 ? p1 : p0;
+        S.key[c][k] = dkey(__dsub_rn(lo, pad));
+        S.key[3 + c][k] = dkey(__dadd_rn(hi, pad));
+      } else {
+        S.key[c][k] = k0 < k1 ? k0 : k1;
+        S.key[3 + c][k] = k0 < k1 ? k1 : k0;
+      }
     }
+  }
+  float mmax = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
     float x = xf[c] + off[c], d = df[c];
     S.x[c][k] = x;
     S.d[c][k] = d;
     float m = dx + 4.7683716e-7f * (fabsf(x) + fabsf(d));  // 2^-21 (|x| + |d|)
+    mmax = fmaxf(mmax, m);
     if (DM) m = __fadd_ru(m, padf);                        // + d_m
     float lo = vid >= 0 ? fminf(x, x + d) - m : INFINITY;
     float hi = vid >= 0 ? fmaxf(x, x + d) + m : -INFINITY;
@@ -254,6 +255,7 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
     b[c] = lo;
     b[3 + c] = hi;
   }
+  if (!DM) S.m[k] = mmax;
 }
 
 // Lane -> slot of the packed staging and culling: lanes 0-14 hold the 15 grid
@@ -285,7 +287,6 @@ __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const 
   int nbcA = stiv_ncol_blocks(PA), nbcB = stiv_ncol_blocks(PB);
   int IA = pa / nbcA, JA = pa % nbcA, IB = pb / nbcB, JB = pb % nbcB;
   bool fA = IA == 0, lA = IA == stiv_nband_blocks(PA) - 1, fB = IB == 0, lB = IB == stiv_nband_blocks(PB) - 1;
-  bool f32keys = MIXED && !DM && code == 13;   // both patches in one key space: unshifted, unwidened
   // this lane's side: shift, frame offset, widening and origin of its vesicle
   auto stage_one = [&](bool onB, int k, float* b) {
     int P = onB ? PB : PA, I = onB ? IB : IA, J = onB ? JB : JA;
@@ -302,7 +303,7 @@ __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const 
     int vid = slot_vid(k, I * STIV_BR, J * STIV_BC, 2 * P, P, f, l);
     stage_slot<MIXED, DM>(onB ? ws.B : ws.A, a, onB ? pi.voff_j : pi.voff_i, a.fprep + (size_t)v * a.fstride,
                           stiv_nverts(P), vid, k, sh, shd, off, dx, b, onB ? a.dm : 0.0,
-                          onB ? __double2float_ru(a.dm) : 0.0f, org, f32keys);
+                          onB ? __double2float_ru(a.dm) : 0.0f, org);
   };
   float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
   bool onB;
@@ -1265,10 +1266,44 @@ __device__ __forceinline__ void load_f32(const int* sl, int kind, const PatchSm*
   }
 }
 
+// The exact FP64 swept-box test of a queued primitive pair from the vertex
+// values themselves (FP64, or the FP32 values widened), the second vesicle's
+// points at the pair's periodic image (added in FP64): the test the staged
+// order keys perform, for the rare pair whose FP32 boxes do not decide it.
+template <bool MIXED>
+__device__ __noinline__ bool exact_box_hit(const narrow_args& a, int r, int kind, const PatchSm* SA, const PatchSm* SB,
+                                           const int* sl) {
+  const stiv_pair_info& pi = a.pinfo[r];
+  int code = pi.code;
+  int sB[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
+  int na = kind == 2 ? 2 : 1;
+  double lo[2][3], hi[2][3];
+  for (int side = 0; side < 2; ++side)
+    for (int c = 0; c < 3; ++c) { lo[side][c] = INFINITY; hi[side][c] = -INFINITY; }
+  for (int q = 0; q < 4; ++q) {
+    const PatchSm* S = q < na ? SA : SB;
+    bool onB = (q < na) == (kind == 1);   // the point belongs to vesicle j (patch B)
+    int side = q < na ? 0 : 1;
+    int v = S->vid[sl[q]];
+    int P = onB ? (pi.Pij >> 16) : (pi.Pij & 0xFFFF);
+    int nv = stiv_nverts(P);
+    size_t vb = (size_t)(onB ? pi.voff_j : pi.voff_i) + v;
+    for (int c = 0; c < 3; ++c) {
+      double p0 = vtx<MIXED>(a.X, vb + (size_t)c * nv), p1 = vtx<MIXED>(a.X, vb + (size_t)(3 + c) * nv);
+      if (onB && sB[c] != 0) { double shc = sB[c] * a.L[c]; p0 = p0 + shc; p1 = p1 + shc; }
+      lo[side][c] = fmin(lo[side][c], fmin(p0, p1));
+      hi[side][c] = fmax(hi[side][c], fmax(p0, p1));
+    }
+  }
+  bool hit = true;
+  for (int c = 0; c < 3; ++c) hit = hit && lo[0][c] <= hi[1][c] && lo[1][c] <= hi[0][c];
+  return hit;
+}
+
 // Stage 2 (exact box) and 3a (Bernstein) on up to n entries of q1; survivors
 // go to the global list of stage 3b (of stage 4 when the FP32 rejection is
 // off) as descriptors.
-template <bool DM>
+template <bool MIXED, bool DM>
 __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, const narrow_args& a,
                                           long long& nprim) {
   bool keep = false;
@@ -1278,15 +1313,39 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
     int kind, x, y, sl[4];
     const PatchSm *SA, *SB;
     entry_slots(ws, e, kind, x, y, sl, SA, SB);
-    // exact FP64 swept-box overlap (order keys)
+    // exact FP64 swept-box overlap
     int na = kind == 2 ? 2 : 1;
     bool hit = true;
-    for (int c = 0; c < 3; ++c) {
-      long long alo = SA->key[c][sl[0]], ahi = SA->key[3 + c][sl[0]];
-      if (na == 2) { alo = min(alo, SA->key[c][sl[1]]); ahi = max(ahi, SA->key[3 + c][sl[1]]); }
-      long long blo = SB->key[c][sl[na]], bhi = SB->key[3 + c][sl[na]];
-      for (int q = na + 1; q < 4; ++q) { blo = min(blo, SB->key[c][sl[q]]); bhi = max(bhi, SB->key[3 + c][sl[q]]); }
-      hit = hit && alo <= bhi && blo <= ahi;
+    if (DM) {   // order keys of the staged exact boxes
+      for (int c = 0; c < 3; ++c) {
+        long long alo = SA->key[c][sl[0]], ahi = SA->key[3 + c][sl[0]];
+        if (na == 2) { alo = min(alo, SA->key[c][sl[1]]); ahi = max(ahi, SA->key[3 + c][sl[1]]); }
+        long long blo = SB->key[c][sl[na]], bhi = SB->key[3 + c][sl[na]];
+        for (int q = na + 1; q < 4; ++q) { blo = min(blo, SB->key[c][sl[q]]); bhi = max(bhi, SB->key[3 + c][sl[q]]); }
+        hit = hit && alo <= bhi && blo <= ahi;
+      }
+    } else {
+      // Each staged FP32 box end lies within m of the exact FP64 box end of
+      // its slot (in the pair frame), so a slot's exact box contains its
+      // FP32 box shrunk by 2m at each end.  If the shrunk boxes of the two
+      // primitives overlap on every axis (boxes shrunk by 3 M, M the largest
+      // m of the primitive's slots, which also covers the rounding of the
+      // shrinking), the exact boxes overlap; the pair came through the
+      // outward boxes of stage 1, so only the pairs in between need the exact
+      // test, on the FP64 values.
+      float ma = SA->m[sl[0]], mb = SB->m[sl[na]];
+      if (na == 2) ma = fmaxf(ma, SA->m[sl[1]]);
+      for (int q = na + 1; q < 4; ++q) mb = fmaxf(mb, SB->m[sl[q]]);
+      float gap = 3.0f * (ma + mb);
+      bool sure = true;
+      for (int c = 0; c < 3; ++c) {
+        float alo = SA->lo[c][sl[0]], ahi = SA->hi[c][sl[0]];
+        if (na == 2) { alo = fminf(alo, SA->lo[c][sl[1]]); ahi = fmaxf(ahi, SA->hi[c][sl[1]]); }
+        float blo = SB->lo[c][sl[na]], bhi = SB->hi[c][sl[na]];
+        for (int q = na + 1; q < 4; ++q) { blo = fminf(blo, SB->lo[c][sl[q]]); bhi = fmaxf(bhi, SB->hi[c][sl[q]]); }
+        sure = sure && alo + gap <= bhi && blo + gap <= ahi;
+      }
+      if (!sure) hit = exact_box_hit<MIXED>(a, r, kind, SA, SB, sl);
     }
     if (hit) {
       ++nprim;
@@ -1323,7 +1382,7 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
 
 // Queue the hits of one stage-1 test (n1: the queue length, the same in every
 // lane); 32 queued entries go through stages 2 and 3a.
-template <bool DM>
+template <bool MIXED, bool DM>
 __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, int lane, int r, const narrow_args& a,
                                         long long& nprim, int& n1) {
   unsigned m = __ballot_sync(0xffffffffu, hit);
@@ -1332,7 +1391,7 @@ __device__ __forceinline__ void enqueue(WarpSm& ws, bool hit, unsigned entry, in
   n1 += __popc(m);
   if (n1 >= 32) {
     __syncwarp();
-    stage_filter<DM>(ws, 32, lane, r, a, nprim);
+    stage_filter<MIXED, DM>(ws, 32, lane, r, a, nprim);
     unsigned rest = (lane + 32 < n1) ? ws.q1[lane + 32] : 0;
     __syncwarp();
     if (lane + 32 < n1) ws.q1[lane] = rest;
@@ -1383,7 +1442,7 @@ __global__ void __launch_bounds__(NW * 32, 3) narrow_kernel(narrow_args a) {
           float4 lo = V.vlo[xk], hi = V.vhi[xk];
           float vb[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
           bool hit = valid && fbox_hit(vb, tb);
-          enqueue<DM>(ws, hit, ((unsigned)dir << 16) | ((unsigned)V.vf[xk] << 8) | (unsigned)y, lane, r, a, nprim, n1);
+          enqueue<MIXED, DM>(ws, hit, ((unsigned)dir << 16) | ((unsigned)V.vf[xk] << 8) | (unsigned)y, lane, r, a, nprim, n1);
         }
       }
     }
@@ -1399,12 +1458,12 @@ __global__ void __launch_bounds__(NW * 32, 3) narrow_kernel(narrow_args a) {
           float4 lo = ws.elo[xk], hi = ws.ehi[xk];
           float ab[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
           bool hit = valid && fbox_hit(ab, eb);
-          enqueue<DM>(ws, hit, (2u << 16) | ((unsigned)ws.A.ef[xk] << 8) | (unsigned)y, lane, r, a, nprim, n1);
+          enqueue<MIXED, DM>(ws, hit, (2u << 16) | ((unsigned)ws.A.ef[xk] << 8) | (unsigned)y, lane, r, a, nprim, n1);
         }
       }
     }
     __syncwarp();
-    if (n1 > 0) stage_filter<DM>(ws, n1, lane, r, a, nprim);
+    if (n1 > 0) stage_filter<MIXED, DM>(ws, n1, lane, r, a, nprim);
     item = __shfl_sync(0xffffffffu, next, 0);
   }
   for (int off = 16; off > 0; off >>= 1) nprim += __shfl_down_sync(0xffffffffu, nprim, off);

@@ -129,7 +129,7 @@ struct detect_ws {
   unsigned long long* seg2;  // [C]
   int32_t* tmp_i32;      // [C] temporaries for the contact permutation
   double* tmp_f64;       // [3C]
-  int64_t* ctr;          // [16] device counters
+  int64_t* ctr;          // [32] device counters
   void* sort_scratch;
   size_t sort_scratch_bytes;
   int64_t R, Q, W, C;
