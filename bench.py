@@ -49,11 +49,11 @@ NARROW_SRC = os.path.join(ROOT, "paper_1812_04719_gb300", "csrc", "narrow.cu")
 # csrc/narrow.cu differs from the captured source (SHA-256 prefix), the
 # instruction roofline and the traffic are reported as null.
 NARROW_NCU = {
-    "src_sha256": "bd6f0441d7bd9250",
-    # 117701884 inst, 19756800 + 934144 B over 44989 patch pairs
-    "fp64": {"inst_per_patch_pair": 2616.23, "dram_bytes_per_patch_pair": 459.91},
-    # 115322204 inst, 7646464 + 708608 B over 44988 patch pairs
-    "mixed": {"inst_per_patch_pair": 2563.40, "dram_bytes_per_patch_pair": 185.72},
+    "src_sha256": "2dd4c40ecb93dc0c",
+    # 108696210 inst, 8429568 + 982016 B over 44989 patch pairs
+    "fp64": {"inst_per_patch_pair": 2416.06, "dram_bytes_per_patch_pair": 209.19},
+    # 110544262 inst, 8447744 + 1272320 B over 44988 patch pairs
+    "mixed": {"inst_per_patch_pair": 2457.20, "dram_bytes_per_patch_pair": 216.06},
 }
 ISSUE_PER_SM_CLK = 4   # warp instructions an SM can issue per clock (4 schedulers)
 METRIC = "vesicle-steps/s of detect+V+∇V at p=16→32, 58% vf; % of roofline vs FP64 form"
