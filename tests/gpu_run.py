@@ -1,5 +1,6 @@
-"""Test helper: run the CUDA path through the C-ABI binding and bring results
-to the host as numpy arrays.  Test infrastructure only."""
+"""Test helpers: run the CUDA path through the C-ABI binding and bring results
+to the host as numpy arrays; run the oracle (passed in) over a whole scene and
+compare whole contact lists.  Test infrastructure only."""
 import numpy as np
 import torch
 
@@ -51,3 +52,35 @@ def verts_list(sc, flat):
 def gpu_pairs_rows(g):
     sv = S.shift_vec(g["shift"])
     return np.concatenate([g["i"][:, None], g["j"][:, None], sv], axis=1).astype(np.int32)
+
+
+def bits(x):
+    return np.ascontiguousarray(x, dtype=np.float64).view(np.int64)
+
+
+def oracle_scene(orc, sc, flat, grad_wrt="X1"):
+    Xs = verts_list(sc, flat)
+    boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
+    pairs = orc.candidate_pairs(boxes, sc.L)
+    c = orc.contacts(sc.P, Xs, pairs, sc.L, sc.eps * sc.dt, grad=True, grad_wrt=grad_wrt)
+    c["pairs"] = pairs
+    return c
+
+
+def assert_whole_list(g, c):
+    assert g["counts"][S.C_STATUS] == 0
+    assert np.array_equal(gpu_pairs_rows(g), c["pairs"])
+    n = len(c["pair"])
+    assert n > 500_000 and len(g["pair"]) == n
+    for k in ("pair", "type", "a", "b"):
+        assert np.array_equal(g[k], c[k]), k
+    assert np.array_equal(bits(g["tau"]), bits(c["tau"]))
+    assert np.array_equal(bits(g["w"]), bits(c["w"]))
+    assert np.all(np.abs(g["V"] - c["V"]) <= 1e-10 * np.abs(c["V"]))
+    assert np.all(np.abs(g["V_pair"] - c["V_pair"]) <= 1e-10 * np.abs(c["V_pair"]))
+    scale = np.abs(c["grad"]).reshape(n, -1).max(axis=1)
+    err = np.abs(g["grad"] - c["grad"]).reshape(n, -1).max(axis=1)
+    assert np.all(err <= 1e-9 * scale)
+    assert np.array_equal(g["gves"], c["gves"]) and np.array_equal(g["gvid"], c["gvid"])
+    assert g["counts"][S.C_PRIM] == c["counts"][1]
+    assert g["counts"][S.C_DEGEN] == c["counts"][2]

@@ -29,7 +29,7 @@ import torch
 from paper_1812_04719_gb300 import accuracy as A
 from paper_1812_04719_gb300 import scenegen as G
 from paper_1812_04719_gb300 import stiv as S
-from tests.gpu_run import gpu_pairs_rows, verts_list
+from tests.gpu_run import assert_whole_list, oracle_scene
 from tests.oracle_pool import oracle_vertices
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -63,34 +63,6 @@ def replay(eng, ds, upsample, replays=3):
     out = {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in r.items()}
     out["verts"] = ds.verts.double().cpu().numpy()
     return out
-
-
-def oracle_scene(orc, sc, flat, grad_wrt="X1"):
-    Xs = verts_list(sc, flat)
-    boxes = np.stack([orc.vesicle_box(X, sc.d_m) for X in Xs])
-    pairs = orc.candidate_pairs(boxes, sc.L)
-    c = orc.contacts(sc.P, Xs, pairs, sc.L, sc.eps * sc.dt, grad=True, grad_wrt=grad_wrt)
-    c["pairs"] = pairs
-    return c
-
-
-def assert_whole_list(g, c):
-    assert g["counts"][S.C_STATUS] == 0
-    assert np.array_equal(gpu_pairs_rows(g), c["pairs"])
-    n = len(c["pair"])
-    assert n > 500_000 and len(g["pair"]) == n
-    for k in ("pair", "type", "a", "b"):
-        assert np.array_equal(g[k], c[k]), k
-    assert np.array_equal(bits(g["tau"]), bits(c["tau"]))
-    assert np.array_equal(bits(g["w"]), bits(c["w"]))
-    assert np.all(np.abs(g["V"] - c["V"]) <= 1e-10 * np.abs(c["V"]))
-    assert np.all(np.abs(g["V_pair"] - c["V_pair"]) <= 1e-10 * np.abs(c["V_pair"]))
-    scale = np.abs(c["grad"]).reshape(n, -1).max(axis=1)
-    err = np.abs(g["grad"] - c["grad"]).reshape(n, -1).max(axis=1)
-    assert np.all(err <= 1e-9 * scale)
-    assert np.array_equal(g["gves"], c["gves"]) and np.array_equal(g["gvid"], c["gvid"])
-    assert g["counts"][S.C_PRIM] == c["counts"][1]
-    assert g["counts"][S.C_DEGEN] == c["counts"][2]
 
 
 @pytest.fixture(scope="module")

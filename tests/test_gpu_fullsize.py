@@ -5,16 +5,17 @@ step).  The upsampled vertices are compared with the oracle's synthesis; the
 detection is then replayed on the oracle's vertices, and its whole
 candidate-pair list is compared with the oracle's all-pairs box test bit for
 bit; contacts, volumes and gradient rows are compared on a sample of vesicle
-pairs that the oracle recomputes one by one (960 of the 4096 workload's
-candidate pairs; the 1440 workload's whole lists are in
-test_gpu_fulllist.py)."""
+pairs that the oracle recomputes one by one.  The 4096 workload's whole
+contact lists are compared in both forms (test_whole_lists_4096, about a
+minute and a half of the oracle on 16 host cores per form); the 1440
+workload's are in test_gpu_fulllist.py."""
 import numpy as np
 import pytest
 import torch
 
 from paper_1812_04719_gb300 import scenegen as G
 from paper_1812_04719_gb300 import stiv as S
-from tests.gpu_run import gpu_pairs_rows, run_gpu_on, verts_list
+from tests.gpu_run import assert_whole_list, gpu_pairs_rows, oracle_scene, run_gpu_on, verts_list
 from tests.oracle_pool import oracle_vertices
 
 pytestmark = pytest.mark.gpu
@@ -81,13 +82,7 @@ def test_sampled_pairs_contacts_volumes_gradients(orc, full):
     rng = np.random.default_rng(11)
     hit = np.nonzero(g["V_pair"] > 0)[0]
     miss = np.nonzero(g["V_pair"] == 0)[0]
-    # the 1440 workload's whole lists are compared in test_gpu_fulllist.py;
-    # the 4096 workload (545M exact-box pairs) is sampled: 720 interfering
-    # and 240 other candidate pairs of its 19,922 (about 90 s of the oracle
-    # on 16 host cores)
-    nh, nm = (24, 8) if sc.n == 1440 else (720, 240)
-    sample = np.sort(np.concatenate([rng.choice(hit, min(nh, len(hit)), replace=False),
-                                     rng.choice(miss, min(nm, len(miss)), replace=False)]))
+    sample = np.sort(np.concatenate([rng.choice(hit, 24, replace=False), rng.choice(miss, 8, replace=False)]))
     c = orc.contacts(sc.P, Xs, rows[sample], sc.L, sc.eps * sc.dt, grad=True)
     n_checked = 0
     for k, r in enumerate(sample):
@@ -171,3 +166,32 @@ def test_dm_sampled_pairs_1440(orc):
             assert np.all(err <= 1e-9 * scale + 1e-300)
         n_checked += int(gm.sum())
     assert n_checked > 500
+
+
+@pytest.fixture(scope="module")
+def scene4096():
+    sc = G.scene_4096()
+    return sc, oracle_vertices(sc)
+
+
+@pytest.fixture(scope="module")
+def oracle4096(orc, scene4096):
+    sc, Xo = scene4096
+    return oracle_scene(orc, sc, Xo)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", [S.STIV_FP64, S.STIV_MIXED], ids=["fp64", "mixed"])
+def test_whole_lists_4096(orc, scene4096, oracle4096, prec):
+    """The batched workload of uneven orders (4096 vesicles at 40%, p in {8,
+    12, 16}, 545M exact-box primitive pairs, 1.33M contacts), graph replay on
+    the oracle's vertices (FP64, or rounded to FP32 for the MIXED form):
+    every candidate pair, every contact (keys, contact time and weights bit
+    for bit), V per contact and per pair within 1e-10, every gradient row
+    within 1e-9, the exact-box pair count, against the oracle's Alg. 2 over
+    the whole scene on the same values."""
+    sc, Xo = scene4096
+    g = run_gpu_on(sc, Xo, precision=prec, grad=True, use_graph=True, replays=3, pair_cap=1 << 15,
+                   contact_cap=1 << 21)
+    c = oracle4096 if prec == S.STIV_FP64 else oracle_scene(orc, sc, g["verts"])
+    assert_whole_list(g, c)
