@@ -401,8 +401,10 @@ __global__ void scatter_grad_kernel(const int64_t* counts, int64_t cap, const in
   }
 }
 
-// gcoef = S^T gX for the X1 block; one CTA per vesicle.  S: Legendre step then
-// Fourier step, so S^T: Fourier analysis sums per ring, then Legendre sums.
+// gcoef = S^T gX for the X1 block; one CTA per (vesicle, coordinate field),
+// so that the three fields' phases overlap across CTAs.  S: Legendre step
+// then Fourier step, so S^T: Fourier analysis sums per ring, then Legendre
+// sums.
 struct adj_args {
   const int32_t* p;
   const int64_t* coef_off;
@@ -415,7 +417,7 @@ struct adj_args {
 
 __global__ void __launch_bounds__(256) adjoint_kernel(adj_args a) {
   extern __shared__ double sm[];
-  int v = blockIdx.x;
+  int v = blockIdx.x, f = blockIdx.y;
   if (a.p[v] < 1 || a.p[v] > STIV_MAX_P || !a.leg[a.p[v]]) return;   // order outside [1, p_max]: skipped
   int p = a.p[v], P = 2 * p, nc = (p + 1) * (p + 1), nl = (p + 1) * (p + 2) / 2, ns = 2 * p + 1, W = 2 * P;
   int nv = stiv_nverts(P);
@@ -427,8 +429,8 @@ __global__ void __launch_bounds__(256) adjoint_kernel(adj_args a) {
   const double* L = a.leg[p];
   double* out = a.gcoef + a.coef_off[v];
   int nq = P / 2 + 1;
-  for (int k = threadIdx.x; k < 3 * nc; k += blockDim.x) out[k] = 0.0;  // X0 block
-  for (int f = 0; f < 3; ++f) {
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) out[f * nc + k] = 0.0;  // X0 block, this field
+  {
     for (int k = threadIdx.x; k < nv; k += blockDim.x) G[k] = g[(size_t)f * nv + k];
     __syncthreads();
     // adjoint of the Fourier step.  The forward writes longitudes j, P-j, P+j,
@@ -466,7 +468,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(adj_args a) {
     __syncthreads();
     // adjoint of the Legendre step (all rings, and the poles for m = 0)
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
-      int n = (int)sqrt((double)q); while (n * n > q) --n; while ((n + 1) * (n + 1) <= q) ++n;
+      int n = (int)sqrtf((float)q); while (n * n > q) --n; while ((n + 1) * (n + 1) <= q) ++n;
       int m = q - n * n - n, am = m < 0 ? -m : m;
       int s = m == 0 ? 0 : (m > 0 ? 2 * m - 1 : 2 * am);
       double acc = 0.0;
@@ -477,7 +479,6 @@ __global__ void __launch_bounds__(256) adjoint_kernel(adj_args a) {
       }
       out[3 * nc + f * nc + q] = acc;
     }
-    __syncthreads();
   }
 }
 
@@ -606,7 +607,7 @@ extern "C" int stiv_grad_to_coef(stiv_handle* h, void* stream, int32_t n_ves, in
                                   (size_t)(Pm + 1) * 4 * (Pm / 2 + 1));
   STIV_CUDA(h, cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   STIV_PROF(h, st, "grad_to_coef");
-  adjoint_kernel<<<n_ves, 256, smem, st>>>(a);
+  adjoint_kernel<<<dim3(n_ves, 3), 256, smem, st>>>(a);
   STIV_LAUNCH(h);
   return STIV_OK;
 }
