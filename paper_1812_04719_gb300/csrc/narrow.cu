@@ -603,9 +603,21 @@ __device__ int inside_cert(int kind, const f3* x, const f3* d, float t0, float w
 // Coefficients of the coplanarity cubic in FP32 and a bound E on the error of
 // any value of the cubic (or of its Bernstein coefficients on any sub-interval
 // of [0, 1]) against the exact cubic of the FP64 inputs.  Every coefficient is
-// a sum of <= 18 products of three difference components; A / Ad bound the
-// position / displacement differences, ep / ed the input errors.
+// a sum of triple products u . (v x w) of difference vectors (six terms each);
+// ep / ed bound the input errors of the positions / displacements per
+// component.  Each triple product's error is bounded with the magnitudes of
+// its own three vectors (tp below), so a pair whose displacement differences
+// are small (a primitive moving nearly rigidly) keeps a tight bound.
 struct cubic32 { float k0, k1, k2, k3, E, ed; };
+
+// Error bound of the FP32 triple product u . (v x w) against the exact one:
+// eu, ev, ew bound the component errors of u, v, w; Au, Av, Aw their largest
+// computed components.  For each of the six terms, |xyz - x'y'z'| <=
+// |x - x'| |y'| |z'| + |x| |y - y'| |z'| + |x| |y| |z - z'| with |y'| <= Ay + ey;
+// rr bounds the relative rounding of the FP32 evaluation per term.
+__device__ __forceinline__ float tp_err(float eu, float Au, float ev, float Av, float ew, float Aw, float rr) {
+  return 6.f * (eu * (Av + ev) * (Aw + ew) + Au * ev * (Aw + ew) + Au * Av * ew + rr * Au * Av * Aw);
+}
 
 __device__ __forceinline__ cubic32 cubic_fp32(int kind, const f3* x, const f3* d, float ep) {
   f3 a, b, c, da, db, dc;
@@ -624,18 +636,21 @@ __device__ __forceinline__ cubic32 cubic_fp32(int kind, const f3* x, const f3* d
   r.k1 = fdot(dc, n0) + fdot(c, n1);
   r.k2 = fdot(c, n2) + fdot(dc, n1);
   r.k3 = fdot(dc, n2);
-  float A = fmaxf(amax3(a), fmaxf(amax3(b), amax3(c)));
-  float Ad = fmaxf(amax3(da), fmaxf(amax3(db), amax3(dc)));
+  float Aa = amax3(a), Ab = amax3(b), Ac = amax3(c), Ada = amax3(da), Adb = amax3(db), Adc = amax3(dc);
+  float A = fmaxf(Aa, fmaxf(Ab, Ac)), Ad = fmaxf(Ada, fmaxf(Adb, Adc));
   float Dm = 0.f;
   for (int q = 0; q < 4; ++q) Dm = fmaxf(Dm, amax3(d[q]));
   float ed = 2.0f * U32 * Dm + 1e-12f;           // |d - D| per component (float rounding of X1 - X0)
-  float epd = 2.0f * ep + 2.0f * U32 * A;        // per position-difference component
-  float edd = 2.0f * ed + 2.0f * U32 * Ad;       // per displacement-difference component
+  // per component of each difference: both inputs' errors and the rounding of the difference
+  float ea = 2.0f * ep + 2.0f * U32 * Aa, eb = 2.0f * ep + 2.0f * U32 * Ab, ec = 2.0f * ep + 2.0f * U32 * Ac;
+  float eda = 2.0f * ed + 2.0f * U32 * Ada, edb = 2.0f * ed + 2.0f * U32 * Adb, edc = 2.0f * ed + 2.0f * U32 * Adc;
   float rr = 8.0f * U32;                         // rounding per term
-  float E0 = 6.f * (3.f * epd * A * A + rr * A * A * A);
-  float E1 = 18.f * (edd * A * A + 2.f * epd * Ad * A + rr * Ad * A * A);
-  float E2 = 18.f * (epd * Ad * Ad + 2.f * edd * A * Ad + rr * A * Ad * Ad);
-  float E3 = 6.f * (3.f * edd * Ad * Ad + rr * Ad * Ad * Ad);
+  float E0 = tp_err(ec, Ac, ea, Aa, eb, Ab, rr);                                    // c . (a x b)
+  float E1 = tp_err(edc, Adc, ea, Aa, eb, Ab, rr) + tp_err(ec, Ac, eda, Ada, eb, Ab, rr) +
+             tp_err(ec, Ac, ea, Aa, edb, Adb, rr);                                  // dc.(a x b) + c.(da x b + a x db)
+  float E2 = tp_err(ec, Ac, eda, Ada, edb, Adb, rr) + tp_err(edc, Adc, eda, Ada, eb, Ab, rr) +
+             tp_err(edc, Adc, ea, Aa, edb, Adb, rr);                                // c.(da x db) + dc.(da x b + a x db)
+  float E3 = tp_err(edc, Adc, eda, Ada, edb, Adb, rr);                              // dc . (da x db)
   float S = fabsf(r.k0) + fabsf(r.k1) + fabsf(r.k2) + fabsf(r.k3);
   float M = (A + Ad) * (A + Ad) * (A + Ad);
   r.E = 1.25f * (E0 + E1 + E2 + E3) + 64.f * U32 * S + 1e-12f * 48.f * M;
