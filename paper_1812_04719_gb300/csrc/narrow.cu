@@ -258,6 +258,17 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
   if (!DM) S.m[k] = mmax;
 }
 
+// Bound on the error of a component of the difference of two FP32 frame
+// positions of the same vesicle: each is x = fl(xf + off) with xf the
+// position relative to the vesicle's origin rounded once (|xf| <= R) and off
+// the same float for every point of the vesicle, so off's own error cancels
+// and U32 (|xf1| + |xf2| + |x1| + |x2|) remains; R: the larger vesicle
+// radius bound of the pair, offm: the largest offset component.  It is at
+// most 2 ep (ep = 2^-22 (R_i + R_j + 2 offm)), the bound stage 3a keeps.
+__device__ __forceinline__ float same_side_err(float R, float offm) {
+  return 1.01f * 5.9604645e-8f * (4.0f * R + 2.0f * offm);
+}
+
 // Lane -> slot of the packed staging and culling: lanes 0-14 hold the 15 grid
 // slots of patch A, lanes 15-29 those of patch B, lane 30 A's pole slot and
 // lane 31 B's (a patch touches at most one pole, except at P = 2, where the
@@ -619,7 +630,8 @@ __device__ __forceinline__ float tp_err(float eu, float Au, float ev, float Av, 
   return 6.f * (eu * (Av + ev) * (Aw + ew) + Au * ev * (Aw + ew) + Au * Av * ew + rr * Au * Av * Aw);
 }
 
-__device__ __forceinline__ cubic32 cubic_fp32(int kind, const f3* x, const f3* d, float ep) {
+// es: the error bound of the same-vesicle differences a and b (at most 2 ep).
+__device__ __forceinline__ cubic32 cubic_fp32(int kind, const f3* x, const f3* d, float ep, float es) {
   f3 a, b, c, da, db, dc;
   if (kind == 0) {
     a = fsub(x[2], x[1]); b = fsub(x[3], x[1]); c = fsub(x[0], x[1]);
@@ -642,7 +654,9 @@ __device__ __forceinline__ cubic32 cubic_fp32(int kind, const f3* x, const f3* d
   for (int q = 0; q < 4; ++q) Dm = fmaxf(Dm, amax3(d[q]));
   float ed = 2.0f * U32 * Dm + 1e-12f;           // |d - D| per component (float rounding of X1 - X0)
   // per component of each difference: both inputs' errors and the rounding of the difference
-  float ea = 2.0f * ep + 2.0f * U32 * Aa, eb = 2.0f * ep + 2.0f * U32 * Ab, ec = 2.0f * ep + 2.0f * U32 * Ac;
+  // a and b join points of one vesicle, whose common frame offset cancels in
+  // the difference (es); c joins the two vesicles (2 ep)
+  float ea = es + 2.0f * U32 * Aa, eb = es + 2.0f * U32 * Ab, ec = 2.0f * ep + 2.0f * U32 * Ac;
   float eda = 2.0f * ed + 2.0f * U32 * Ada, edb = 2.0f * ed + 2.0f * U32 * Adb, edc = 2.0f * ed + 2.0f * U32 * Adc;
   float rr = 8.0f * U32;                         // rounding per term
   float E0 = tp_err(ec, Ac, ea, Aa, eb, Ab, rr);                                    // c . (a x b)
@@ -710,8 +724,8 @@ __device__ __forceinline__ bool out_of_band(float c0, float c1, float c2, float 
   return fmin > 0.f && fmin * fmin * (1.f - 1e-5f) > rhs;
 }
 
-__device__ int band_reject(int kind, const f3* x, const f3* d, float ep, float dm) {
-  cubic32 q = cubic_fp32(kind, x, d, ep);
+__device__ int band_reject(int kind, const f3* x, const f3* d, float ep, float es, float dm) {
+  cubic32 q = cubic_fp32(kind, x, d, ep, es);
   float b1 = q.k0 + q.k1 * (1.f / 3.f), b2 = q.k0 + (2.f * q.k1 + q.k2) * (1.f / 3.f), b3 = q.k0 + q.k1 + q.k2 + q.k3;
   if (!certain_sign4(q.k0, b1, b2, b3, q.E)) return 0;
   return out_of_band(q.k0, b1, b2, b3, q.E, band_rhs(kind, x, d, ep, dm, q)) ? 1 : 0;
@@ -1232,7 +1246,7 @@ __device__ __forceinline__ void desc_points(ulonglong2 e, int& r, int& type, int
 
 // FP32 points of a descriptor in the frame of its pair (for stage 3b).
 __device__ __forceinline__ void desc_points_f32(const narrow_args& a, ulonglong2 e, int& kind, f3* xq, f3* dq,
-                                                float& ep) {
+                                                float& ep, float& es) {
   int r, ty, ga, gb, vid[4];
   bool onj[4];
   desc_points(e, r, ty, ga, gb, vid, onj);
@@ -1240,6 +1254,8 @@ __device__ __forceinline__ void desc_points_f32(const narrow_args& a, ulonglong2
   float4 fr = pi->frame;
   int vi = pi->vi, vj = pi->vj;
   ep = fr.w;
+  es = same_side_err(fmaxf(((const float4*)a.vorg)[vi].w, ((const float4*)a.vorg)[vj].w),
+                     fmaxf(fabsf(fr.x), fmaxf(fabsf(fr.y), fabsf(fr.z))));
   kind = ty == 2 ? 1 : 0;
   for (int q = 0; q < 4; ++q) {
     int v = onj[q] ? vj : vi;
@@ -1368,11 +1384,11 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
       if (DM && !a.exact_only) {   // d_m > 0: drop pairs that certainly stay out of the d_m band
         f3 xq[4], dq[4];
         load_f32(sl, kind, SA, SB, xq, dq);
-        keep = !band_reject(kind == 2 ? 1 : 0, xq, dq, ws.dx, (float)a.dm);
+        keep = !band_reject(kind == 2 ? 1 : 0, xq, dq, ws.dx, 2.0f * ws.dx, (float)a.dm);
       } else if (!a.exact_only) {
         f3 xq[4], dq[4];
         load_f32(sl, kind, SA, SB, xq, dq);
-        cubic32 q = cubic_fp32(kind == 2 ? 1 : 0, xq, dq, ws.dx);
+        cubic32 q = cubic_fp32(kind == 2 ? 1 : 0, xq, dq, ws.dx, 2.0f * ws.dx);
         keep = !bernstein_reject(q);
       }
       if (keep) {
@@ -1529,9 +1545,9 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
     if (valid) {
       int kind;
       f3 xq[4], dq[4];
-      float ep;
-      desc_points_f32(a, e, kind, xq, dq, ep);
-      cubic32 q = cubic_fp32(kind, xq, dq, ep);
+      float ep, es;
+      desc_points_f32(a, e, kind, xq, dq, ep, es);
+      cubic32 q = cubic_fp32(kind, xq, dq, ep, es);
       for (int p = 0; p < 4; ++p) {
         W.x[lane][p][0] = xq[p].x; W.x[lane][p][1] = xq[p].y; W.x[lane][p][2] = xq[p].z;
         W.d[lane][p][0] = dq[p].x; W.d[lane][p][1] = dq[p].y; W.d[lane][p][2] = dq[p].z;
