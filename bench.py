@@ -695,6 +695,7 @@ def run_ours(args, rank, world, local):
         eng_dm = S.Stiv.for_scene(sc_dm, precision=prec, pair_cap=8192, contact_cap=1 << 20, device=dev)
         ds_dm = S.DeviceScene.from_scene(sc_dm, precision=prec, device=dev)
         eng_dm.step(ds_dm, grad=True)          # sizes the buffers
+        shapes_dm = None if args.no_autotune else eng_dm.autotune(ds_dm, stream=stream)
         S.stiv_profile(eng_dm.h, True)
         ms_d = []
         prof_d = {}
@@ -714,6 +715,7 @@ def run_ours(args, rank, world, local):
         fp64_dm = prof_d.get("fp64", 0.0)
         dm_rec = {"d_m": dm_val, "ms_per_step": round(float(np.mean(ms_d)), 3), "contacts": int(cdm[S.C_VF] + cdm[S.C_EE]),
                   "fp64_ms": round(fp64_dm, 3),
+                  "piece_levels": shapes_dm["piece_levels"] if shapes_dm else None,
                   "fp64_frac": round(float(cdm[S.C_FLOPS]) / (fp64_dm * 1e-3) / 1e9 / peaks["fp64_gflops"], 3)
                   if fp64_dm > 0 else None}
         eng_dm.close()

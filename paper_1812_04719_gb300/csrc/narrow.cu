@@ -529,13 +529,12 @@ constexpr float U32 = 5.9604645e-8f;   // 2^-24, unit roundoff of float
 // interval (plus the input error 2 eg), R_i = h |gd_i| (half width times the
 // rate); the norms of the vectors an inside test shares between its forms
 // are taken once.
-__device__ __forceinline__ int form_sign_m(f3 g0, f3 g1, f3 g2, f3 g3, const float* M, const float* R, float eg) {
+__device__ __forceinline__ int form_sign_m(f3 g0, f3 g1, f3 g2, f3 g3, const float* M, const float* R, const float* G) {
   float val = fdot(fcross(g0, g1), fcross(g2, g3));
   float p01 = M[0] * M[1], p23 = M[2] * M[3];
   float prod = p01 * p23;
-  float var = R[0] * M[1] * p23 + M[0] * R[1] * p23 + p01 * R[2] * M[3] + p01 * M[2] * R[3];
-  float inp = 2.0f * eg * (M[1] * p23 + M[0] * p23 + p01 * M[3] + p01 * M[2]);
-  float rad = (var + inp + 64.0f * U32 * prod) * 1.001f;
+  float var = (R[0] + G[0]) * M[1] * p23 + M[0] * (R[1] + G[1]) * p23 + p01 * (R[2] + G[2]) * M[3] + p01 * M[2] * (R[3] + G[3]);
+  float rad = (var + 64.0f * U32 * prod) * 1.001f;
   if (val > rad) return 1;
   if (val < -rad) return -1;
   return 0;
@@ -549,39 +548,42 @@ __device__ __forceinline__ int form_sign_m(f3 g0, f3 g1, f3 g2, f3 g3, const flo
 // (g1 x g2) . (g3 x g4) of linear g: |(g1 x g2) . (g3 x g4)| <= prod |g_i|,
 // so its change over the interval is at most sum_i h |gd_i| prod_{j != i}
 // max |g_j|; form_sign_m certifies its sign.
-__device__ int inside_cert(int kind, const f3* x, const f3* d, float t0, float w, float ep, float ed) {
+__device__ int inside_cert(int kind, const f3* x, const f3* d, float t0, float w, float ep, float ed, float es) {
   float h = 0.5f * w + 1e-6f;           // half width, widened past the FP64 root's last ulp
   float tm = t0 + 0.5f * w;
   f3 P[4];
   for (int q = 0; q < 4; ++q) P[q] = fat(x[q], tm, d[q]);
   float pm = fmaxf(fmaxf(amax3(P[0]), amax3(P[1])), fmaxf(amax3(P[2]), amax3(P[3])));
   float eg = 2.0f * (ep + ed) + 4.0f * U32 * pm;  // per component, differences of positions at tm
-  // vector (position difference at tm, rate) -> M, R of form_sign_m
-  auto mr = [&](f3 gv, f3 gd, float& M, float& R) {
+  float egs = es + 2.0f * ed + 4.0f * U32 * pm;     // the same for two points of one vesicle
+  // vector (position difference at tm, rate) -> M, R, G (2 x its error) of form_sign_m
+  auto mr = [&](f3 gv, f3 gd, float e, float& M, float& R, float& G) {
     R = h * fnorm(gd);
-    M = fnorm(gv) + R + 2.0f * eg;
+    G = 2.0f * e;
+    M = fnorm(gv) + R + G;
   };
   if (kind == 0) {
     // barycentric weight of T_k ~ ((T_{k+2} - T_{k+1}) x (p - T_{k+1})) . n,  n = (T1 - T0) x (T2 - T0)
     f3 t01 = fsub(P[2], P[1]), t02 = fsub(P[3], P[1]), t12 = fsub(P[3], P[2]);
     f3 q0 = fsub(P[0], P[1]), q1 = fsub(P[0], P[2]), q2 = fsub(P[0], P[3]);
-    float Mt01, Rt01, Mt02, Rt02, Mt12, Rt12, Mq0, Rq0, Mq1, Rq1, Mq2, Rq2;
-    mr(t01, fsub(d[2], d[1]), Mt01, Rt01);
-    mr(t02, fsub(d[3], d[1]), Mt02, Rt02);
-    mr(t12, fsub(d[3], d[2]), Mt12, Rt12);
-    mr(q0, fsub(d[0], d[1]), Mq0, Rq0);
-    mr(q1, fsub(d[0], d[2]), Mq1, Rq1);
-    mr(q2, fsub(d[0], d[3]), Mq2, Rq2);
+    float Mt01, Rt01, Mt02, Rt02, Mt12, Rt12, Mq0, Rq0, Mq1, Rq1, Mq2, Rq2, Gs, Gc;
+    mr(t01, fsub(d[2], d[1]), egs, Mt01, Rt01, Gs);
+    mr(t02, fsub(d[3], d[1]), egs, Mt02, Rt02, Gs);
+    mr(t12, fsub(d[3], d[2]), egs, Mt12, Rt12, Gs);
+    mr(q0, fsub(d[0], d[1]), eg, Mq0, Rq0, Gc);
+    mr(q1, fsub(d[0], d[2]), eg, Mq1, Rq1, Gc);
+    mr(q2, fsub(d[0], d[3]), eg, Mq2, Rq2, Gc);
+    float G[4] = {Gs, Gc, Gs, Gs};
     f3 nt02 = {-t02.x, -t02.y, -t02.z};
     // k = 0: (T2 - T1) x (p - T1); k = 1: (T0 - T2) x (p - T2); k = 2: (T1 - T0) x (p - T0)
     float M0[4] = {Mt12, Mq1, Mt01, Mt02}, R0[4] = {Rt12, Rq1, Rt01, Rt02};
-    int sg0 = form_sign_m(t12, q1, t01, t02, M0, R0, eg);
+    int sg0 = form_sign_m(t12, q1, t01, t02, M0, R0, G);
     if (sg0 < 0) return 1;
     float M1[4] = {Mt02, Mq2, Mt01, Mt02}, R1[4] = {Rt02, Rq2, Rt01, Rt02};
-    int sg1 = form_sign_m(nt02, q2, t01, t02, M1, R1, eg);
+    int sg1 = form_sign_m(nt02, q2, t01, t02, M1, R1, G);
     if (sg1 < 0) return 1;
     float M2[4] = {Mt01, Mq0, Mt01, Mt02}, R2[4] = {Rt01, Rq0, Rt01, Rt02};
-    int sg2 = form_sign_m(t01, q0, t01, t02, M2, R2, eg);
+    int sg2 = form_sign_m(t01, q0, t01, t02, M2, R2, G);
     if (sg2 < 0) return 1;
     return (sg0 > 0 && sg1 > 0 && sg2 > 0) ? 2 : 0;
   }
@@ -590,23 +592,24 @@ __device__ int inside_cert(int kind, const f3* x, const f3* d, float t0, float w
   // u - 1 ~ ((q1 - p0) x (p1 - p0)) . m   (each divided by |m|^2)
   f3 e1v = fsub(P[1], P[0]), e2v = fsub(P[3], P[2]);
   f3 a0 = fsub(P[2], P[0]), a1 = fsub(P[2], P[1]), a3 = fsub(P[3], P[0]);
-  float Me1, Re1, Me2, Re2, Ma0, Ra0, Ma1, Ra1, Ma3, Ra3;
-  mr(e1v, fsub(d[1], d[0]), Me1, Re1);
-  mr(e2v, fsub(d[3], d[2]), Me2, Re2);
-  mr(a0, fsub(d[2], d[0]), Ma0, Ra0);
-  mr(a1, fsub(d[2], d[1]), Ma1, Ra1);
-  mr(a3, fsub(d[3], d[0]), Ma3, Ra3);
+  float Me1, Re1, Me2, Re2, Ma0, Ra0, Ma1, Ra1, Ma3, Ra3, Gs, Gc;
+  mr(e1v, fsub(d[1], d[0]), egs, Me1, Re1, Gs);
+  mr(e2v, fsub(d[3], d[2]), egs, Me2, Re2, Gs);
+  mr(a0, fsub(d[2], d[0]), eg, Ma0, Ra0, Gc);
+  mr(a1, fsub(d[2], d[1]), eg, Ma1, Ra1, Gc);
+  mr(a3, fsub(d[3], d[0]), eg, Ma3, Ra3, Gc);
+  float G[4] = {Gc, Gs, Gs, Gs};
   float Ms[4] = {Ma0, Me2, Me1, Me2}, Rs[4] = {Ra0, Re2, Re1, Re2};
-  int s0 = form_sign_m(a0, e2v, e1v, e2v, Ms, Rs, eg);
+  int s0 = form_sign_m(a0, e2v, e1v, e2v, Ms, Rs, G);
   if (s0 < 0) return 1;
   float Ms1[4] = {Ma1, Me2, Me1, Me2}, Rs1[4] = {Ra1, Re2, Re1, Re2};
-  int s1 = form_sign_m(a1, e2v, e1v, e2v, Ms1, Rs1, eg);
+  int s1 = form_sign_m(a1, e2v, e1v, e2v, Ms1, Rs1, G);
   if (s1 > 0) return 1;
   float Mu[4] = {Ma0, Me1, Me1, Me2}, Ru[4] = {Ra0, Re1, Re1, Re2};
-  int u0 = form_sign_m(a0, e1v, e1v, e2v, Mu, Ru, eg);
+  int u0 = form_sign_m(a0, e1v, e1v, e2v, Mu, Ru, G);
   if (u0 < 0) return 1;
   float Mu1[4] = {Ma3, Me1, Me1, Me2}, Ru1[4] = {Ra3, Re1, Re1, Re2};
-  int u1 = form_sign_m(a3, e1v, e1v, e2v, Mu1, Ru1, eg);
+  int u1 = form_sign_m(a3, e1v, e1v, e2v, Mu1, Ru1, G);
   if (u1 > 0) return 1;
   return (s0 > 0 && s1 < 0 && u0 > 0 && u1 < 0) ? 2 : 0;
 }
@@ -1516,7 +1519,7 @@ static_assert(NPIECE << (NLEVEL - 1) <= 1024, "piece index fits 10 bits");
 
 struct PieceWarp {
   float x[32][4][3], d[32][4][3];
-  float k[32][4], E[32], ep[32], ed[32];
+  float k[32][4], E[32], ep[32], ed[32], es[32];
   float rhs[32];   // d_m > 0: band_rhs of each pair
   int kind[32], fail[32];
   unsigned short task[MAXTASK], task2[MAXTASK];
@@ -1553,7 +1556,7 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
         W.d[lane][p][0] = dq[p].x; W.d[lane][p][1] = dq[p].y; W.d[lane][p][2] = dq[p].z;
       }
       W.k[lane][0] = q.k0; W.k[lane][1] = q.k1; W.k[lane][2] = q.k2; W.k[lane][3] = q.k3;
-      W.E[lane] = q.E; W.ep[lane] = ep; W.ed[lane] = q.ed; W.kind[lane] = kind;
+      W.E[lane] = q.E; W.ep[lane] = ep; W.ed[lane] = q.ed; W.es[lane] = es; W.kind[lane] = kind;
       if (DM) W.rhs[lane] = band_rhs(kind, xq, dq, ep, (float)a.dm, q);
       if (fabsf(q.k0) <= q.E && fabsf(q.k1) <= q.E && fabsf(q.k2) <= q.E && fabsf(q.k3) <= q.E) {
         W.fail[lane] = 1;   // may vanish identically: FP64 decides (degenerate)
@@ -1616,7 +1619,7 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
               xq[q] = {W.x[owner][q][0], W.x[owner][q][1], W.x[owner][q][2]};
               dq[q] = {W.d[owner][q][0], W.d[owner][q][1], W.d[owner][q][2]};
             }
-            int res = inside_cert(W.kind[owner], xq, dq, tl, w, W.ep[owner], W.ed[owner]);
+            int res = inside_cert(W.kind[owner], xq, dq, tl, w, W.ep[owner], W.ed[owner], W.es[owner]);
             if (res == 2) {
               W.fail[owner] = 1;                       // a contact: the FP64 test decides its time
             } else if (res == 0) {
