@@ -13,8 +13,9 @@
 //   pieces_kernel (stage 3b) and fp64_kernel (stage 4) work on those lists,
 //     so that every stage runs on full warps.  The stages:
 //     1. FP32 swept-box test (conservative: never drops an overlapping pair);
-//     2. the exact FP64 swept-box test, on integer order keys of the FP64 bit
-//        patterns (no FP64 instruction; counts the pairs tested);
+//     2. the exact FP64 swept-box test (counts the pairs tested), decided
+//        from the FP32 boxes and their error bound, on the FP64 values only
+//        for the pairs those do not decide;
 //     3. certified FP32 rejection: a pair is dropped only when error-bounded
 //        FP32 arithmetic proves that the FP64 test below cannot report a
 //        contact (Bernstein bound: no root of the cubic in [0,1]; or, on every
@@ -52,10 +53,7 @@ static_assert(NS <= 32, "one lane per vertex slot");
 static_assert(STIV_BR == 2 && STIV_BC % 2 == 0, "patches tile every even-order grid exactly");
 
 struct PatchSm {
-  union {
-    long long key[6][NS];          // d_m > 0: exact swept box of each slot, order keys of lo xyz, hi xyz
-    float m[NS];                   // d_m = 0: bound on the FP32 error of the slot's box ends
-  };
+  float m[NS];                     // bound on the FP32 error of the slot's box ends (before any widening)
   float x[3][NS], d[3][NS];        // FP32: X0 - origin of vesicle i, X1 - X0
   float lo[3][NS], hi[3][NS];      // FP32 conservative swept box of each slot (frame of vesicle i)
   int vid[NS];                     // global vertex id of each slot (-1: unused)
@@ -112,14 +110,6 @@ template <bool MIXED>
 __device__ __forceinline__ double vtx(const void* X, size_t i) {
   if (MIXED) return (double)((const float*)X)[i];
   return ((const double*)X)[i];
-}
-
-// Order-preserving integer key of a double (-0.0 folded onto +0.0): for finite
-// a, b:  a <= b  <=>  key(a) <= key(b).
-__device__ __forceinline__ long long dkey(double v) {
-  long long b = __double_as_longlong(v);
-  if (b == (long long)0x8000000000000000ull) b = 0;
-  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
 }
 
 // ---------------------------------------------------------------------------
@@ -195,18 +185,15 @@ __device__ __forceinline__ int fkey32(float f) {
 }
 __device__ __forceinline__ float fkey_val(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7FFFFFFF); }
 
-// One vertex slot: FP32 frame coordinates, the slot's conservative FP32 swept
-// box (also returned in b) and, with d_m > 0, its exact FP64 swept-box keys.
-// With d_m = 0 the exact box is not staged: the FP32 box ends are within m of
-// the exact ones (m stored per slot), which decides almost every exact box
-// test; the rare undecided pair reads the FP64 values (stage 2).  s: periodic
-// image of the vesicle (applied to both time levels in FP64, as the contact
-// test sees it); off: FP32 offset of the vesicle's frame origin in the pair
-// frame.
+// One vertex slot: FP32 frame coordinates and the slot's conservative FP32
+// swept box (also returned in b; vesicle j's widened by d_m, rounded up).  The
+// exact box is not staged: the FP32 box ends are within m of the exact ones
+// (m stored per slot), which decides almost every exact box test; the rare
+// undecided pair reads the FP64 values (stage 2).  off: FP32 offset of the
+// vesicle's frame origin in the pair frame.
 template <bool MIXED, bool DM>
-__device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int64_t base, const float* fp, int nv,
-                                           int vid, int k, const int* s, const double* sh, const float* off, float dx,
-                                           float* b, double pad, float padf, const float* org) {
+__device__ __forceinline__ void stage_slot(PatchSm& S, const float* fp, int vid, int k, const float* off, float dx,
+                                           float* b, float padf, const float* org) {
   int v = vid >= 0 ? vid : 0;
   S.vid[k] = vid;
   float4 fx = ((const float4*)fp)[2 * v], fd = ((const float4*)fp)[2 * v + 1];
@@ -220,23 +207,6 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
     } else {
       xf[c] = f0[c];
       df[c] = f1[c];
-    }
-  }
-  if (DM) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double p0 = MIXED ? (double)f0[c] : vtx<MIXED>(a.X, (size_t)base + (size_t)c * nv + v);
-      double p1 = MIXED ? (double)f1[c] : vtx<MIXED>(a.X, (size_t)base + (size_t)(3 + c) * nv + v);
-      if (s[c] != 0) { p0 = p0 + sh[c]; p1 = p1 + sh[c]; }
-      long long k0 = dkey(p0), k1 = dkey(p1);
-      if (pad > 0.0) {   // d_m > 0: this side's boxes widened by d_m (FP64, as computed)
-        double lo = k0 < k1 ? p0 : p1, hi = k0 < k1 ? p1 : p0;
-        S.key[c][k] = dkey(__dsub_rn(lo, pad));
-        S.key[3 + c][k] = dkey(__dadd_rn(hi, pad));
-      } else {
-        S.key[c][k] = k0 < k1 ? k0 : k1;
-        S.key[3 + c][k] = k0 < k1 ? k1 : k0;
-      }
     }
   }
   float mmax = 0.0f;
@@ -255,7 +225,7 @@ __device__ __forceinline__ void stage_slot(PatchSm& S, const narrow_args& a, int
     b[c] = lo;
     b[3 + c] = hi;
   }
-  if (!DM) S.m[k] = mmax;
+  S.m[k] = mmax;
 }
 
 // Bound on the error of a component of the difference of two FP32 frame
@@ -291,8 +261,7 @@ __device__ __forceinline__ int packed_slot(int lane, bool fA, bool lA, bool fB, 
 template <bool MIXED, bool DM>
 __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const PatchTopo* topo,
                                         const stiv_pair_info& pi, int pa, int pb, int lane) {
-  int vi = pi.vi, vj = pi.vj, code = pi.code;
-  int s1[3] = {code / 9 - 1, (code / 3) % 3 - 1, code % 3 - 1};
+  int vi = pi.vi, vj = pi.vj;
   float dx = pi.frame.w;
   int PA = pi.Pij & 0xFFFF, PB = pi.Pij >> 16;
   int nbcA = stiv_ncol_blocks(PA), nbcB = stiv_ncol_blocks(PB);
@@ -302,8 +271,6 @@ __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const 
   auto stage_one = [&](bool onB, int k, float* b) {
     int P = onB ? PB : PA, I = onB ? IB : IA, J = onB ? JB : JA;
     int v = onB ? vj : vi;
-    int sh[3] = {onB ? s1[0] : 0, onB ? s1[1] : 0, onB ? s1[2] : 0};
-    double shd[3] = {sh[0] * a.L[0], sh[1] * a.L[1], sh[2] * a.L[2]};
     float off[3] = {onB ? pi.frame.x : 0.f, onB ? pi.frame.y : 0.f, onB ? pi.frame.z : 0.f};
     float org[3] = {0.f, 0.f, 0.f};
     if (MIXED) {
@@ -312,8 +279,7 @@ __device__ __noinline__ void stage_pair(WarpSm& ws, const narrow_args& a, const 
     }
     bool f = onB ? fB : fA, l = onB ? lB : lA;
     int vid = slot_vid(k, I * STIV_BR, J * STIV_BC, 2 * P, P, f, l);
-    stage_slot<MIXED, DM>(onB ? ws.B : ws.A, a, onB ? pi.voff_j : pi.voff_i, a.fprep + (size_t)v * a.fstride,
-                          stiv_nverts(P), vid, k, sh, shd, off, dx, b, onB ? a.dm : 0.0,
+    stage_slot<MIXED, DM>(onB ? ws.B : ws.A, a.fprep + (size_t)v * a.fstride, vid, k, off, dx, b,
                           onB ? __double2float_ru(a.dm) : 0.0f, org);
   };
   float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
@@ -1304,7 +1270,7 @@ __device__ __forceinline__ void load_f32(const int* sl, int kind, const PatchSm*
 // values themselves (FP64, or the FP32 values widened), the second vesicle's
 // points at the pair's periodic image (added in FP64): the test the staged
 // order keys perform, for the rare pair whose FP32 boxes do not decide it.
-template <bool MIXED>
+template <bool MIXED, bool DM>
 __device__ __noinline__ bool exact_box_hit(const narrow_args& a, int r, int kind, const PatchSm* SA, const PatchSm* SB,
                                            const int* sl) {
   const stiv_pair_info& pi = a.pinfo[r];
@@ -1325,8 +1291,13 @@ __device__ __noinline__ bool exact_box_hit(const narrow_args& a, int r, int kind
     for (int c = 0; c < 3; ++c) {
       double p0 = vtx<MIXED>(a.X, vb + (size_t)c * nv), p1 = vtx<MIXED>(a.X, vb + (size_t)(3 + c) * nv);
       if (onB && sB[c] != 0) { double shc = sB[c] * a.L[c]; p0 = p0 + shc; p1 = p1 + shc; }
-      lo[side][c] = fmin(lo[side][c], fmin(p0, p1));
-      hi[side][c] = fmax(hi[side][c], fmax(p0, p1));
+      double l = fmin(p0, p1), h = fmax(p0, p1);
+      if (DM && onB) {   // d_m > 0: vesicle j's boxes widened by d_m per vertex (FP64, as computed)
+        l = __dsub_rn(l, a.dm);
+        h = __dadd_rn(h, a.dm);
+      }
+      lo[side][c] = fmin(lo[side][c], l);
+      hi[side][c] = fmax(hi[side][c], h);
     }
   }
   bool hit = true;
@@ -1350,15 +1321,7 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
     // exact FP64 swept-box overlap
     int na = kind == 2 ? 2 : 1;
     bool hit = true;
-    if (DM) {   // order keys of the staged exact boxes
-      for (int c = 0; c < 3; ++c) {
-        long long alo = SA->key[c][sl[0]], ahi = SA->key[3 + c][sl[0]];
-        if (na == 2) { alo = min(alo, SA->key[c][sl[1]]); ahi = max(ahi, SA->key[3 + c][sl[1]]); }
-        long long blo = SB->key[c][sl[na]], bhi = SB->key[3 + c][sl[na]];
-        for (int q = na + 1; q < 4; ++q) { blo = min(blo, SB->key[c][sl[q]]); bhi = max(bhi, SB->key[3 + c][sl[q]]); }
-        hit = hit && alo <= bhi && blo <= ahi;
-      }
-    } else {
+    {
       // Each staged FP32 box end lies within m of the exact FP64 box end of
       // its slot (in the pair frame), so a slot's exact box contains its
       // FP32 box shrunk by 2m at each end.  If the shrunk boxes of the two
@@ -1366,11 +1329,14 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
       // m of the primitive's slots, which also covers the rounding of the
       // shrinking), the exact boxes overlap; the pair came through the
       // outward boxes of stage 1, so only the pairs in between need the exact
-      // test, on the FP64 values.
+      // test, on the FP64 values.  With d_m > 0 vesicle j's boxes are widened
+      // by d_m on both sides: FP32 rounded up, FP64 as computed per vertex;
+      // 2^-21 d_m covers the difference of the two roundings.
       float ma = SA->m[sl[0]], mb = SB->m[sl[na]];
       if (na == 2) ma = fmaxf(ma, SA->m[sl[1]]);
       for (int q = na + 1; q < 4; ++q) mb = fmaxf(mb, SB->m[sl[q]]);
       float gap = 3.0f * (ma + mb);
+      if (DM) gap += 4.7683716e-7f * __double2float_ru(a.dm);
       bool sure = true;
       for (int c = 0; c < 3; ++c) {
         float alo = SA->lo[c][sl[0]], ahi = SA->hi[c][sl[0]];
@@ -1379,7 +1345,7 @@ __device__ __noinline__ void stage_filter(WarpSm& ws, int n, int lane, int r, co
         for (int q = na + 1; q < 4; ++q) { blo = fminf(blo, SB->lo[c][sl[q]]); bhi = fmaxf(bhi, SB->hi[c][sl[q]]); }
         sure = sure && alo + gap <= bhi && blo + gap <= ahi;
       }
-      if (!sure) hit = exact_box_hit<MIXED>(a, r, kind, SA, SB, sl);
+      if (!sure) hit = exact_box_hit<MIXED, DM>(a, r, kind, SA, SB, sl);
     }
     if (hit) {
       ++nprim;
@@ -1867,9 +1833,9 @@ int stiv_narrow_phase(stiv_handle* h, cudaStream_t st, const int32_t* p_dev, con
   a.rc_pair = w.tmp_i32; a.rc_type = w.tmp_i32 + w.C; a.rc_a = w.tmp_i32 + 2 * w.C; a.rc_b = w.tmp_i32 + 3 * w.C;
   a.rc_tau = w.tmp_f64; a.rc_w = w.tmp_f64 + w.C;
   a.ctr = w.ctr;
-  size_t smem = stiv_narrow_smem();
   // d_m > 0: widened boxes and the degree-six test, in kernels of their own
   bool dmk = h->prm.d_m > 0.0;
+  size_t smem = stiv_narrow_smem();
   auto nk = mixed ? (dmk ? narrow_kernel<true, true> : narrow_kernel<true, false>)
                   : (dmk ? narrow_kernel<false, true> : narrow_kernel<false, false>);
   STIV_CUDA(h, cudaFuncSetAttribute(nk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
