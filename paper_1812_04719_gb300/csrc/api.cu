@@ -235,7 +235,7 @@ static int detect_layout(stiv_handle* h, int n, int p_max, const stiv_pairs* can
   size_t off = 0;
   size_t o_vbox = off; off = align_up(off + sizeof(double) * 6 * (size_t)n);
   w.pstride = stiv_npatches(2 * p_max);
-  size_t o_pbox = off; off = align_up(off + sizeof(float) * 6 * (size_t)w.pstride * n);
+  size_t o_pbox = off; off = align_up(off + sizeof(float) * STIV_PBOX * (size_t)w.pstride * n);
   w.fstride = 8 * (int64_t)stiv_nverts(2 * p_max);
   size_t o_vorg = off; off = align_up(off + sizeof(float) * 4 * (size_t)n);
   size_t o_fprep = off; off = align_up(off + sizeof(float) * (size_t)w.fstride * n);

@@ -191,65 +191,74 @@ __global__ void __launch_bounds__(256) boxes_kernel(int n, const int32_t* pv, co
     f4[2 * k] = make_float4(xo[0], xo[1], xo[2], 0.f);
     f4[2 * k + 1] = make_float4(dd[0], dd[1], dd[2], 0.f);
   }
-  // patch boxes: vertex rows [I*BR, min(I*BR+BR, P)], columns [J*BC, J*BC+ncol] (wrapping), poles.
-  // From the per-vertex FP32 boxes in shared memory when they fit: rounding
-  // outward is monotone, so the result equals rounding the FP64 min / max.
+  // patch boxes: vertex rows [I*BR, I*BR+BR], columns [J*BC, J*BC+BC]
+  // (wrapping), poles; each as the union of its four cells' boxes (band b of
+  // the two, column half h), every cell box written beside it.  Per column
+  // half, the boxes of its three rows are formed once and merged into its
+  // two cells.  P is even, so every patch
+  // spans BR bands and BC columns.  From the per-vertex FP32 boxes in shared
+  // memory when they fit: rounding outward is monotone, so the result equals
+  // rounding the FP64 min / max.
   int nbr = stiv_nband_blocks(P), nbc = stiv_ncol_blocks(P), W = 2 * P;
   __syncthreads();
-  if (use_sm) {
-    for (int patch = threadIdx.x; patch < nbr * nbc; patch += blockDim.x) {
-      int I = patch / nbc, J = patch % nbc;
-      int r0 = I * STIV_BR, r1 = min(r0 + STIV_BR, P);
-      int c0 = J * STIV_BC, nc = min(STIV_BC, W - c0);
-      float plo[3] = {INFINITY, INFINITY, INFINITY}, phi[3] = {-INFINITY, -INFINITY, -INFINITY};
-      for (int r = r0; r <= r1; ++r)
-        for (int cc = 0; cc <= nc; ++cc) {
-          int col = c0 + cc; if (col >= W) col -= W;
-          int vid = r * W + col;
-          for (int c = 0; c < 3; ++c) {
-            plo[c] = fminf(plo[c], vbs[c * nv + vid]);
-            phi[c] = fmaxf(phi[c], vbs[(3 + c) * nv + vid]);
-          }
-        }
-      for (int pole = 0; pole < 2; ++pole) {
-        if ((pole == 0 && I != 0) || (pole == 1 && I != nbr - 1)) continue;
-        int vid = W * (P + 1) + pole;
-        for (int c = 0; c < 3; ++c) {
-          plo[c] = fminf(plo[c], vbs[c * nv + vid]);
-          phi[c] = fmaxf(phi[c], vbs[(3 + c) * nv + vid]);
-        }
-      }
-      float* B = pbox + ((size_t)v * pstride + patch) * 6;
-      for (int c = 0; c < 3; ++c) { B[c] = plo[c]; B[3 + c] = phi[c]; }
-    }
-    return;
-  }
   for (int patch = threadIdx.x; patch < nbr * nbc; patch += blockDim.x) {
     int I = patch / nbc, J = patch % nbc;
-    int r0 = I * STIV_BR, r1 = min(r0 + STIV_BR, P);
-    int c0 = J * STIV_BC, nc = min(STIV_BC, W - c0);
-    double plo[3] = {INFINITY, INFINITY, INFINITY}, phi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int r = r0; r <= r1; ++r)
-      for (int cc = 0; cc <= nc; ++cc) {
-        int col = c0 + cc; if (col >= W) col -= W;
-        int vid = r * W + col;
-        for (int t = 0; t < 2; ++t)
-          for (int c = 0; c < 3; ++c) {
-            double x = vload(X, mixed, base + (size_t)(t * 3 + c) * nv + vid);
-            plo[c] = fmin(plo[c], x); phi[c] = fmax(phi[c], x);
-          }
-      }
-    for (int pole = 0; pole < 2; ++pole) {
-      if ((pole == 0 && I != 0) || (pole == 1 && I != nbr - 1)) continue;
-      int vid = W * (P + 1) + pole;
-      for (int t = 0; t < 2; ++t)
+    int r0 = I * STIV_BR, c0 = J * STIV_BC;
+    // per column half: rb[row][lo xyz, hi xyz] of its three rows; pb[pole]:
+    // FP32, rounded outward
+    float pb[2][6];
+    auto vbox_of = [&](int vid, float* o) {
+      if (use_sm) {
+        for (int c = 0; c < 3; ++c) { o[c] = vbs[c * nv + vid]; o[3 + c] = vbs[(3 + c) * nv + vid]; }
+      } else {
         for (int c = 0; c < 3; ++c) {
-          double x = vload(X, mixed, base + (size_t)(t * 3 + c) * nv + vid);
-          plo[c] = fmin(plo[c], x); phi[c] = fmax(phi[c], x);
+          double x0 = vload(X, mixed, base + (size_t)c * nv + vid), x1 = vload(X, mixed, base + (size_t)(3 + c) * nv + vid);
+          o[c] = __double2float_rd(fmin(x0, x1));
+          o[3 + c] = __double2float_ru(fmax(x0, x1));
         }
+      }
+    };
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      bool has = q == 0 ? I == 0 : I == nbr - 1;
+      if (has) vbox_of(W * (P + 1) + q, pb[q]);
+      else for (int c = 0; c < 3; ++c) { pb[q][c] = INFINITY; pb[q][3 + c] = -INFINITY; }
     }
-    float* B = pbox + ((size_t)v * pstride + patch) * 6;
-    for (int c = 0; c < 3; ++c) { B[c] = __double2float_rd(plo[c]); B[3 + c] = __double2float_ru(phi[c]); }
+    float* B = pbox + ((size_t)v * pstride + patch) * STIV_PBOX;
+    float plo[3] = {INFINITY, INFINITY, INFINITY}, phi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      float rb[3][6];
+#pragma unroll
+      for (int rr = 0; rr < 3; ++rr) {
+#pragma unroll
+        for (int cc = 0; cc <= 2; ++cc) {
+          int col = c0 + 2 * h + cc; if (col >= W) col -= W;
+          float o[6];
+          vbox_of((r0 + rr) * W + col, o);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            rb[rr][c] = cc == 0 ? o[c] : fminf(rb[rr][c], o[c]);
+            rb[rr][3 + c] = cc == 0 ? o[3 + c] : fmaxf(rb[rr][3 + c], o[3 + c]);
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        float lo[3], hi[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          lo[c] = fminf(fminf(rb[b][c], rb[b + 1][c]), pb[b][c]);
+          hi[c] = fmaxf(fmaxf(rb[b][3 + c], rb[b + 1][3 + c]), pb[b][3 + c]);
+          plo[c] = fminf(plo[c], lo[c]);
+          phi[c] = fmaxf(phi[c], hi[c]);
+        }
+        float4* C = (float4*)(B + STIV_PBOX_CELLS) + 2 * (2 * b + h);
+        C[0] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        C[1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+      }
+    }
+    for (int c = 0; c < 3; ++c) { B[c] = plo[c]; B[3 + c] = phi[c]; }
   }
 }
 

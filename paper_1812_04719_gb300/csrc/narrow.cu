@@ -1619,7 +1619,7 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
 // stage 4: the FP64 contact test, one descriptor per thread.
 // ---------------------------------------------------------------------------
 template <bool MIXED, bool DM>
-__global__ void __launch_bounds__(128) fp64_kernel(narrow_args a) {
+__global__ void __launch_bounds__(128, DM ? 8 : 1) fp64_kernel(narrow_args a) {
   int lane = threadIdx.x & 31;
   int64_t n2 = a.ctr[15];
   if (n2 > a.Q2) n2 = a.Q2;
@@ -1748,11 +1748,11 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
       bj[3 + c] = __fadd_ru(__double2float_ru(vbox[6 * j + 3 + c]), shhi[c]);
     }
     for (int k = lane; k < ni; k += 32)
-      for (int c = 0; c < 6; ++c) sbw[(0 * mp + k) * 6 + c] = pbox[((size_t)i * mp + k) * 6 + c];
+      for (int c = 0; c < 6; ++c) sbw[(0 * mp + k) * 6 + c] = pbox[((size_t)i * mp + k) * STIV_PBOX + c];
     for (int k = lane; k < nj; k += 32)
       for (int c = 0; c < 3; ++c) {
-        sbw[(1 * mp + k) * 6 + c] = __fadd_rd(pbox[((size_t)j * mp + k) * 6 + c], shlo[c]);
-        sbw[(1 * mp + k) * 6 + 3 + c] = __fadd_ru(pbox[((size_t)j * mp + k) * 6 + 3 + c], shhi[c]);
+        sbw[(1 * mp + k) * 6 + c] = __fadd_rd(pbox[((size_t)j * mp + k) * STIV_PBOX + c], shlo[c]);
+        sbw[(1 * mp + k) * 6 + 3 + c] = __fadd_ru(pbox[((size_t)j * mp + k) * STIV_PBOX + 3 + c], shhi[c]);
       }
     __syncwarp();
     int na = 0, nb = 0;
@@ -1778,6 +1778,29 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
       if (e < na * nb) {
         pa = law[e / nb]; pb = lbw[e % nb];
         hit = fbox_hit(&sbw[(0 * mp + pa) * 6], &sbw[(1 * mp + pb) * 6]);
+        if (hit) {
+          // every primitive lies in one of its patch's four cells: some cell
+          // of pa must meet some cell of pb (vesicle j's at its image,
+          // widened by d_m, rounded outward as the patch boxes)
+          const float4* ca = (const float4*)(pbox + ((size_t)i * mp + pa) * STIV_PBOX + STIV_PBOX_CELLS);
+          const float4* cb = (const float4*)(pbox + ((size_t)j * mp + pb) * STIV_PBOX + STIV_PBOX_CELLS);
+          float bB[4][6];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float4 l = cb[2 * q], u = cb[2 * q + 1];
+            bB[q][0] = __fadd_rd(l.x, shlo[0]); bB[q][1] = __fadd_rd(l.y, shlo[1]); bB[q][2] = __fadd_rd(l.z, shlo[2]);
+            bB[q][3] = __fadd_ru(u.x, shhi[0]); bB[q][4] = __fadd_ru(u.y, shhi[1]); bB[q][5] = __fadd_ru(u.z, shhi[2]);
+          }
+          bool any = false;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float4 l = ca[2 * q], u = ca[2 * q + 1];
+            float bA[6] = {l.x, l.y, l.z, u.x, u.y, u.z};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) any = any || fbox_hit(bA, bB[w]);
+          }
+          hit = any;
+        }
       }
       unsigned m = __ballot_sync(0xffffffffu, hit);
       if (m) {

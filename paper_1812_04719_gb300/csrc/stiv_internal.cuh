@@ -17,6 +17,14 @@
 #define STIV_MAX_PP 64         // largest mesh order P
 #define STIV_BR 2              // patch height in grid bands
 #define STIV_BC 4              // patch width in grid columns
+// Floats per patch in the patch-box array (160 bytes): floats 0-5 the
+// patch's swept box (lo xyz, hi xyz), 6-7 unused, then floats 8 + 8 c to
+// 15 + 8 c the box of cell c as a float4 pair (lo xyz, 0; hi xyz, 0), cell
+// c = 2 b + h for band b and column half h: rows I*BR + b .. + 1, columns
+// J*BC + 2 h .. + 2, with the pole of that band.  Every primitive of the
+// patch lies in one cell.
+#define STIV_PBOX 40
+#define STIV_PBOX_CELLS 8
 
 // ---------------------------------------------------------------------------
 // handle and scratch
