@@ -49,11 +49,11 @@ NARROW_SRC = os.path.join(ROOT, "paper_1812_04719_gb300", "csrc", "narrow.cu")
 # csrc/narrow.cu differs from the captured source (SHA-256 prefix), the
 # instruction roofline and the traffic are reported as null.
 NARROW_NCU = {
-    "src_sha256": "2dd4c40ecb93dc0c",
-    # 108696210 inst, 8429568 + 982016 B over 44989 patch pairs
-    "fp64": {"inst_per_patch_pair": 2416.06, "dram_bytes_per_patch_pair": 209.19},
-    # 110544262 inst, 8447744 + 1272320 B over 44988 patch pairs
-    "mixed": {"inst_per_patch_pair": 2457.20, "dram_bytes_per_patch_pair": 216.06},
+    "src_sha256": "fa0867f38bae9abf",
+    # 103304406 inst, 7199488 + 953856 B over 35339 patch pairs
+    "fp64": {"inst_per_patch_pair": 2923.24, "dram_bytes_per_patch_pair": 230.72},
+    # 103061110 inst, 7204096 + 946432 B over 35339 patch pairs
+    "mixed": {"inst_per_patch_pair": 2916.36, "dram_bytes_per_patch_pair": 230.64},
 }
 ISSUE_PER_SM_CLK = 4   # warp instructions an SM can issue per clock (4 schedulers)
 METRIC = "vesicle-steps/s of detect+V+∇V at p=16→32, 58% vf; % of roofline vs FP64 form"
