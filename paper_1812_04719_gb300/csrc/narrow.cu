@@ -586,18 +586,14 @@ __device__ int inside_cert(int kind, const f3* x, const f3* d, float t0, float w
 // a sum of triple products u . (v x w) of difference vectors (six terms each);
 // ep / ed bound the input errors of the positions / displacements per
 // component.  Each triple product's error is bounded with the magnitudes of
-// its own three vectors (tp below), so a pair whose displacement differences
-// are small (a primitive moving nearly rigidly) keeps a tight bound.
+// its own three vectors, so a pair whose displacement differences are small
+// (a primitive moving nearly rigidly) keeps a tight bound:  with eu, ev, ew
+// the component errors of u, v, w and Au, Av, Aw their largest computed
+// components, each of the six terms obeys |xyz - x'y'z'| <= |x - x'||y'||z'|
+// + |x||y - y'||z'| + |x||y||z - z'| with |y'| <= Ay + ey, so the product's
+// error is at most 6 ((Au + eu)(Av + ev)(Aw + ew) - Au Av Aw + rr Au Av Aw)
+// (rr: the relative rounding of the FP32 evaluation per term).
 struct cubic32 { float k0, k1, k2, k3, E, ed; };
-
-// Error bound of the FP32 triple product u . (v x w) against the exact one:
-// eu, ev, ew bound the component errors of u, v, w; Au, Av, Aw their largest
-// computed components.  For each of the six terms, |xyz - x'y'z'| <=
-// |x - x'| |y'| |z'| + |x| |y - y'| |z'| + |x| |y| |z - z'| with |y'| <= Ay + ey;
-// rr bounds the relative rounding of the FP32 evaluation per term.
-__device__ __forceinline__ float tp_err(float eu, float Au, float ev, float Av, float ew, float Aw, float rr) {
-  return 6.f * (eu * (Av + ev) * (Aw + ew) + Au * ev * (Aw + ew) + Au * Av * ew + rr * Au * Av * Aw);
-}
 
 // es: the error bound of the same-vesicle differences a and b (at most 2 ep).
 __device__ __forceinline__ cubic32 cubic_fp32(int kind, const f3* x, const f3* d, float ep, float es) {
@@ -628,15 +624,19 @@ __device__ __forceinline__ cubic32 cubic_fp32(int kind, const f3* x, const f3* d
   float ea = es + 2.0f * U32 * Aa, eb = es + 2.0f * U32 * Ab, ec = 2.0f * ep + 2.0f * U32 * Ac;
   float eda = 2.0f * ed + 2.0f * U32 * Ada, edb = 2.0f * ed + 2.0f * U32 * Adb, edc = 2.0f * ed + 2.0f * U32 * Adc;
   float rr = 8.0f * U32;                         // rounding per term
-  float E0 = tp_err(ec, Ac, ea, Aa, eb, Ab, rr);                                    // c . (a x b)
-  float E1 = tp_err(edc, Adc, ea, Aa, eb, Ab, rr) + tp_err(ec, Ac, eda, Ada, eb, Ab, rr) +
-             tp_err(ec, Ac, ea, Aa, edb, Adb, rr);                                  // dc.(a x b) + c.(da x b + a x db)
-  float E2 = tp_err(ec, Ac, eda, Ada, edb, Adb, rr) + tp_err(edc, Adc, eda, Ada, eb, Ab, rr) +
-             tp_err(edc, Adc, ea, Aa, edb, Adb, rr);                                // c.(da x db) + dc.(da x b + a x db)
-  float E3 = tp_err(edc, Adc, eda, Ada, edb, Adb, rr);                              // dc . (da x db)
+  // The coefficients are sums of the eight triple products u . (v x w) with
+  // u in {c, dc}, v in {a, da}, w in {b, db} (k0: c.(a x b); k1: dc.(a x b),
+  // c.(da x b), c.(a x db); k2: c.(da x db), dc.(da x b), dc.(a x db); k3:
+  // dc.(da x db)).  The sum of their bounds (above) factors over the three
+  // choices: with U = Ac + Adc, V = Aa + Ada, W = Ab + Adb and eU, eV, eW the
+  // sums of the matching errors, it is 6 ((U + eU)(V + eV)(W + eW) - U V W
+  // + rr U V W), evaluated below without cancellation.
+  float U = Ac + Adc, V = Aa + Ada, W = Ab + Adb;
+  float eU = ec + edc, eV = ea + eda, eW = eb + edb;
+  float Esum = 6.f * (eU * (V + eV) * (W + eW) + U * eV * (W + eW) + U * V * eW + rr * U * V * W);
   float S = fabsf(r.k0) + fabsf(r.k1) + fabsf(r.k2) + fabsf(r.k3);
   float M = (A + Ad) * (A + Ad) * (A + Ad);
-  r.E = 1.25f * (E0 + E1 + E2 + E3) + 64.f * U32 * S + 1e-12f * 48.f * M;
+  r.E = 1.25f * Esum + 64.f * U32 * S + 1e-12f * 48.f * M;
   r.ed = ed;
   return r;
 }
