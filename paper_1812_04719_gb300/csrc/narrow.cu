@@ -1763,12 +1763,45 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
       if (hit) law[na + __popc(m & ((1u << lane) - 1u))] = (unsigned short)k;
       na += __popc(m);
     }
+    // union box of a list of staged patch boxes (side 0: A, 1: B)
+    auto list_union = [&](const unsigned short* lst, int n, int side, float* u) {
+      float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int q = lane; q < n; q += 32) {
+        const float* bx = &sbw[(side * mp + lst[q]) * 6];
+        for (int c = 0; c < 3; ++c) { lo[c] = fminf(lo[c], bx[c]); hi[c] = fmaxf(hi[c], bx[3 + c]); }
+      }
+      for (int c = 0; c < 3; ++c) {
+        u[c] = fkey_val(__reduce_min_sync(0xffffffffu, fkey32(lo[c])));
+        u[3 + c] = fkey_val(__reduce_max_sync(0xffffffffu, fkey32(hi[c])));
+      }
+    };
+    // B's patches against the union of A's kept patches (a patch of B that
+    // meets a kept patch of A meets their union), then A's kept patches
+    // against the union of B's
+    __syncwarp();
+    float ua[6], ub[6];
+    list_union(law, na, 0, ua);
     for (int k0 = 0; k0 < nj; k0 += 32) {
       int k = k0 + lane;
-      bool hit = k < nj && fbox_hit(&sbw[(1 * mp + k) * 6], bi);
+      bool hit = k < nj && fbox_hit(&sbw[(1 * mp + k) * 6], ua);
       unsigned m = __ballot_sync(0xffffffffu, hit);
       if (hit) lbw[nb + __popc(m & ((1u << lane) - 1u))] = (unsigned short)k;
       nb += __popc(m);
+    }
+    __syncwarp();
+    list_union(lbw, nb, 1, ub);
+    {
+      int na2 = 0;
+      for (int q0 = 0; q0 < na; q0 += 32) {
+        int q = q0 + lane;
+        int k = q < na ? law[q] : 0;
+        bool hit = q < na && fbox_hit(&sbw[(0 * mp + k) * 6], ub);
+        unsigned m = __ballot_sync(0xffffffffu, hit);
+        __syncwarp();
+        if (hit) law[na2 + __popc(m & ((1u << lane) - 1u))] = (unsigned short)k;
+        na2 += __popc(m);
+      }
+      na = na2;
     }
     __syncwarp();
     for (int e0 = 0; e0 < na * nb; e0 += 32) {
