@@ -1619,7 +1619,7 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
 // stage 4: the FP64 contact test, one descriptor per thread.
 // ---------------------------------------------------------------------------
 template <bool MIXED, bool DM>
-__global__ void __launch_bounds__(128, DM ? 8 : 1) fp64_kernel(narrow_args a) {
+__global__ void __launch_bounds__(128, DM ? 8 : 6) fp64_kernel(narrow_args a) {
   int lane = threadIdx.x & 31;
   int64_t n2 = a.ctr[15];
   if (n2 > a.Q2) n2 = a.Q2;
