@@ -593,9 +593,13 @@ __device__ int inside_cert(int kind, const f3* x, const f3* d, float t0, float w
 // + |x||y - y'||z'| + |x||y||z - z'| with |y'| <= Ay + ey, so the product's
 // error is at most 6 ((Au + eu)(Av + ev)(Aw + ew) - Au Av Aw + rr Au Av Aw)
 // (rr: the relative rounding of the FP32 evaluation per term).
-struct cubic32 { float k0, k1, k2, k3, E, ed; };
+// With d_m > 0 the band test also takes mn = |n0| + |n1| + |n2| (the FP32
+// normals' magnitudes) and the largest position / displacement difference
+// components A2, Ad2 of the primitive's own pair of vectors (a, b / da, db).
+struct cubic32 { float k0, k1, k2, k3, E, ed, mn, A2, Ad2; };
 
 // es: the error bound of the same-vesicle differences a and b (at most 2 ep).
+template <bool WM = false>
 __device__ __forceinline__ cubic32 cubic_fp32(int kind, const f3* x, const f3* d, float ep, float es) {
   f3 a, b, c, da, db, dc;
   if (kind == 0) {
@@ -638,6 +642,11 @@ __device__ __forceinline__ cubic32 cubic_fp32(int kind, const f3* x, const f3* d
   float M = (A + Ad) * (A + Ad) * (A + Ad);
   r.E = 1.25f * Esum + 64.f * U32 * S + 1e-12f * 48.f * M;
   r.ed = ed;
+  if (WM) {
+    r.mn = fnorm(n0) + fnorm(n1) + fnorm(n2);
+    r.A2 = fmaxf(Aa, Ab);
+    r.Ad2 = fmaxf(Ada, Adb);
+  }
   return r;
 }
 
@@ -663,23 +672,12 @@ __device__ int bernstein_reject(const cubic32& q) {
 // cross products with their error bounds (the error model of cubic_fp32); a
 // margin of 1e-12 of the squared magnitudes covers the FP64 evaluation of g.
 // Right-hand side of the band test: (d_m max|m|)^2 with its margins.
-__device__ float band_rhs(int kind, const f3* x, const f3* d, float ep, float dm, const cubic32& q) {
-  f3 a, b, da, db;
-  if (kind == 0) {
-    a = fsub(x[2], x[1]); b = fsub(x[3], x[1]); da = fsub(d[2], d[1]); db = fsub(d[3], d[1]);
-  } else {
-    a = fsub(x[1], x[0]); b = fsub(x[3], x[2]); da = fsub(d[1], d[0]); db = fsub(d[3], d[2]);
-  }
-  f3 n0 = fcross(a, b), n1 = fadd(fcross(da, b), fcross(a, db)), n2 = fcross(da, db);
-  float A = fmaxf(amax3(a), amax3(b)), Ad = fmaxf(amax3(da), amax3(db));
-  float Dm = 0.f;
-  for (int k = 0; k < 4; ++k) Dm = fmaxf(Dm, amax3(d[k]));
-  float ed = 2.0f * U32 * Dm + 1e-12f;
+__device__ float band_rhs(const cubic32& q, float ep, float dm) {
+  float A = q.A2, Ad = q.Ad2, ed = q.ed;
   float epd = 2.0f * ep + 2.0f * U32 * A, edd = 2.0f * ed + 2.0f * U32 * Ad;
   float en = 2.0f * ((4.f * epd * A + 4.f * U32 * A * A) + (4.f * edd * A + 4.f * epd * Ad + 8.f * U32 * A * Ad) +
                      (4.f * edd * Ad + 4.f * U32 * Ad * Ad));
-  float mn = fnorm(n0) + fnorm(n1) + fnorm(n2);
-  float mmax = mn * (1.f + 8.f * U32) + en;
+  float mmax = q.mn * (1.f + 8.f * U32) + en;
   float S = fabsf(q.k0) + fabsf(q.k1) + fabsf(q.k2) + fabsf(q.k3) + 4.f * q.E;
   float dmm = dm * (1.f + 4.f * U32) * mmax;
   return dmm * dmm * (1.f + 1e-5f) + 1e-12f * (S * S + dmm * dmm);
@@ -694,10 +692,10 @@ __device__ __forceinline__ bool out_of_band(float c0, float c1, float c2, float 
 }
 
 __device__ int band_reject(int kind, const f3* x, const f3* d, float ep, float es, float dm) {
-  cubic32 q = cubic_fp32(kind, x, d, ep, es);
+  cubic32 q = cubic_fp32<true>(kind, x, d, ep, es);
   float b1 = q.k0 + q.k1 * (1.f / 3.f), b2 = q.k0 + (2.f * q.k1 + q.k2) * (1.f / 3.f), b3 = q.k0 + q.k1 + q.k2 + q.k3;
   if (!certain_sign4(q.k0, b1, b2, b3, q.E)) return 0;
-  return out_of_band(q.k0, b1, b2, b3, q.E, band_rhs(kind, x, d, ep, dm, q)) ? 1 : 0;
+  return out_of_band(q.k0, b1, b2, b3, q.E, band_rhs(q, ep, dm)) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1516,14 +1514,14 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
       f3 xq[4], dq[4];
       float ep, es;
       desc_points_f32(a, e, kind, xq, dq, ep, es);
-      cubic32 q = cubic_fp32(kind, xq, dq, ep, es);
+      cubic32 q = cubic_fp32<DM>(kind, xq, dq, ep, es);
       for (int p = 0; p < 4; ++p) {
         W.x[lane][p][0] = xq[p].x; W.x[lane][p][1] = xq[p].y; W.x[lane][p][2] = xq[p].z;
         W.d[lane][p][0] = dq[p].x; W.d[lane][p][1] = dq[p].y; W.d[lane][p][2] = dq[p].z;
       }
       W.k[lane][0] = q.k0; W.k[lane][1] = q.k1; W.k[lane][2] = q.k2; W.k[lane][3] = q.k3;
       W.E[lane] = q.E; W.ep[lane] = ep; W.ed[lane] = q.ed; W.es[lane] = es; W.kind[lane] = kind;
-      if (DM) W.rhs[lane] = band_rhs(kind, xq, dq, ep, (float)a.dm, q);
+      if (DM) W.rhs[lane] = band_rhs(q, ep, (float)a.dm);
       if (fabsf(q.k0) <= q.E && fabsf(q.k1) <= q.E && fabsf(q.k2) <= q.E && fabsf(q.k3) <= q.E) {
         W.fail[lane] = 1;   // may vanish identically: FP64 decides (degenerate)
       } else {
@@ -1741,9 +1739,8 @@ __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, con
       // d_m > 0: vesicle j's patch boxes widened by d_m (rounded outward)
       shlo[c] = __double2float_rd(__dsub_rd(sh, dm)); shhi[c] = __double2float_ru(__dadd_ru(sh, dm));
     }
-    float bi[6], bj[6];
+    float bj[6];   // vesicle j's box at its image (A's patches are filtered against it)
     for (int c = 0; c < 3; ++c) {
-      bi[c] = __double2float_rd(vbox[6 * i + c]); bi[3 + c] = __double2float_ru(vbox[6 * i + 3 + c]);
       bj[c] = __fadd_rd(__double2float_rd(vbox[6 * j + c]), shlo[c]);
       bj[3 + c] = __fadd_ru(__double2float_ru(vbox[6 * j + 3 + c]), shhi[c]);
     }
