@@ -49,11 +49,11 @@ NARROW_SRC = os.path.join(ROOT, "paper_1812_04719_gb300", "csrc", "narrow.cu")
 # csrc/narrow.cu differs from the captured source (SHA-256 prefix), the
 # instruction roofline and the traffic are reported as null.
 NARROW_NCU = {
-    "src_sha256": "1c4bb8076985f65b",
-    # 97860990 inst, 7212800 + 954624 B over 35339 patch pairs
-    "fp64": {"inst_per_patch_pair": 2769.21, "dram_bytes_per_patch_pair": 231.12},
-    # 97617838 inst, 7217152 + 866304 B over 35339 patch pairs
-    "mixed": {"inst_per_patch_pair": 2762.33, "dram_bytes_per_patch_pair": 228.74},
+    "src_sha256": "5f1fb818e0492fd7",
+    # 97860990 inst, 7215616 + 975872 B over 35339 patch pairs
+    "fp64": {"inst_per_patch_pair": 2769.21, "dram_bytes_per_patch_pair": 231.80},
+    # 97617838 inst, 7210752 + 868864 B over 35339 patch pairs
+    "mixed": {"inst_per_patch_pair": 2762.33, "dram_bytes_per_patch_pair": 228.63},
 }
 ISSUE_PER_SM_CLK = 4   # warp instructions an SM can issue per clock (4 schedulers)
 METRIC = "vesicle-steps/s of detect+V+∇V at p=16→32, 58% vf; % of roofline vs FP64 form"

@@ -20,8 +20,6 @@
 
 namespace {
 
-__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
-
 template <typename T>
 __device__ __forceinline__ double ld(const void* p, size_t i) { return (double)((const T*)p)[i]; }
 

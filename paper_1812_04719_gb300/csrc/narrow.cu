@@ -1266,8 +1266,9 @@ __device__ __forceinline__ void load_f32(const int* sl, int kind, const PatchSm*
 
 // The exact FP64 swept-box test of a queued primitive pair from the vertex
 // values themselves (FP64, or the FP32 values widened), the second vesicle's
-// points at the pair's periodic image (added in FP64): the test the staged
-// order keys perform, for the rare pair whose FP32 boxes do not decide it.
+// points at the pair's periodic image (added in FP64) and, with d_m > 0, its
+// per-vertex boxes widened by d_m: the test that defines the pairs tested,
+// for the rare pair whose FP32 boxes and their error bound do not decide it.
 template <bool MIXED, bool DM>
 __device__ __noinline__ bool exact_box_hit(const narrow_args& a, int r, int kind, const PatchSm* SA, const PatchSm* SB,
                                            const int* sl) {
