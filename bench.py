@@ -49,11 +49,11 @@ NARROW_SRC = os.path.join(ROOT, "paper_1812_04719_gb300", "csrc", "narrow.cu")
 # csrc/narrow.cu differs from the captured source (SHA-256 prefix), the
 # instruction roofline and the traffic are reported as null.
 NARROW_NCU = {
-    "src_sha256": "5f1fb818e0492fd7",
-    # 97860990 inst, 7215616 + 975872 B over 35339 patch pairs
-    "fp64": {"inst_per_patch_pair": 2769.21, "dram_bytes_per_patch_pair": 231.80},
-    # 97617838 inst, 7210752 + 868864 B over 35339 patch pairs
-    "mixed": {"inst_per_patch_pair": 2762.33, "dram_bytes_per_patch_pair": 228.63},
+    "src_sha256": "92e5397a85063d40",
+    # 97860990 inst, 7229952 + 889600 B over 35339 patch pairs
+    "fp64": {"inst_per_patch_pair": 2769.21, "dram_bytes_per_patch_pair": 229.76},
+    # 97617838 inst, 7206144 + 858880 B over 35339 patch pairs
+    "mixed": {"inst_per_patch_pair": 2762.33, "dram_bytes_per_patch_pair": 228.22},
 }
 ISSUE_PER_SM_CLK = 4   # warp instructions an SM can issue per clock (4 schedulers)
 METRIC = "vesicle-steps/s of detect+V+∇V at p=16→32, 58% vf; % of roofline vs FP64 form"
@@ -561,8 +561,9 @@ def run_ours(args, rank, world, local):
 
     # stage 4 alone: the FP64 operations it executed over its time; and the
     # narrow phase's effective rate: the FP64 contact test's operations on
-    # every exact-box pair (SURVEY's algorithmic count, most of which the
-    # certified FP32 cascade avoids) over the four kernels' time
+    # every exact-box pair (the algorithmic count of the method's narrow
+    # phase, most of which the certified FP32 cascade avoids) over the four
+    # kernels' time
     fp64_ms = stage_ms.get("fp64", 0.0)
     roof_fp64 = None
     if fp64_ms > 0:

@@ -1,12 +1,14 @@
 // Narrow phase of Alg. 2 checkContact: every vertex-triangle pair (both
 // directions) and edge-edge pair of a candidate vesicle pair whose swept boxes
-// overlap is tested with the coplanarity cubic of Eq. 3.1 (d_m = 0).
+// overlap is tested with the coplanarity cubic of Eq. 3.1 (d_m = 0), or with
+// the degree-six equation of the d_m band (d_m > 0).
 //
 // The triangulated grid (Sec. 3.1.2, Fig. 3) is cut into patches of 2 x 4 grid
 // quads; each primitive belongs to exactly one patch, so each primitive pair
 // is examined by exactly one patch pair.
 //   patch_pairs_kernel: per candidate vesicle pair, one warp lists the patch
-//     pairs whose FP32 (outward) boxes overlap;
+//     pairs whose FP32 (outward) boxes overlap and some of whose cells (1 x 2
+//     quads) meet;
 //   narrow_kernel (stages 1-3a): per patch pair, one warp stages both patches
 //     in shared memory and filters the primitive pairs; the survivors leave
 //     as global pair descriptors;
@@ -1615,7 +1617,10 @@ __global__ void __launch_bounds__(PW * 32, 4) pieces_kernel(narrow_args a) {
 }
 
 // ---------------------------------------------------------------------------
-// stage 4: the FP64 contact test, one descriptor per thread.
+// stage 4: the FP64 contact test, one descriptor per thread.  The register
+// budget is capped (6 blocks of 128 threads per SM, 80 registers, for the
+// cubic; 8 blocks, 64 registers, for d_m > 0): the dependent FP64 operations
+// need the warps more than the spilled registers cost.
 // ---------------------------------------------------------------------------
 template <bool MIXED, bool DM>
 __global__ void __launch_bounds__(128, DM ? 8 : 6) fp64_kernel(narrow_args a) {
@@ -1697,8 +1702,12 @@ __global__ void __launch_bounds__(128, DM ? 8 : 6) fp64_kernel(narrow_args a) {
   }
 }
 
-// Level 1: patch pairs of one candidate vesicle pair per warp.  Dynamic shared
-// memory: per warp 2 x mp patch boxes and 2 x mp list entries.
+// Level 1: patch pairs of one candidate vesicle pair per warp.  A's patches
+// are kept that meet vesicle j's box, then B's that meet the union of A's
+// kept patches, then A's that meet the union of B's; a pair of kept patches
+// is emitted when their boxes overlap and some cell of one meets some cell
+// of the other (every primitive lies in one cell of its patch).  Dynamic
+// shared memory: per warp 2 x mp patch boxes and 2 x mp list entries.
 __global__ void __launch_bounds__(128) patch_pairs_kernel(const int32_t* pv, const double* vbox, const float* pbox,
                                                           double Lx, double Ly, double Lz, const int32_t* ci,
                                                           const int32_t* cj, const int32_t* cs, int64_t cap,
